@@ -1,0 +1,163 @@
+/*
+ * ar.h - C ABI of the GB300 (sm_103a) Anti-Reflective deblurring library.
+ *
+ * The library implements the hot path of the preconditioned Landweber
+ * restoration of Dell'Acqua, Serra-Capizzano and Tablino-Possio, "Optimal
+ * preconditioning for image deblurring with Anti-Reflective boundary
+ * conditions": the AR blurring matrix A_n (Section 2.2 boundary rules and
+ * eq. modello_discreto), its reblurred counterpart A' (Section 4), and the
+ * optimal preconditioner D = T_n diag(d) T~_n (Theorems 1, 2 and 4, eq.
+ * TikFilter) inside the D-Landweber iteration (eq. DLandweberMeth).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Images are n1 x n2, row-major (row index i1, column index i2), float32,
+ *    contiguous, in DEVICE memory owned by the caller.  n1, n2 >= 3.
+ *  - A PSF of support q = (q1, q2) is a (2q1+1) x (2q2+1) row-major array with
+ *    psf[(i1+q1)*(2q2+1) + (i2+q2)] = h_{i1,i2} (eq. coefficienti_psf).
+ *    The blur is a true convolution, g_i = sum_s h_s f_{i-s}.
+ *    0 <= q_j <= n_j - 1 for the blur (the anti-reflection must stay inside
+ *    the image); the preconditioner additionally needs q_j <= n_j - 3 (the
+ *    support condition of Section 2.2).  q_j <= 15 runs on the fast
+ *    register-blocked kernels, larger supports on a generic kernel.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous on `stream` unless stated otherwise.
+ *  - Every call returns an ar_status; AR_OK is 0.  Nothing throws across
+ *    the ABI.  ar_status_string() names a status; ar_last_error_detail()
+ *    gives a human-readable detail of the last failure on the calling thread.
+ *  - No call keeps a pointer to caller memory after it returns (asynchronous
+ *    calls read/write it in stream order).
+ */
+#ifndef AR_H
+#define AR_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ar_status {
+    AR_OK = 0,
+    AR_ERR_INVALID_ARG = 1,        /* null pointer, bad size or support, alpha <= 0, ... */
+    AR_ERR_ALIAS = 2,              /* an output overlaps an input it must not overlap */
+    AR_ERR_PSF_NOT_NORMALIZED = 3, /* |sum(h) - 1| > 1e-6 where the method needs sum(h) = 1 */
+    AR_ERR_ALLOC = 4,              /* device or host allocation failed */
+    AR_ERR_CUDA = 5,               /* a CUDA runtime/driver call failed */
+    AR_ERR_NONFINITE = 6,          /* the restoration produced NaN or Inf */
+    AR_ERR_TIMEOUT = 7,            /* a bounded device-side wait gave up */
+    AR_ERR_UNSUPPORTED = 8         /* valid request this build cannot serve (e.g. no sm_103a GPU) */
+} ar_status;
+
+/* Opaque preconditioner: the symmetrized-PSF eigenvalues and Tikhonov filter
+ * for one (PSF, n1, n2, alpha), plus the AR transform operands and scratch
+ * used by ar_symprec_solve.  Owned by the library; free with
+ * ar_symprec_destroy. */
+typedef struct ar_prec ar_prec;
+
+/*
+ * y = A_n x : anti-reflective blur (Section 2.2 extension rules applied
+ * separably, which yields the double anti-reflection at the corners, then the
+ * convolution of eq. modello_discreto).
+ *   x, y    device float32, n1*n2 each; y must not overlap x (AR_ERR_ALIAS).
+ *   psf     device float32, (2q1+1)*(2q2+1).  Not required to sum to one.
+ * Errors: AR_ERR_INVALID_ARG (null pointer, n_j < 1, q_j < 0 or q_j > n_j - 1),
+ *         AR_ERR_ALIAS, AR_ERR_CUDA (launch failure).
+ */
+ar_status ar_blur_apply(const float* x, float* y, int n1, int n2,
+                        const float* psf, int q1, int q2, void* stream);
+
+/*
+ * y = A' x : the reblurred matrix of Section 4, i.e. the AR blur with the PSF
+ * rotated by 180 degrees (h'_s = h_{-s}).  A' differs from A^T under AR BCs.
+ * Arguments and errors as ar_blur_apply.
+ */
+ar_status ar_reblur_apply(const float* x, float* y, int n1, int n2,
+                          const float* psf, int q1, int q2, void* stream);
+
+/*
+ * Build the optimal AR preconditioner (Theorem 4) for a PSF and image size:
+ *   S0  s = symmetrized PSF, eq. simmetrizzata2d, in float64 on the GPU;
+ *   S1  lambda[i1,i2] = f_s(x1_{i1}, x2_{i2}), the symbol of eq.
+ *       funzione_generatrice on the AR grid of Theorem 2 (x = 0 for the first
+ *       and last index, k*pi/(n-1) for k = 1..n-2), float64 on the GPU;
+ *   S2  d = 1/(lambda^2 + alpha), eq. TikFilter, float64 on the GPU, kept in
+ *       float64 and rounded once to float32 for the iteration;
+ * and the AR transform operands of Theorem 1 (T_m, T~_m with the
+ * normalisation alpha_m dropped, which cancels in T diag(d) T~).
+ *   psf_host host float64 (2q1+1)*(2q2+1); must sum to 1 within 1e-6.
+ *   alpha    Tikhonov parameter, > 0.
+ *   out      receives the new object (left untouched on error).
+ * Synchronizes `stream` before returning.
+ * Errors: AR_ERR_INVALID_ARG (null, n_j < 3, q_j > n_j - 3, alpha <= 0 or not
+ *         finite), AR_ERR_PSF_NOT_NORMALIZED, AR_ERR_ALLOC, AR_ERR_CUDA.
+ */
+ar_status ar_symprec_setup(const double* psf_host, int q1, int q2, int n1, int n2,
+                           double alpha, void* stream, ar_prec** out);
+
+/*
+ * z = D y = T_n diag(d) T~_n y (Theorem 1 with the filtered eigenvalues).
+ *   y, z device float32, n1*n2 (the sizes given at setup).  z may equal y
+ *   (in-place) but must not partially overlap it.
+ * Uses scratch owned by P: concurrent solves with the same P on different
+ * streams race; use one preconditioner per stream.
+ * Errors: AR_ERR_INVALID_ARG, AR_ERR_ALIAS, AR_ERR_CUDA.
+ */
+ar_status ar_symprec_solve(const ar_prec* P, const float* y, float* z, void* stream);
+
+/*
+ * Copy the float64 eigenvalues lambda and filter d of P to host arrays of
+ * n1*n2 doubles each (either may be NULL).  Synchronous.
+ */
+ar_status ar_symprec_eigenvalues(const ar_prec* P, double* lambda_host, double* d_host);
+
+/* Sizes a preconditioner was built for (either pointer may be NULL). */
+ar_status ar_symprec_shape(const ar_prec* P, int* n1, int* n2);
+
+/* Free a preconditioner (NULL is a no-op).  Waits for its pending work. */
+void ar_symprec_destroy(ar_prec* P);
+
+/*
+ * (D-)Landweber restoration with reblurring, eqs. LandweberMeth and
+ * DLandweberMeth with A' in place of A^H (Section 4):
+ *     x_{k+1} = x_k + tau * D * A'(g - A x_k),  k = 0..iters-1,
+ * D = I when precondition == 0, else the preconditioner of ar_symprec_setup
+ * built inside the call from psf_host and alpha.
+ *   g          device float32 n1*n2, the observed image.
+ *   psf_host   host float64 PSF; must sum to 1 within 1e-6.
+ *   alpha      Tikhonov parameter (> 0; ignored when precondition == 0).
+ *   tau        step (> 0); the paper uses 1.
+ *   iters      >= 0 iterations.
+ *   x0         device float32 start image or NULL for x_0 = 0.  May equal x_out.
+ *   f_true     device float32 true image or NULL.  When given, the relative
+ *              restoration error ||x_{k+1} - f||_F / ||f||_F of every iterate
+ *              is accumulated in float64 on the GPU.
+ *   x_out      device float32 n1*n2, the final iterate; must not overlap g or f_true.
+ *   rre_trace  host double[iters] or NULL (needs f_true): RRE of x_1..x_iters.
+ *   best_iter  host int or NULL (needs f_true): first k in 1..iters with the
+ *              minimum RRE (the tables' IT); 0 when iters == 0.
+ * Synchronizes `stream` before returning.  Scratch is taken from the stream's
+ * memory pool (cudaMallocAsync) and returned before the call ends.
+ * Errors: AR_ERR_INVALID_ARG, AR_ERR_ALIAS, AR_ERR_PSF_NOT_NORMALIZED,
+ *         AR_ERR_ALLOC, AR_ERR_CUDA, AR_ERR_NONFINITE (x_out holds NaN/Inf;
+ *         the iterate is still written).
+ */
+ar_status ar_restore(const float* g, const double* psf_host,
+                     int n1, int n2, int q1, int q2, double alpha, double tau,
+                     int iters, int precondition,
+                     const float* x0, const float* f_true, float* x_out,
+                     double* rre_trace, int* best_iter, void* stream);
+
+/* Static name of a status code ("AR_OK", ...; "AR_UNKNOWN" otherwise). */
+const char* ar_status_string(ar_status s);
+
+/* Detail of the last failure on the calling thread ("" if none).  Valid
+ * until the next failing call on the same thread. */
+const char* ar_last_error_detail(void);
+
+/* Library version string. */
+const char* ar_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AR_H */
