@@ -1,0 +1,400 @@
+"""Benchmark of the AR-BC preconditioned Landweber restoration on one GB300.
+
+One step = one ``ar_restore`` call on the 1024 x 1024 ellipses scene blurred by
+the 15 x 15 motion PSF (0.5% noise): float64 setup of the symmetrized-PSF
+preconditioner, 50 D-Landweber iterations (two AR stencils and the AR
+transform pair each), float64 RRE of every iterate, non-finite scan.
+
+The JSON line reports Mpixel*iter/s with inputs resident in HBM (``value``),
+the same through host buffers (``e2e``), the roofline of the dominant kernel,
+the FP64 oracle timed on the host cores (``cpu_baseline``), clocks sampled
+during the timed region, and the restoration quality of the preconditioned
+method against plain Landweber.  ``--impl reference`` times the FP64 oracle
+instead (a bounded sample per step).
+
+Run with several GPUs through torchrun: every rank restores its own copy of
+the workload (independent problems, no collective on the data path).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1211_0393_gb300 import workloads as W  # noqa: E402
+
+METRIC = "AR-PCG Mpixel·iter/s at 1024²; time & iters to oracle-matched error vs plain"
+UNIT = "Mpixel*iter/s"
+WORKLOAD = "ellipses1024_motion15"
+N1 = N2 = 1024
+ITERS = 50
+ALPHA = 0.3          # smallest half-decade alpha for which tau = 1 is stable with this PSF
+TAU = 1.0
+NU = 0.005
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-quality", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def config_dict(extra=None):
+    c = {"workload": WORKLOAD, "n1": N1, "n2": N2, "psf": "15x15 motion(len 11, 30 deg)+0.2 gauss",
+         "iters_per_step": ITERS, "alpha": ALPHA, "tau": TAU, "precondition": True, "noise": NU,
+         "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MiB write)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ------------------------------------------------------------------ inputs --
+
+def make_host_inputs(ar, torch, dev):
+    """Seeded scene, PSF and noise; g = crop(A_ext scene) + noise, blurred on the GPU.
+
+    The crop of the AR blur of the scene extended by q on every side is the
+    plain 'valid' convolution of the wider scene (eq. modello_discreto_sistema).
+    """
+    h = W.psf_config2()
+    q1, q2 = (h.shape[0] - 1) // 2, (h.shape[1] - 1) // 2
+    ext, f, e = W.make_inputs(N1, N2, h, "ellipses", 1)
+    ext_d = torch.from_numpy(ext.astype(np.float32)).to(dev)
+    blurred = ar.ar_blur_apply(ext_d, torch.from_numpy(h.astype(np.float32)).to(dev))
+    gc = W.crop(blurred.cpu().numpy().astype(np.float64), q1, q2)
+    g = W.add_noise(gc, e, NU).astype(np.float32)
+    return h, g, f.astype(np.float32)
+
+
+# ----------------------------------------------------------------- clocks ---
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        under = [v for v in sm if smax and v > 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(under) if under else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- own arm ----
+
+def run_own(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1211_0393_gb300 import ar
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    ar.lib()
+    stream = torch.cuda.current_stream(dev)
+
+    h, g, f = make_host_inputs(ar, torch, dev)
+    g_d = torch.from_numpy(g).to(dev)
+    f_d = torch.from_numpy(f).to(dev)
+    x_d = torch.empty_like(g_d)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        return ar.ar_restore(g_d, h, ALPHA, TAU, ITERS, True, f_true=f_d, x_out=x_d)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(local_rank)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    launches0 = ar.kernel_launches()
+    for i in range(args.steps):
+        flush.fill_(float(i))                     # evict the previous step's data from L2
+        ev[i][0].record(stream)
+        _, trace, best = step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    launches = ar.kernel_launches() - launches0
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units = N1 * N2 * ITERS * args.steps * world / 1e6
+    value = units / (total_ms / 1e3)
+
+    # ---- end to end through host buffers: H2D of g and f, restore, D2H of x
+    g_h = torch.from_numpy(g).pin_memory()
+    f_h = torch.from_numpy(f).pin_memory()
+    x_h = torch.empty_like(g_h).pin_memory()
+    e2e_ms = []
+    for i in range(max(args.steps, 1)):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g_d.copy_(g_h, non_blocking=True)
+        f_d.copy_(f_h, non_blocking=True)
+        step()
+        x_h.copy_(x_d, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_total = sum(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = N1 * N2 * ITERS * len(e2e_ms) * world / 1e6 / (e2e_total / 1e3)
+
+    out = None
+    if rank == 0:
+        roof, kernels = kernel_rooflines(ar, torch, dev, stream, h, g_d, flush)
+        out = {
+            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_dict({"parallelism": f"replicas{world}" if world > 1 else "single"}),
+            "e2e": {"value": round(e2e_value, 2), "unit": UNIT,
+                    "h2d_bytes_per_step": int(g.nbytes + f.nbytes),
+                    "d2h_bytes_per_step": int(g.nbytes + 8 * ITERS + 8 * (ITERS + 1))},
+            "roofline": roof,
+            "kernels": kernels,
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "rre_last_step": {"best_iter": best, "rre_best": float(np.min(trace)),
+                              "rre_final": float(trace[-1])},
+        }
+        if not args.no_quality:
+            out["quality"] = quality_vs_plain(ar, torch, g_d, f_d, h)
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(h, g, f)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+def _time_launches(torch, stream, fn, reps, flush):
+    """Average device time of `fn` over `reps` launches, L2 flushed before each."""
+    tot = 0.0
+    for i in range(reps):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    return tot / reps
+
+
+def kernel_rooflines(ar, torch, dev, stream, h, g_d, flush):
+    """Per-kernel timings on the bench shapes (CUDA events on the launching stream)."""
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    smax = peaks.get("sm_max_mhz", 2070.0)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = nsm * 128 * 2 * smax * 1e6 / 1e12          # TFLOP/s, FFMA = 2 flops
+    k1, k2 = h.shape
+    h_d = torch.from_numpy(h.astype(np.float32)).to(dev)
+    y = torch.empty_like(g_d)
+    t_conv = _time_launches(torch, stream, lambda: ar.ar_blur_apply(g_d, h_d, y), 20, flush)
+    conv_flops = 2.0 * k1 * k2 * N1 * N2
+    P = ar.ar_symprec_setup(h, N1, N2, ALPHA)
+    z = torch.empty_like(g_d)
+    t_solve = _time_launches(torch, stream, lambda: ar.ar_symprec_solve(P, g_d, z), 10, flush)
+    P.close()
+    gemm_flops = 4 * 2.0 * N1 * N2 * (N1 + N2) / 2            # four n^3 contractions
+    kernels = {
+        "conv_fast_q7": {"ms": round(t_conv, 5), "tflops": round(conv_flops / t_conv / 1e9, 2),
+                         "bound": "alu", "peak_tflops_fp32": round(fp32_peak, 1),
+                         "hbm_gbs": round(8.0 * N1 * N2 / t_conv / 1e6, 1)},
+        "transform_D_4_contractions": {"ms": round(t_solve, 5),
+                                       "tflops_fp32_equiv": round(gemm_flops / t_solve / 1e9, 2)},
+    }
+    # dominant kernel per iteration: 2 stencils vs one 4-contraction transform
+    if 2 * t_conv >= t_solve:
+        roof = {"kernel": "conv_fast_q7", "bound": "alu", "achieved": round(conv_flops / t_conv / 1e9, 3),
+                "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
+                "frac": round(conv_flops / t_conv / 1e9 / fp32_peak, 4), "traffic": None,
+                "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock (MEASURED_PEAKS sm_max_mhz)"}
+    else:
+        ach = gemm_flops / 4 / (t_solve / 4) / 1e9
+        roof = {"kernel": "transform_contraction", "bound": "alu", "achieved": round(ach, 3),
+                "peak": round(fp32_peak, 1), "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4),
+                "traffic": None,
+                "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock (MEASURED_PEAKS sm_max_mhz)"}
+    return roof, kernels
+
+
+def quality_vs_plain(ar, torch, g_d, f_d, h):
+    """Iterations and time for D-Landweber and plain Landweber to reach the
+    plain method's best RRE (within 1%), both on the GPU."""
+    plain_iters = 200
+    t0 = time.perf_counter()
+    _, tr_p, best_p = ar.ar_restore(g_d, h, ALPHA, TAU, plain_iters, False, f_true=f_d)
+    t_plain = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, tr_d, best_d = ar.ar_restore(g_d, h, ALPHA, TAU, ITERS, True, f_true=f_d)
+    t_prec = time.perf_counter() - t0
+    target = float(np.min(tr_p)) * 1.01
+
+    def first(tr):
+        idx = np.nonzero(tr <= target)[0]
+        return int(idx[0]) + 1 if len(idx) else None
+
+    kp, kd = first(tr_p), first(tr_d)
+    return {"target_rre": round(target, 6), "plain_best_rre": float(np.min(tr_p)),
+            "plain_best_iter": best_p, "precond_best_rre": float(np.min(tr_d)),
+            "precond_best_iter": best_d, "plain_iters_to_target": kp,
+            "precond_iters_to_target": kd,
+            "plain_ms_to_target": round(t_plain * 1e3 * kp / plain_iters, 3) if kp else None,
+            "precond_ms_to_target": round(t_prec * 1e3 * kd / ITERS, 3) if kd else None}
+
+
+# ------------------------------------------------------------ oracle arm ----
+
+ORACLE_SAMPLE_ITERS = 3          # per reference-arm step
+CPU_BASELINE_ITERS = 12          # about 10 s of oracle work on the host cores
+
+
+def oracle_sample(h, g, f, iters):
+    import oracle as O
+
+    t0 = time.perf_counter()
+    O.restore(g.astype(np.float64), h, ALPHA, TAU, iters, True, f_true=f.astype(np.float64))
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(h, g, f):
+    iters = CPU_BASELINE_ITERS
+    oracle_sample(h, g, f, 1)
+    dt = oracle_sample(h, g, f, iters)
+    return {"value": round(N1 * N2 * iters / dt / 1e6, 4), "unit": UNIT,
+            "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"FP64 NumPy oracle, {iters} D-Landweber iterations (setup included) of the "
+                      f"{WORKLOAD} workload; numpy default threads",
+            "seconds": round(dt, 3)}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    # inputs built on the host without a GPU: blur the extended scene with the oracle
+    import oracle as O
+
+    h = W.psf_config2()
+    q1, q2 = 7, 7
+    ext, f, e = W.make_inputs(N1, N2, h, "ellipses", 1)
+    g = W.add_noise(W.crop(O.ar_blur(ext, h), q1, q2), e, NU).astype(np.float32)
+    f = f.astype(np.float32)
+    iters = ORACLE_SAMPLE_ITERS
+    for _ in range(max(args.warmup, 0)):
+        oracle_sample(h, g, f, 1)
+    tot = 0.0
+    for _ in range(args.steps):
+        tot += oracle_sample(h, g, f, iters)
+    value = N1 * N2 * iters * args.steps / 1e6 / tot
+    cb = {"value": round(value, 4), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+          "sample": f"FP64 NumPy oracle, {iters} D-Landweber iterations (setup included) per step of "
+                    f"the {WORKLOAD} workload (warm-up steps run 1 iteration)"}
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot / args.steps * 1e3, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict({"iters_per_step": iters}),
+        "cpu_baseline": cb,
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_own(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -12,7 +12,8 @@
  * Conventions shared by every call
  * --------------------------------
  *  - Images are n1 x n2, row-major (row index i1, column index i2), float32,
- *    contiguous, in DEVICE memory owned by the caller.  n1, n2 >= 3.
+ *    contiguous, in DEVICE memory owned by the caller.  n1, n2 >= 1 for the
+ *    blur, >= 3 wherever the preconditioner is involved.
  *  - A PSF of support q = (q1, q2) is a (2q1+1) x (2q2+1) row-major array with
  *    psf[(i1+q1)*(2q2+1) + (i2+q2)] = h_{i1,i2} (eq. coefficienti_psf).
  *    The blur is a true convolution, g_i = sum_s h_s f_{i-s}.
@@ -30,6 +31,12 @@
  */
 #ifndef AR_H
 #define AR_H
+
+#if defined(__GNUC__)
+#define AR_API __attribute__((visibility("default")))
+#else
+#define AR_API
+#endif
 
 #ifdef __cplusplus
 extern "C" {
@@ -62,7 +69,7 @@ typedef struct ar_prec ar_prec;
  * Errors: AR_ERR_INVALID_ARG (null pointer, n_j < 1, q_j < 0 or q_j > n_j - 1),
  *         AR_ERR_ALIAS, AR_ERR_CUDA (launch failure).
  */
-ar_status ar_blur_apply(const float* x, float* y, int n1, int n2,
+AR_API ar_status ar_blur_apply(const float* x, float* y, int n1, int n2,
                         const float* psf, int q1, int q2, void* stream);
 
 /*
@@ -70,7 +77,7 @@ ar_status ar_blur_apply(const float* x, float* y, int n1, int n2,
  * rotated by 180 degrees (h'_s = h_{-s}).  A' differs from A^T under AR BCs.
  * Arguments and errors as ar_blur_apply.
  */
-ar_status ar_reblur_apply(const float* x, float* y, int n1, int n2,
+AR_API ar_status ar_reblur_apply(const float* x, float* y, int n1, int n2,
                           const float* psf, int q1, int q2, void* stream);
 
 /*
@@ -90,7 +97,7 @@ ar_status ar_reblur_apply(const float* x, float* y, int n1, int n2,
  * Errors: AR_ERR_INVALID_ARG (null, n_j < 3, q_j > n_j - 3, alpha <= 0 or not
  *         finite), AR_ERR_PSF_NOT_NORMALIZED, AR_ERR_ALLOC, AR_ERR_CUDA.
  */
-ar_status ar_symprec_setup(const double* psf_host, int q1, int q2, int n1, int n2,
+AR_API ar_status ar_symprec_setup(const double* psf_host, int q1, int q2, int n1, int n2,
                            double alpha, void* stream, ar_prec** out);
 
 /*
@@ -101,19 +108,19 @@ ar_status ar_symprec_setup(const double* psf_host, int q1, int q2, int n1, int n
  * streams race; use one preconditioner per stream.
  * Errors: AR_ERR_INVALID_ARG, AR_ERR_ALIAS, AR_ERR_CUDA.
  */
-ar_status ar_symprec_solve(const ar_prec* P, const float* y, float* z, void* stream);
+AR_API ar_status ar_symprec_solve(const ar_prec* P, const float* y, float* z, void* stream);
 
 /*
  * Copy the float64 eigenvalues lambda and filter d of P to host arrays of
  * n1*n2 doubles each (either may be NULL).  Synchronous.
  */
-ar_status ar_symprec_eigenvalues(const ar_prec* P, double* lambda_host, double* d_host);
+AR_API ar_status ar_symprec_eigenvalues(const ar_prec* P, double* lambda_host, double* d_host);
 
 /* Sizes a preconditioner was built for (either pointer may be NULL). */
-ar_status ar_symprec_shape(const ar_prec* P, int* n1, int* n2);
+AR_API ar_status ar_symprec_shape(const ar_prec* P, int* n1, int* n2);
 
 /* Free a preconditioner (NULL is a no-op).  Waits for its pending work. */
-void ar_symprec_destroy(ar_prec* P);
+AR_API void ar_symprec_destroy(ar_prec* P);
 
 /*
  * (D-)Landweber restoration with reblurring, eqs. LandweberMeth and
@@ -140,21 +147,25 @@ void ar_symprec_destroy(ar_prec* P);
  *         AR_ERR_ALLOC, AR_ERR_CUDA, AR_ERR_NONFINITE (x_out holds NaN/Inf;
  *         the iterate is still written).
  */
-ar_status ar_restore(const float* g, const double* psf_host,
+AR_API ar_status ar_restore(const float* g, const double* psf_host,
                      int n1, int n2, int q1, int q2, double alpha, double tau,
                      int iters, int precondition,
                      const float* x0, const float* f_true, float* x_out,
                      double* rre_trace, int* best_iter, void* stream);
 
 /* Static name of a status code ("AR_OK", ...; "AR_UNKNOWN" otherwise). */
-const char* ar_status_string(ar_status s);
+AR_API const char* ar_status_string(ar_status s);
 
 /* Detail of the last failure on the calling thread ("" if none).  Valid
  * until the next failing call on the same thread. */
-const char* ar_last_error_detail(void);
+AR_API const char* ar_last_error_detail(void);
+
+/* Number of kernels this library has launched in this process (all devices,
+ * all threads), for launch accounting by benchmarks. */
+AR_API unsigned long long ar_kernel_launches(void);
 
 /* Library version string. */
-const char* ar_version(void);
+AR_API const char* ar_version(void);
 
 #ifdef __cplusplus
 }

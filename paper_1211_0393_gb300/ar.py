@@ -1,0 +1,232 @@
+"""ctypes binding of ``libar.so``: the C ABI of ``include/ar.h`` under the same names.
+
+Argument marshalling only: every function checks tensor placement, dtype and
+shape, passes raw pointers and the current CUDA stream, and turns a non-zero
+``ar_status`` into :class:`ARError`.  All arithmetic happens in the library's
+CUDA kernels.  Importing this module on a machine without the built library
+raises immediately; there is no fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libar.so")
+
+STATUS = {
+    0: "AR_OK", 1: "AR_ERR_INVALID_ARG", 2: "AR_ERR_ALIAS", 3: "AR_ERR_PSF_NOT_NORMALIZED",
+    4: "AR_ERR_ALLOC", 5: "AR_ERR_CUDA", 6: "AR_ERR_NONFINITE", 7: "AR_ERR_TIMEOUT",
+    8: "AR_ERR_UNSUPPORTED",
+}
+
+EXPORTS = [
+    "ar_blur_apply", "ar_reblur_apply", "ar_symprec_setup", "ar_symprec_solve",
+    "ar_symprec_eigenvalues", "ar_symprec_shape", "ar_symprec_destroy", "ar_restore",
+    "ar_status_string", "ar_last_error_detail", "ar_version", "ar_kernel_launches",
+]
+
+
+class ARError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        self.status = status
+        self.name = STATUS.get(status, f"AR_UNKNOWN({status})")
+        super().__init__(f"{where}: {self.name}: {detail}")
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_d = ctypes.c_double
+
+
+def lib() -> ctypes.CDLL:
+    """Load ``libar.so`` once; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} not built; run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "ar_blur_apply": [_vp, _vp, _i, _i, _vp, _i, _i, _vp],
+            "ar_reblur_apply": [_vp, _vp, _i, _i, _vp, _i, _i, _vp],
+            "ar_symprec_setup": [_vp, _i, _i, _i, _i, _d, _vp, ctypes.POINTER(_vp)],
+            "ar_symprec_solve": [_vp, _vp, _vp, _vp],
+            "ar_symprec_eigenvalues": [_vp, _vp, _vp],
+            "ar_symprec_shape": [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)],
+            "ar_restore": [_vp, _vp, _i, _i, _i, _i, _d, _d, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = _i
+        L.ar_symprec_destroy.argtypes = [_vp]
+        L.ar_symprec_destroy.restype = None
+        for name in ("ar_status_string",):
+            getattr(L, name).argtypes = [_i]
+            getattr(L, name).restype = ctypes.c_char_p
+        for name in ("ar_last_error_detail", "ar_version"):
+            getattr(L, name).argtypes = []
+            getattr(L, name).restype = ctypes.c_char_p
+        L.ar_kernel_launches.argtypes = []
+        L.ar_kernel_launches.restype = ctypes.c_ulonglong
+        _lib = L
+    return _lib
+
+
+def _check(status: int, where: str) -> None:
+    if status != 0:
+        raise ARError(status, where, lib().ar_last_error_detail().decode())
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _image(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or t.dim() != 2:
+        raise TypeError(f"{name} must be a 2D float32 CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _support(psf_shape) -> tuple[int, int]:
+    k1, k2 = psf_shape
+    if k1 % 2 == 0 or k2 % 2 == 0:
+        raise ValueError("PSF sides must be odd")
+    return (k1 - 1) // 2, (k2 - 1) // 2
+
+
+def _host_psf(psf) -> np.ndarray:
+    h = psf.detach().cpu().numpy() if isinstance(psf, torch.Tensor) else np.asarray(psf)
+    return np.ascontiguousarray(h, dtype=np.float64)
+
+
+def ar_blur_apply(x: torch.Tensor, psf: torch.Tensor, y: torch.Tensor | None = None,
+                  stream=None) -> torch.Tensor:
+    """``y = A_n x`` (AR blur).  ``psf`` is a float32 CUDA tensor of odd sides."""
+    return _apply("ar_blur_apply", x, psf, y, stream)
+
+
+def ar_reblur_apply(x: torch.Tensor, psf: torch.Tensor, y: torch.Tensor | None = None,
+                    stream=None) -> torch.Tensor:
+    """``y = A' x`` (AR blur with the PSF rotated by 180 degrees)."""
+    return _apply("ar_reblur_apply", x, psf, y, stream)
+
+
+def _apply(name, x, psf, y, stream):
+    _image(x, "x")
+    if not isinstance(psf, torch.Tensor) or not psf.is_cuda or psf.dtype != torch.float32:
+        raise TypeError("psf must be a float32 CUDA tensor")
+    psf = psf.contiguous()
+    q1, q2 = _support(psf.shape)
+    if y is None:
+        y = torch.empty_like(x)
+    _image(y, "y")
+    if y.shape != x.shape:
+        raise ValueError("y must have the shape of x")
+    n1, n2 = x.shape
+    _check(getattr(lib(), name)(x.data_ptr(), y.data_ptr(), n1, n2, psf.data_ptr(), q1, q2,
+                                _stream(stream)), name)
+    return y
+
+
+class Prec:
+    """Owner of an ``ar_prec*`` (freed with ``ar_symprec_destroy``)."""
+
+    def __init__(self, handle: int, n1: int, n2: int):
+        self.handle = handle
+        self.shape = (n1, n2)
+
+    def close(self) -> None:
+        if self.handle:
+            lib().ar_symprec_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ar_symprec_setup(psf, n1: int, n2: int, alpha: float, stream=None) -> Prec:
+    """Build the symmetrized-PSF AR preconditioner (float64 setup on the GPU)."""
+    h = _host_psf(psf)
+    q1, q2 = _support(h.shape)
+    out = _vp()
+    _check(lib().ar_symprec_setup(h.ctypes.data, q1, q2, n1, n2, float(alpha), _stream(stream),
+                                  ctypes.byref(out)), "ar_symprec_setup")
+    return Prec(out.value, n1, n2)
+
+
+def ar_symprec_solve(P: Prec, y: torch.Tensor, z: torch.Tensor | None = None,
+                     stream=None) -> torch.Tensor:
+    """``z = D y = T diag(d) T~ y``."""
+    _image(y, "y")
+    if tuple(y.shape) != P.shape:
+        raise ValueError(f"y has shape {tuple(y.shape)}, preconditioner expects {P.shape}")
+    if z is None:
+        z = torch.empty_like(y)
+    _image(z, "z")
+    _check(lib().ar_symprec_solve(P.handle, y.data_ptr(), z.data_ptr(), _stream(stream)),
+           "ar_symprec_solve")
+    return z
+
+
+def ar_symprec_eigenvalues(P: Prec) -> tuple[np.ndarray, np.ndarray]:
+    """Float64 ``(lambda, d)`` of the preconditioner, copied to the host."""
+    lam = np.empty(P.shape, dtype=np.float64)
+    d = np.empty(P.shape, dtype=np.float64)
+    _check(lib().ar_symprec_eigenvalues(P.handle, lam.ctypes.data, d.ctypes.data),
+           "ar_symprec_eigenvalues")
+    return lam, d
+
+
+def ar_symprec_shape(P: Prec) -> tuple[int, int]:
+    a, b = _i(), _i()
+    _check(lib().ar_symprec_shape(P.handle, ctypes.byref(a), ctypes.byref(b)), "ar_symprec_shape")
+    return a.value, b.value
+
+
+def ar_restore(g: torch.Tensor, psf, alpha: float, tau: float = 1.0, iters: int = 20,
+               precondition: bool = True, x0: torch.Tensor | None = None,
+               f_true: torch.Tensor | None = None, x_out: torch.Tensor | None = None,
+               trace: bool = True, stream=None):
+    """(D-)Landweber restoration.  Returns ``(x, rre_trace or None, best_iter or None)``."""
+    _image(g, "g")
+    h = _host_psf(psf)
+    q1, q2 = _support(h.shape)
+    n1, n2 = g.shape
+    if x_out is None:
+        x_out = torch.empty_like(g)
+    _image(x_out, "x_out")
+    want = f_true is not None and trace
+    tr = np.zeros(max(iters, 1), dtype=np.float64) if want else None
+    best = _i(0)
+    _check(lib().ar_restore(
+        g.data_ptr(), h.ctypes.data, n1, n2, q1, q2, float(alpha), float(tau), int(iters),
+        1 if precondition else 0,
+        _image(x0, "x0").data_ptr() if x0 is not None else None,
+        _image(f_true, "f_true").data_ptr() if f_true is not None else None,
+        x_out.data_ptr(),
+        tr.ctypes.data if want else None,
+        ctypes.addressof(best) if want else None,
+        _stream(stream)), "ar_restore")
+    return x_out, (tr[:iters] if want else None), (best.value if want else None)
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(lib().ar_kernel_launches())
+
+
+def version() -> str:
+    return lib().ar_version().decode()

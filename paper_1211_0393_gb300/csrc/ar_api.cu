@@ -1,0 +1,393 @@
+// C ABI of the library: argument validation, the preconditioner object and
+// the (D-)Landweber restoration loop (eqs. LandweberMeth / DLandweberMeth with
+// the reblurred A' of Section 4).  All arithmetic runs in the kernels of the
+// other translation units; this file only validates, allocates and launches.
+
+#include "ar_internal.cuh"
+
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+namespace ar {
+
+static thread_local char g_detail[512] = "";
+
+ar_status fail(ar_status s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_detail, sizeof(g_detail), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+ar_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? AR_ERR_ALLOC : AR_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launch(unsigned k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+int sm_count() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+    if (!cached[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = v > 0 ? v : 148;
+    }
+    return cached[dev];
+}
+
+}  // namespace ar
+
+using namespace ar;
+
+namespace {
+
+bool overlaps(const void* a, size_t abytes, const void* b, size_t bbytes) {
+    const char* pa = static_cast<const char*>(a);
+    const char* pb = static_cast<const char*>(b);
+    return pa < pb + bbytes && pb < pa + abytes;
+}
+
+ar_status check_image_sizes(int n1, int n2, int nmin) {
+    if (n1 < nmin || n2 < nmin)
+        return fail(AR_ERR_INVALID_ARG, "image sizes n1=%d n2=%d must be >= %d", n1, n2, nmin);
+    if ((long long)n1 * (long long)n2 > (1LL << 31))
+        return fail(AR_ERR_INVALID_ARG, "image of %d x %d exceeds 2^31 pixels", n1, n2);
+    return AR_OK;
+}
+
+ar_status check_support(int n1, int n2, int q1, int q2, int margin) {
+    if (q1 < 0 || q2 < 0 || q1 > n1 - margin || q2 > n2 - margin)
+        return fail(AR_ERR_INVALID_ARG,
+                    "PSF support q=(%d,%d) must satisfy 0 <= q_j <= n_j - %d for n=(%d,%d)", q1, q2,
+                    margin, n1, n2);
+    return AR_OK;
+}
+
+ar_status check_psf_host(const double* h, int q1, int q2) {
+    const size_t k = (size_t)(2 * q1 + 1) * (2 * q2 + 1);
+    double s = 0.0;
+    for (size_t i = 0; i < k; ++i) {
+        if (!std::isfinite(h[i])) return fail(AR_ERR_INVALID_ARG, "PSF entry %zu is not finite", i);
+        s += h[i];
+    }
+    if (std::fabs(s - 1.0) > 1e-6)
+        return fail(AR_ERR_PSF_NOT_NORMALIZED, "PSF sums to %.17g, expected 1 within 1e-6", s);
+    return AR_OK;
+}
+
+void set_pool_threshold_once() {
+    static bool done[64] = {false};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        unsigned long long thr = ~0ULL;  // keep freed blocks in this process's pool
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    done[dev] = true;
+}
+
+// Stream-ordered scratch released in the destructor (in stream order).
+struct Scratch {
+    cudaStream_t s;
+    std::vector<void*> ptrs;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    ~Scratch() {
+        for (void* p : ptrs) cudaFreeAsync(p, s);
+    }
+    template <class T>
+    ar_status get(T** p, size_t count) {
+        void* q = nullptr;
+        cudaError_t e = cudaMallocAsync(&q, count * sizeof(T) + 16, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (scratch)");
+        ptrs.push_back(q);
+        *p = static_cast<T*>(q);
+        return AR_OK;
+    }
+};
+
+ar_status apply_common(const float* x, float* y, int n1, int n2, const float* psf, int q1, int q2,
+                       void* stream, int flip) {
+    if (!x || !y || !psf) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
+    AR_TRY(check_image_sizes(n1, n2, 1));
+    AR_TRY(check_support(n1, n2, q1, q2, 1));
+    const size_t nb = (size_t)n1 * n2 * sizeof(float);
+    const size_t kb = (size_t)(2 * q1 + 1) * (2 * q2 + 1) * sizeof(float);
+    if (overlaps(x, nb, y, nb)) return fail(AR_ERR_ALIAS, "output image overlaps the input image");
+    if (overlaps(psf, kb, y, nb)) return fail(AR_ERR_ALIAS, "output image overlaps the PSF");
+    ConvArgs a{};
+    a.x = x;
+    a.out = y;
+    a.psf = psf;
+    a.n1 = n1;
+    a.n2 = n2;
+    a.q1 = q1;
+    a.q2 = q2;
+    a.flip = flip;
+    a.mode = CONV_STORE;
+    return conv_launch(a, static_cast<cudaStream_t>(stream));
+}
+
+// Builds the preconditioner's device data on `s` without synchronizing.
+ar_status prec_build(const double* psf_host, int q1, int q2, int n1, int n2, double alpha,
+                     cudaStream_t s, bool keep64, ar_prec** out) {
+    set_pool_threshold_once();
+    ar_prec* P = new (std::nothrow) ar_prec();
+    if (!P) return fail(AR_ERR_ALLOC, "host allocation of ar_prec");
+    std::memset(P, 0, sizeof(*P));
+    P->n1 = n1;
+    P->n2 = n2;
+    P->q1 = q1;
+    P->q2 = q2;
+    P->alpha = alpha;
+    cudaGetDevice(&P->device);
+    const size_t n = (size_t)n1 * n2;
+    const size_t k = (size_t)(2 * q1 + 1) * (2 * q2 + 1);
+    ar_status st = AR_OK;
+    {
+        Scratch tmp(s);
+        double* h64 = nullptr;
+        double* work = nullptr;
+        st = tmp.get(&h64, k);
+        if (st == AR_OK) st = tmp.get(&work, setup_scratch_doubles(q1, q2, n1, n2));
+        if (st == AR_OK) {
+            cudaError_t e = cudaMemcpyAsync(h64, psf_host, k * sizeof(double),
+                                            cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) st = cuda_fail(e, "PSF upload");
+        }
+        if (st == AR_OK && keep64) {
+            if (cudaMallocAsync((void**)&P->lam64, n * sizeof(double), s) != cudaSuccess ||
+                cudaMallocAsync((void**)&P->d64, n * sizeof(double), s) != cudaSuccess)
+                st = fail(AR_ERR_ALLOC, "eigenvalue buffers");
+        }
+        if (st == AR_OK && cudaMallocAsync((void**)&P->d32, n * sizeof(float), s) != cudaSuccess)
+            st = fail(AR_ERR_ALLOC, "filter buffer");
+        if (st == AR_OK) st = setup_eigen(h64, q1, q2, n1, n2, alpha, P->lam64, P->d64, P->d32, work, s);
+        if (st == AR_OK) st = transform_plan_create(n1, n2, s, &P->plan);
+    }
+    if (st != AR_OK) {
+        ar_symprec_destroy(P);
+        return st;
+    }
+    *out = P;
+    return AR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ar_status_string(ar_status s) {
+    switch (s) {
+        case AR_OK: return "AR_OK";
+        case AR_ERR_INVALID_ARG: return "AR_ERR_INVALID_ARG";
+        case AR_ERR_ALIAS: return "AR_ERR_ALIAS";
+        case AR_ERR_PSF_NOT_NORMALIZED: return "AR_ERR_PSF_NOT_NORMALIZED";
+        case AR_ERR_ALLOC: return "AR_ERR_ALLOC";
+        case AR_ERR_CUDA: return "AR_ERR_CUDA";
+        case AR_ERR_NONFINITE: return "AR_ERR_NONFINITE";
+        case AR_ERR_TIMEOUT: return "AR_ERR_TIMEOUT";
+        case AR_ERR_UNSUPPORTED: return "AR_ERR_UNSUPPORTED";
+    }
+    return "AR_UNKNOWN";
+}
+
+const char* ar_last_error_detail(void) { return g_detail; }
+
+const char* ar_version(void) { return "ar-gb300 0.1 (sm_103a)"; }
+
+unsigned long long ar_kernel_launches(void) { return g_launches.load(); }
+
+ar_status ar_blur_apply(const float* x, float* y, int n1, int n2, const float* psf, int q1, int q2,
+                        void* stream) {
+    return apply_common(x, y, n1, n2, psf, q1, q2, stream, 0);
+}
+
+ar_status ar_reblur_apply(const float* x, float* y, int n1, int n2, const float* psf, int q1,
+                          int q2, void* stream) {
+    return apply_common(x, y, n1, n2, psf, q1, q2, stream, 1);
+}
+
+ar_status ar_symprec_setup(const double* psf_host, int q1, int q2, int n1, int n2, double alpha,
+                           void* stream, ar_prec** out) {
+    if (!psf_host || !out) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
+    AR_TRY(check_image_sizes(n1, n2, 3));
+    AR_TRY(check_support(n1, n2, q1, q2, 3));
+    if (!(alpha > 0.0) || !std::isfinite(alpha))
+        return fail(AR_ERR_INVALID_ARG, "alpha must be finite and > 0 (got %g)", alpha);
+    AR_TRY(check_psf_host(psf_host, q1, q2));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ar_prec* P = nullptr;
+    AR_TRY(prec_build(psf_host, q1, q2, n1, n2, alpha, s, true, &P));
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        ar_symprec_destroy(P);
+        return cuda_fail(e, "setup");
+    }
+    *out = P;
+    return AR_OK;
+}
+
+ar_status ar_symprec_solve(const ar_prec* P, const float* y, float* z, void* stream) {
+    if (!P || !y || !z) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
+    const size_t nb = (size_t)P->n1 * P->n2 * sizeof(float);
+    if (y != z && overlaps(y, nb, z, nb)) return fail(AR_ERR_ALIAS, "z partially overlaps y");
+    return transform_apply(P->plan, P->d32, y, DIN_FP32, z, DOUT_STORE, 0.f,
+                           static_cast<cudaStream_t>(stream));
+}
+
+ar_status ar_symprec_eigenvalues(const ar_prec* P, double* lambda_host, double* d_host) {
+    if (!P) return fail(AR_ERR_INVALID_ARG, "null preconditioner");
+    if (!P->lam64 || !P->d64) return fail(AR_ERR_INVALID_ARG, "float64 eigenvalues not kept");
+    const size_t nb = (size_t)P->n1 * P->n2 * sizeof(double);
+    if (lambda_host) AR_CUDA(cudaMemcpy(lambda_host, P->lam64, nb, cudaMemcpyDeviceToHost));
+    if (d_host) AR_CUDA(cudaMemcpy(d_host, P->d64, nb, cudaMemcpyDeviceToHost));
+    return AR_OK;
+}
+
+ar_status ar_symprec_shape(const ar_prec* P, int* n1, int* n2) {
+    if (!P) return fail(AR_ERR_INVALID_ARG, "null preconditioner");
+    if (n1) *n1 = P->n1;
+    if (n2) *n2 = P->n2;
+    return AR_OK;
+}
+
+void ar_symprec_destroy(ar_prec* P) {
+    if (!P) return;
+    cudaDeviceSynchronize();
+    transform_plan_destroy(P->plan);
+    cudaFree(P->lam64);
+    cudaFree(P->d64);
+    cudaFree(P->d32);
+    delete P;
+}
+
+ar_status ar_restore(const float* g, const double* psf_host, int n1, int n2, int q1, int q2,
+                     double alpha, double tau, int iters, int precondition, const float* x0,
+                     const float* f_true, float* x_out, double* rre_trace, int* best_iter,
+                     void* stream) {
+    if (!g || !psf_host || !x_out) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
+    const bool pc = precondition != 0;
+    AR_TRY(check_image_sizes(n1, n2, pc ? 3 : 1));
+    AR_TRY(check_support(n1, n2, q1, q2, pc ? 3 : 1));
+    if (iters < 0) return fail(AR_ERR_INVALID_ARG, "iters must be >= 0 (got %d)", iters);
+    if (!(tau > 0.0) || !std::isfinite(tau))
+        return fail(AR_ERR_INVALID_ARG, "tau must be finite and > 0 (got %g)", tau);
+    if (pc && (!(alpha > 0.0) || !std::isfinite(alpha)))
+        return fail(AR_ERR_INVALID_ARG, "alpha must be finite and > 0 (got %g)", alpha);
+    if ((rre_trace || best_iter) && !f_true)
+        return fail(AR_ERR_INVALID_ARG, "rre_trace/best_iter need f_true");
+    AR_TRY(check_psf_host(psf_host, q1, q2));
+    const size_t n = (size_t)n1 * n2;
+    const size_t nb = n * sizeof(float);
+    if (overlaps(x_out, nb, g, nb)) return fail(AR_ERR_ALIAS, "x_out overlaps g");
+    if (f_true && overlaps(x_out, nb, f_true, nb)) return fail(AR_ERR_ALIAS, "x_out overlaps f_true");
+    if (x0 && x0 != x_out && overlaps(x0, nb, x_out, nb))
+        return fail(AR_ERR_ALIAS, "x0 partially overlaps x_out");
+
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    set_pool_threshold_once();
+    const size_t k = (size_t)(2 * q1 + 1) * (2 * q2 + 1);
+    std::vector<float> h32(k);
+    for (size_t i = 0; i < k; ++i) h32[i] = (float)psf_host[i];
+
+    ar_prec* P = nullptr;
+    unsigned long long bad = 0;
+    std::vector<double> sums((size_t)iters + 1, 0.0);
+    ar_status st = AR_OK;
+    {
+        Scratch ws(s);
+        float *psf = nullptr, *r = nullptr, *z = nullptr;
+        double* dsum = nullptr;
+        unsigned long long* dbad = nullptr;
+        st = ws.get(&psf, k);
+        if (st == AR_OK) st = ws.get(&r, n);
+        if (st == AR_OK && pc) st = ws.get(&z, n);
+        if (st == AR_OK) st = ws.get(&dsum, (size_t)iters + 1);
+        if (st == AR_OK) st = ws.get(&dbad, 1);
+        if (st == AR_OK) {
+            cudaError_t e = cudaMemcpyAsync(psf, h32.data(), k * sizeof(float),
+                                            cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(dsum, 0, ((size_t)iters + 1) * sizeof(double), s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(dbad, 0, sizeof(unsigned long long), s);
+            if (e == cudaSuccess) {
+                if (!x0) e = cudaMemsetAsync(x_out, 0, nb, s);
+                else if (x0 != x_out) e = cudaMemcpyAsync(x_out, x0, nb, cudaMemcpyDeviceToDevice, s);
+            }
+            if (e != cudaSuccess) st = cuda_fail(e, "restore initialisation");
+        }
+        if (st == AR_OK && pc) st = prec_build(psf_host, q1, q2, n1, n2, alpha, s, false, &P);
+        if (st == AR_OK && f_true) st = reduce_sq(f_true, n, dsum + iters, s);
+
+        ConvArgs blur{};
+        blur.x = x_out;
+        blur.out = r;
+        blur.aux = g;
+        blur.psf = psf;
+        blur.n1 = n1;
+        blur.n2 = n2;
+        blur.q1 = q1;
+        blur.q2 = q2;
+        blur.flip = 0;
+        blur.mode = CONV_RESIDUAL;
+        ConvArgs reblur = blur;
+        reblur.x = r;
+        reblur.aux = nullptr;
+        reblur.flip = 1;
+        if (pc) {
+            reblur.out = z;
+            reblur.mode = CONV_STORE;
+        } else {
+            reblur.out = x_out;
+            reblur.mode = CONV_AXPY;
+            reblur.tau = (float)tau;
+        }
+        for (int it = 0; st == AR_OK && it < iters; ++it) {
+            st = conv_launch(blur, s);                           // r = g - A x_k
+            if (st == AR_OK) st = conv_launch(reblur, s);        // z = A' r  (or x += tau A' r)
+            if (st == AR_OK && pc)                               // x += tau D z
+                st = transform_apply(P->plan, P->d32, z, DIN_FP32, x_out, DOUT_AXPY, (float)tau, s);
+            if (st == AR_OK && f_true) st = reduce_diff_sq(x_out, f_true, n, dsum + it, s);
+        }
+        if (st == AR_OK) st = count_nonfinite(x_out, n, dbad, s);
+        if (st == AR_OK) {
+            cudaError_t e = cudaMemcpyAsync(sums.data(), dsum, sums.size() * sizeof(double),
+                                            cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, dbad, sizeof(bad), cudaMemcpyDeviceToHost, s);
+            if (e != cudaSuccess) st = cuda_fail(e, "restore readback");
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (P) ar_symprec_destroy(P);
+    if (st != AR_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "restore");
+    if (f_true) {
+        const double fn = sums[(size_t)iters];
+        int best = 0;
+        double bestv = 0.0;
+        for (int it = 0; it < iters; ++it) {
+            const double v = std::sqrt(sums[(size_t)it] / fn);
+            if (rre_trace) rre_trace[it] = v;
+            if (best == 0 || v < bestv) {
+                best = it + 1;
+                bestv = v;
+            }
+        }
+        if (best_iter) *best_iter = best;
+    }
+    if (bad) return fail(AR_ERR_NONFINITE, "%llu non-finite entries in the final iterate", bad);
+    return AR_OK;
+}
+
+}  // extern "C"

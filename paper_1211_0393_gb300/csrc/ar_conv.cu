@@ -1,0 +1,207 @@
+// Fused anti-reflective extension + 2D convolution (y = A_n x and y = A' x).
+//
+// A_n x is the convolution g_i = sum_s h_s xt_{i-s} (eq. modello_discreto) of
+// the image extended by the anti-reflective rules of Section 2.2: along each
+// axis xt_{-i} = 2 x_0 - x_i and xt_{n-1+i} = 2 x_{n-1} - x_{n-1-i}; applying
+// the row rule and then the column rule gives the double anti-reflection
+// 4 x_c - 2 x - 2 x + x at the corners.  A' (Section 4, reblurring) is the same
+// operator with the PSF rotated by 180 degrees.
+//
+// The extension is never materialised: every CTA builds its halo tile in
+// shared memory, evaluating out-of-image samples from in-image ones as it
+// loads them.  Each thread then computes a vertical strip of R outputs of one
+// column, sliding a register window down the tile: per PSF column it loads
+// R + 2Q values from shared memory (consecutive lanes read consecutive
+// columns: conflict-free) and issues R (2Q+1) FMAs against broadcast PSF
+// coefficients.  The kernel is FP32-FMA bound for Q >= 2.
+
+#include "ar_internal.cuh"
+
+#include <cuda_bf16.h>
+
+namespace ar {
+namespace {
+
+constexpr int TX = 64;   // tile columns, one per thread
+constexpr int TY = 4;    // row strips per CTA
+constexpr int RS = 16;   // rows per strip
+constexpr int TH = TY * RS;
+constexpr int QMAX_FAST = 15;
+
+// Sample of the anti-reflectively extended image at (j1, j2) (0-based; may
+// lie outside the image by up to q).  Outside the extended domain the value
+// only feeds outputs that are never stored, so 0 is returned without reading.
+__device__ __forceinline__ float ext_value(const float* __restrict__ x, int n1, int n2,
+                                           int q1, int q2, int j1, int j2) {
+    if (j1 < -q1 || j1 >= n1 + q1 || j2 < -q2 || j2 >= n2 + q2) return 0.f;
+    const bool r_in = (j1 >= 0 && j1 < n1);
+    const bool c_in = (j2 >= 0 && j2 < n2);
+    // row terms: edge row re (weight 2) and mirror row rm (weight -1)
+    const int re = j1 < 0 ? 0 : n1 - 1;
+    const int rm = j1 < 0 ? -j1 : 2 * (n1 - 1) - j1;
+    const int ce = j2 < 0 ? 0 : n2 - 1;
+    const int cm = j2 < 0 ? -j2 : 2 * (n2 - 1) - j2;
+    if (r_in && c_in) return __ldg(x + (size_t)j1 * n2 + j2);
+    if (c_in) {  // top/bottom border: rows are extended first
+        return 2.f * __ldg(x + (size_t)re * n2 + j2) - __ldg(x + (size_t)rm * n2 + j2);
+    }
+    if (r_in) {  // left/right border
+        const float* row = x + (size_t)j1 * n2;
+        return 2.f * __ldg(row + ce) - __ldg(row + cm);
+    }
+    // corner: extend the two rows re, rm along the columns, then combine them
+    const float* xe = x + (size_t)re * n2;
+    const float* xm = x + (size_t)rm * n2;
+    const float ve = 2.f * __ldg(xe + ce) - __ldg(xe + cm);
+    const float vm = 2.f * __ldg(xm + ce) - __ldg(xm + cm);
+    return 2.f * ve - vm;
+}
+
+__device__ __forceinline__ void split3_store(uint16_t* planes, size_t pstride, size_t off, float v) {
+    const __nv_bfloat16 p0 = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(p0);
+    const __nv_bfloat16 p1 = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(p1);
+    const __nv_bfloat16 p2 = __float2bfloat16_rn(r2);
+    planes[off] = __bfloat16_as_ushort(p0);
+    planes[pstride + off] = __bfloat16_as_ushort(p1);
+    planes[2 * pstride + off] = __bfloat16_as_ushort(p2);
+}
+
+__device__ __forceinline__ void conv_epilogue(const ConvArgs& a, int row, int col, float v) {
+    const size_t o = (size_t)row * a.n2 + col;
+    switch (a.mode) {
+        case CONV_STORE: a.out[o] = v; break;
+        case CONV_RESIDUAL: a.out[o] = __ldg(a.aux + o) - v; break;
+        case CONV_AXPY: a.out[o] = fmaf(a.tau, v, a.out[o]); break;
+        default: split3_store(a.planes, a.plane_stride, (size_t)row * a.ld + col, v); break;
+    }
+}
+
+// Fast path: support padded to Q x Q (Q = max(q1, q2) <= 15, zero taps outside
+// the true support), tile TH x TX, R = RS rows per thread.
+template <int Q>
+__global__ void __launch_bounds__(TX * TY)
+conv_fast_kernel(const ConvArgs a) {
+    constexpr int W = TX + 2 * Q;        // tile row length
+    constexpr int H = TH + 2 * Q;        // tile rows
+    constexpr int K = 2 * Q + 1;
+    __shared__ float tile[H * W];
+    __shared__ float coef[K * K];        // coef[b * K + a] = h_{a-Q, b-Q} (flipped for A')
+
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    const int r0 = blockIdx.y * TH;
+    const int c0 = blockIdx.x * TX;
+    const int kw = 2 * a.q2 + 1;
+
+    for (int i = tid; i < K * K; i += TX * TY) {
+        const int b = i / K, aa = i % K;
+        const int s1 = aa - Q, s2 = b - Q;      // tap offsets in the padded support
+        float v = 0.f;
+        if (s1 >= -a.q1 && s1 <= a.q1 && s2 >= -a.q2 && s2 <= a.q2) {
+            const int t1 = a.flip ? -s1 : s1, t2 = a.flip ? -s2 : s2;
+            v = __ldg(a.psf + (t1 + a.q1) * kw + (t2 + a.q2));
+        }
+        coef[i] = v;
+    }
+    for (int i = tid; i < H * W; i += TX * TY) {
+        const int r = i / W, c = i % W;
+        tile[i] = ext_value(a.x, a.n1, a.n2, a.q1, a.q2, r0 - Q + r, c0 - Q + c);
+    }
+    __syncthreads();
+
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    float acc[RS];
+#pragma unroll
+    for (int r = 0; r < RS; ++r) acc[r] = 0.f;
+
+#pragma unroll 1
+    for (int b = 0; b < K; ++b) {
+        // output column tx reads tile column tx - s2 + Q = tx + 2Q - b
+        const float* col = tile + (ty * RS) * W + tx + 2 * Q - b;
+        float win[RS + 2 * Q];
+#pragma unroll
+        for (int t = 0; t < RS + 2 * Q; ++t) win[t] = col[t * W];
+        const float* cb = coef + b * K;
+#pragma unroll
+        for (int aa = 0; aa < K; ++aa) {
+            const float hv = cb[aa];
+            // output row r reads tile row r - s1 + Q = r + 2Q - aa (strip-relative)
+#pragma unroll
+            for (int r = 0; r < RS; ++r) acc[r] = fmaf(hv, win[r + 2 * Q - aa], acc[r]);
+        }
+    }
+
+    const int col = c0 + tx;
+    if (col < a.n2) {
+#pragma unroll
+        for (int r = 0; r < RS; ++r) {
+            const int row = r0 + ty * RS + r;
+            if (row < a.n1) conv_epilogue(a, row, col, acc[r]);
+        }
+    }
+}
+
+// Generic path for large supports: one output per thread, taps read straight
+// from the (L2-resident) input through the virtual extension.
+__global__ void __launch_bounds__(256)
+conv_generic_kernel(const ConvArgs a) {
+    const int col = blockIdx.x * 32 + threadIdx.x;
+    const int row = blockIdx.y * 8 + threadIdx.y;
+    if (row >= a.n1 || col >= a.n2) return;
+    const int kw = 2 * a.q2 + 1;
+    float acc = 0.f;
+    for (int s2 = -a.q2; s2 <= a.q2; ++s2) {
+        for (int s1 = -a.q1; s1 <= a.q1; ++s1) {
+            const int t1 = a.flip ? -s1 : s1, t2 = a.flip ? -s2 : s2;
+            const float hv = __ldg(a.psf + (t1 + a.q1) * kw + (t2 + a.q2));
+            acc = fmaf(hv, ext_value(a.x, a.n1, a.n2, a.q1, a.q2, row - s1, col - s2), acc);
+        }
+    }
+    conv_epilogue(a, row, col, acc);
+}
+
+template <int Q>
+cudaError_t launch_fast(const ConvArgs& a, cudaStream_t s) {
+    dim3 grid((a.n2 + TX - 1) / TX, (a.n1 + TH - 1) / TH);
+    conv_fast_kernel<Q><<<grid, dim3(TX, TY), 0, s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+ar_status conv_launch(const ConvArgs& a, cudaStream_t s) {
+    if (a.n1 <= 0 || a.n2 <= 0) return AR_OK;
+    const int q = a.q1 > a.q2 ? a.q1 : a.q2;
+    cudaError_t e;
+    switch (q) {
+        case 0: e = launch_fast<0>(a, s); break;
+        case 1: e = launch_fast<1>(a, s); break;
+        case 2: e = launch_fast<2>(a, s); break;
+        case 3: e = launch_fast<3>(a, s); break;
+        case 4: e = launch_fast<4>(a, s); break;
+        case 5: e = launch_fast<5>(a, s); break;
+        case 6: e = launch_fast<6>(a, s); break;
+        case 7: e = launch_fast<7>(a, s); break;
+        case 8: e = launch_fast<8>(a, s); break;
+        case 9: e = launch_fast<9>(a, s); break;
+        case 10: e = launch_fast<10>(a, s); break;
+        case 11: e = launch_fast<11>(a, s); break;
+        case 12: e = launch_fast<12>(a, s); break;
+        case 13: e = launch_fast<13>(a, s); break;
+        case 14: e = launch_fast<14>(a, s); break;
+        case 15: e = launch_fast<15>(a, s); break;
+        default: {
+            dim3 grid((a.n2 + 31) / 32, (a.n1 + 7) / 8);
+            conv_generic_kernel<<<grid, dim3(32, 8), 0, s>>>(a);
+            count_launch();
+            e = cudaGetLastError();
+        }
+    }
+    static_assert(QMAX_FAST == 15, "dispatch table covers 0..15");
+    if (e != cudaSuccess) return cuda_fail(e, "conv kernel launch");
+    return AR_OK;
+}
+
+}  // namespace ar

@@ -1,0 +1,115 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/ar.h"
+
+namespace ar {
+
+// ---------------------------------------------------------------- errors ---
+// Records a human-readable detail for ar_last_error_detail() and returns s.
+ar_status fail(ar_status s, const char* fmt, ...);
+ar_status cuda_fail(cudaError_t e, const char* what);
+
+#define AR_CUDA(call)                                                         \
+    do {                                                                      \
+        cudaError_t _e = (call);                                              \
+        if (_e != cudaSuccess) return ::ar::cuda_fail(_e, #call);             \
+    } while (0)
+
+#define AR_TRY(call)                                                          \
+    do {                                                                      \
+        ar_status _s = (call);                                                \
+        if (_s != AR_OK) return _s;                                           \
+    } while (0)
+
+// ------------------------------------------------------------- stencils ---
+// Epilogue of the fused AR pad + convolution kernel.
+enum ConvMode : int {
+    CONV_STORE = 0,      // out = A x
+    CONV_RESIDUAL = 1,   // out = g - A x            (aux = g)
+    CONV_AXPY = 2,       // out += tau * A x         (out read-modify-write)
+    CONV_SPLIT3 = 3      // out planes = bf16x3 split of A x (transform operand)
+};
+
+struct ConvArgs {
+    const float* x;      // input image n1 x n2
+    float* out;          // output image (CONV_STORE/RESIDUAL/AXPY)
+    const float* aux;    // g for CONV_RESIDUAL
+    uint16_t* planes;    // CONV_SPLIT3: 3 bf16 planes, plane stride plane_stride, row pitch ld
+    size_t plane_stride;
+    int ld;
+    const float* psf;    // device PSF (2q1+1) x (2q2+1)
+    int n1, n2, q1, q2;
+    int flip;            // 1: use h_{-s} (reblur A')
+    int mode;
+    float tau;
+};
+
+// Launches the AR stencil on `stream` (validated arguments).
+ar_status conv_launch(const ConvArgs& a, cudaStream_t stream);
+
+// ------------------------------------------------------------ transform ---
+// The AR transform pair for one image size, applied as four dense
+// contractions.  Implemented in ar_transform.cu.
+struct TransformPlan;
+
+ar_status transform_plan_create(int n1, int n2, cudaStream_t stream, TransformPlan** out);
+void transform_plan_destroy(TransformPlan* p);
+
+// Where the input of D comes from.
+enum DInput : int {
+    DIN_FP32 = 0,        // y is a float32 image (ar_symprec_solve)
+    DIN_SPLIT = 1        // the operand planes were already written by the stencil
+};
+
+// Final epilogue of D.
+enum DOutput : int {
+    DOUT_STORE = 0,      // z = D y
+    DOUT_AXPY = 1        // x += tau * D y
+};
+
+// Pointer to the operand planes the stencil must fill for DIN_SPLIT.
+uint16_t* transform_input_planes(TransformPlan* p, size_t* plane_stride, int* ld);
+
+ar_status transform_apply(TransformPlan* p, const float* d32, const float* y, DInput din,
+                          float* out, DOutput dout, float tau, cudaStream_t stream);
+
+// Number of kernels one transform_apply launches (for launch accounting).
+int transform_launches(const TransformPlan* p, DInput din);
+
+// ---------------------------------------------------------------- setup ---
+// FP64 eigenvalue setup on the GPU: symmetrize (eq. simmetrizzata2d), symbol
+// on the AR grid (eq. funzione_generatrice, Theorem 2), Tikhonov (eq. TikFilter).
+ar_status setup_eigen(const double* psf_dev64, int q1, int q2, int n1, int n2, double alpha,
+                      double* lam64, double* d64, float* d32, double* scratch_dev,
+                      cudaStream_t stream);
+size_t setup_scratch_doubles(int q1, int q2, int n1, int n2);
+
+// ------------------------------------------------------------- reductions ---
+// acc[0] += sum (x - f)^2, both n floats, float64 accumulation.
+ar_status reduce_diff_sq(const float* x, const float* f, size_t n, double* acc, cudaStream_t s);
+// acc[0] += sum f^2.
+ar_status reduce_sq(const float* f, size_t n, double* acc, cudaStream_t s);
+// cnt[0] += number of non-finite entries of x.
+ar_status count_nonfinite(const float* x, size_t n, unsigned long long* cnt, cudaStream_t s);
+
+int sm_count();
+
+// Launch accounting: every kernel launch site calls count_launch(k).
+void count_launch(unsigned k = 1);
+
+}  // namespace ar
+
+struct ar_prec {
+    int n1, n2, q1, q2;
+    double alpha;
+    int device;
+    double* lam64;
+    double* d64;
+    float* d32;
+    ar::TransformPlan* plan;
+};

@@ -1,0 +1,101 @@
+// FP64 eigenvalue setup of the optimal AR preconditioner, on the GPU.
+//
+//  S0  s = symmetrized PSF (eq. simmetrizzata2d, Theorem 4):
+//        s_{+-i1,+-i2} = (h_{-i1,-i2} + h_{-i1,i2} + h_{i1,-i2} + h_{i1,i2}) / 4
+//  S1  lambda[i1,i2] = f_s(x1_{i1}, x2_{i2}), the generating function of eq.
+//      funzione_generatrice, on the grid of Theorem 2 in T_n's column order:
+//      x_k = 0 for k = 0 and k = m-1 (the anti-reflection centres) and
+//      x_k = k pi/(m-1) for k = 1..m-2 (the tau grid of Q_{m-2}).
+//      f is separable, f = sum_a cos(a x1) t_a(x2) with
+//      t_a(x2) = w_a (s_{a,0} + 2 sum_{b>=1} s_{a,b} cos(b x2)), w_0 = 1, w_a = 2,
+//      which regroups the four sums of the equation.
+//  S2  d = 1/(lambda^2 + alpha), eq. TikFilter.
+//
+// All arithmetic is float64.  Cosines take an exactly reduced argument,
+// cos(a k pi/(m-1)) = cospi(((a k) mod 2(m-1)) / (m-1)).
+
+#include "ar_internal.cuh"
+
+namespace ar {
+namespace {
+
+__device__ __forceinline__ double grid_cos(int a, int k, int m) {
+    // cos(a * x_k) on the AR grid of size m
+    if (k == 0 || k == m - 1) return 1.0;
+    const long long per = 2LL * (m - 1);
+    const long long r = ((long long)a * k) % per;
+    return cospi((double)r / (double)(m - 1));
+}
+
+// scratch layout: s[(q1+1)*(q2+1)] | t[(q1+1) * n2] | c1[(q1+1) * n1]
+__global__ void symmetrize_kernel(const double* __restrict__ h, int q1, int q2, double* s) {
+    const int kw = 2 * q2 + 1;
+    for (int i = threadIdx.x; i < (q1 + 1) * (q2 + 1); i += blockDim.x) {
+        const int a = i / (q2 + 1), b = i % (q2 + 1);
+        const double v = h[(q1 - a) * kw + (q2 - b)] + h[(q1 - a) * kw + (q2 + b)]
+                       + h[(q1 + a) * kw + (q2 - b)] + h[(q1 + a) * kw + (q2 + b)];
+        s[i] = 0.25 * v;
+    }
+}
+
+// t[a][j] = w_a (s_{a,0} + 2 sum_{b>=1} s_{a,b} cos(b x2_j)),  c1[a][i] = cos(a x1_i)
+__global__ void symbol_tables_kernel(const double* __restrict__ s, int q1, int q2, int n1, int n2,
+                                     double* __restrict__ t, double* __restrict__ c1) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nt = (q1 + 1) * n2;
+    if (idx < nt) {
+        const int a = idx / n2, j = idx % n2;
+        double acc = 0.0;
+        for (int b = q2; b >= 1; --b) acc += s[a * (q2 + 1) + b] * grid_cos(b, j, n2);
+        acc = s[a * (q2 + 1)] + 2.0 * acc;
+        t[idx] = (a == 0 ? 1.0 : 2.0) * acc;
+    } else if (idx < nt + (q1 + 1) * n1) {
+        const int k = idx - nt;
+        const int a = k / n1, i = k % n1;
+        c1[k] = grid_cos(a, i, n1);
+    }
+}
+
+__global__ void eigen_kernel(const double* __restrict__ t, const double* __restrict__ c1,
+                             int q1, int n1, int n2, double alpha,
+                             double* __restrict__ lam64, double* __restrict__ d64,
+                             float* __restrict__ d32) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)n1 * n2) return;
+    const int i = (int)(idx / n2), j = (int)(idx % n2);
+    double lam = 0.0;
+    for (int a = q1; a >= 0; --a) lam += c1[(size_t)a * n1 + i] * t[(size_t)a * n2 + j];
+    const double d = 1.0 / (lam * lam + alpha);
+    if (lam64) lam64[idx] = lam;
+    if (d64) d64[idx] = d;
+    d32[idx] = (float)d;
+}
+
+}  // namespace
+
+size_t setup_scratch_doubles(int q1, int q2, int n1, int n2) {
+    return (size_t)(q1 + 1) * (q2 + 1) + (size_t)(q1 + 1) * n2 + (size_t)(q1 + 1) * n1;
+}
+
+ar_status setup_eigen(const double* psf_dev64, int q1, int q2, int n1, int n2, double alpha,
+                      double* lam64, double* d64, float* d32, double* scratch,
+                      cudaStream_t stream) {
+    double* s = scratch;
+    double* t = s + (size_t)(q1 + 1) * (q2 + 1);
+    double* c1 = t + (size_t)(q1 + 1) * n2;
+    symmetrize_kernel<<<1, 256, 0, stream>>>(psf_dev64, q1, q2, s);
+    count_launch();
+    AR_CUDA(cudaGetLastError());
+    const int ntab = (q1 + 1) * (n2 + n1);
+    symbol_tables_kernel<<<(ntab + 255) / 256, 256, 0, stream>>>(s, q1, q2, n1, n2, t, c1);
+    count_launch();
+    AR_CUDA(cudaGetLastError());
+    const size_t n = (size_t)n1 * n2;
+    eigen_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(t, c1, q1, n1, n2, alpha,
+                                                                  lam64, d64, d32);
+    count_launch();
+    AR_CUDA(cudaGetLastError());
+    return AR_OK;
+}
+
+}  // namespace ar
