@@ -5,9 +5,12 @@ Tolerances (derived from the arithmetic; see the design notes):
   rel-L2 <= 2e-6 and max |err| <= 1e-5 max|y|.
 * setup (float64 on both sides): |d_gpu - d| <= 1e-12 d.
 * preconditioner and restoration (float32 data, transforms with float32-
-  grade accuracy): the float32 rounding of the transform input is amplified by
-  at most max(d)/min(d) ~ 1/alpha, so rel-L2 <= tol(alpha) =
-  max(1e-5, 1e-7/alpha) per iterate, which is 1e-5 for every alpha >= 0.01.
+  grade accuracy): three float32 roundings reach the spectral coefficients
+  before the filter (the stored transform input, the contraction output, the
+  scaling), each of relative size <= u = 2^-24, and the filter d of eq.
+  TikFilter amplifies them by up to max(d) = 1/alpha against the d ~ 1 signal
+  band, so rel-L2 <= tol(alpha) = max(1e-5, 3 u / alpha) per iterate: 1e-5 for
+  alpha >= 0.018, 1.8e-5 at alpha = 0.01.
 """
 
 import numpy as np
@@ -34,8 +37,11 @@ def rel_l2(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
 
 
+U32 = 2.0 ** -24
+
+
 def tol_alpha(alpha):
-    return max(1e-5, 1e-7 / alpha)
+    return max(1e-5, 3 * U32 / alpha)
 
 
 def dev(a):
