@@ -304,16 +304,16 @@ ar_status ar_restore(const float* g, const double* psf_host, int n1, int n2, int
 
     ar_prec* P = nullptr;
     unsigned long long bad = 0;
+    int timeout = 0;
     std::vector<double> sums((size_t)iters + 1, 0.0);
     ar_status st = AR_OK;
     {
         Scratch ws(s);
-        float *psf = nullptr, *r = nullptr, *z = nullptr;
+        float *psf = nullptr, *r = nullptr;
         double* dsum = nullptr;
         unsigned long long* dbad = nullptr;
         st = ws.get(&psf, k);
         if (st == AR_OK) st = ws.get(&r, n);
-        if (st == AR_OK && pc) st = ws.get(&z, n);
         if (st == AR_OK) st = ws.get(&dsum, (size_t)iters + 1);
         if (st == AR_OK) st = ws.get(&dbad, 1);
         if (st == AR_OK) {
@@ -345,9 +345,11 @@ ar_status ar_restore(const float* g, const double* psf_host, int n1, int n2, int
         reblur.x = r;
         reblur.aux = nullptr;
         reblur.flip = 1;
-        if (pc) {
-            reblur.out = z;
-            reblur.mode = CONV_STORE;
+        if (pc && st == AR_OK) {
+            // A' r is written straight into the transform's bf16x3 operand planes
+            reblur.out = nullptr;
+            reblur.mode = CONV_SPLIT3;
+            reblur.planes = transform_input_planes(P->plan, &reblur.plane_stride, &reblur.ld);
         } else {
             reblur.out = x_out;
             reblur.mode = CONV_AXPY;
@@ -357,7 +359,8 @@ ar_status ar_restore(const float* g, const double* psf_host, int n1, int n2, int
             st = conv_launch(blur, s);                           // r = g - A x_k
             if (st == AR_OK) st = conv_launch(reblur, s);        // z = A' r  (or x += tau A' r)
             if (st == AR_OK && pc)                               // x += tau D z
-                st = transform_apply(P->plan, P->d32, z, DIN_FP32, x_out, DOUT_AXPY, (float)tau, s);
+                st = transform_apply(P->plan, P->d32, nullptr, DIN_SPLIT, x_out, DOUT_AXPY,
+                                     (float)tau, s);
             if (st == AR_OK && f_true) st = reduce_diff_sq(x_out, f_true, n, dsum + it, s);
         }
         if (st == AR_OK) st = count_nonfinite(x_out, n, dbad, s);
@@ -365,6 +368,9 @@ ar_status ar_restore(const float* g, const double* psf_host, int n1, int n2, int
             cudaError_t e = cudaMemcpyAsync(sums.data(), dsum, sums.size() * sizeof(double),
                                             cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, dbad, sizeof(bad), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess && P)
+                e = cudaMemcpyAsync(&timeout, transform_error_flag(P->plan), sizeof(int),
+                                    cudaMemcpyDeviceToHost, s);
             if (e != cudaSuccess) st = cuda_fail(e, "restore readback");
         }
     }
@@ -386,6 +392,7 @@ ar_status ar_restore(const float* g, const double* psf_host, int n1, int n2, int
         }
         if (best_iter) *best_iter = best;
     }
+    if (timeout) return fail(AR_ERR_TIMEOUT, "a tensor-core contraction gave up waiting");
     if (bad) return fail(AR_ERR_NONFINITE, "%llu non-finite entries in the final iterate", bad);
     return AR_OK;
 }

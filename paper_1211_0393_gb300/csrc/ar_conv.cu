@@ -7,9 +7,10 @@
 // 4 x_c - 2 x - 2 x + x at the corners.  A' (Section 4, reblurring) is the same
 // operator with the PSF rotated by 180 degrees.
 //
-// The extension is never materialised: every CTA builds its halo tile in
-// shared memory, evaluating out-of-image samples from in-image ones as it
-// loads them.  Each thread then computes a vertical strip of R outputs of one
+// The extension is never materialised: every CTA loads its halo tile into
+// shared memory (all loads of a thread in flight at once) and, on tiles that
+// reach past the image, overwrites the out-of-image samples with their
+// anti-reflections computed from in-tile samples.  Each thread then computes a vertical strip of R outputs of one
 // column, sliding a register window down the tile: per PSF column it loads
 // R + 2Q values from shared memory (consecutive lanes read consecutive
 // columns: conflict-free) and issues R (2Q+1) FMAs against broadcast PSF
@@ -104,11 +105,57 @@ conv_fast_kernel(const ConvArgs a) {
         }
         coef[i] = v;
     }
-    for (int i = tid; i < H * W; i += TX * TY) {
-        const int r = i / W, c = i % W;
-        tile[i] = ext_value(a.x, a.n1, a.n2, a.q1, a.q2, r0 - Q + r, c0 - Q + c);
+    // Phase 1: every tile sample at its coordinate clamped into the image.
+    // All loads of a thread are issued before the first shared-memory store.
+    constexpr int NLD = (H * W + TX * TY - 1) / (TX * TY);
+    {
+        float v[NLD];
+#pragma unroll
+        for (int k = 0; k < NLD; ++k) {
+            const int i = tid + k * TX * TY;
+            v[k] = 0.f;
+            if (i < H * W) {
+                const int r = i / W, c = i % W;
+                const int j1 = min(max(r0 - Q + r, 0), a.n1 - 1);
+                const int j2 = min(max(c0 - Q + c, 0), a.n2 - 1);
+                v[k] = __ldg(a.x + (size_t)j1 * a.n2 + j2);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NLD; ++k) {
+            const int i = tid + k * TX * TY;
+            if (i < H * W) tile[i] = v[k];
+        }
     }
     __syncthreads();
+    // Phase 2 (tiles that reach past the image only): the anti-reflected
+    // samples, rows first (Section 2.2 border rule on in-image columns), then
+    // columns on every row, which yields the corner rule.  Edge and mirror
+    // samples always lie inside the tile.
+    if (r0 - Q < 0 || r0 + TH + Q > a.n1 || c0 - Q < 0 || c0 + TX + Q > a.n2) {
+        for (int i = tid; i < H * W; i += TX * TY) {
+            const int r = i / W, c = i % W;
+            const int j1 = r0 - Q + r, j2 = c0 - Q + c;
+            if (j2 < 0 || j2 >= a.n2) continue;
+            int re, rm;
+            if (j1 < 0 && j1 >= -a.q1) { re = 0; rm = -j1; }
+            else if (j1 >= a.n1 && j1 < a.n1 + a.q1) { re = a.n1 - 1; rm = 2 * (a.n1 - 1) - j1; }
+            else continue;
+            tile[i] = 2.f * tile[(re - (r0 - Q)) * W + c] - tile[(rm - (r0 - Q)) * W + c];
+        }
+        __syncthreads();
+        for (int i = tid; i < H * W; i += TX * TY) {
+            const int r = i / W, c = i % W;
+            const int j1 = r0 - Q + r, j2 = c0 - Q + c;
+            if (j1 < -a.q1 || j1 >= a.n1 + a.q1) continue;
+            int ce, cm;
+            if (j2 < 0 && j2 >= -a.q2) { ce = 0; cm = -j2; }
+            else if (j2 >= a.n2 && j2 < a.n2 + a.q2) { ce = a.n2 - 1; cm = 2 * (a.n2 - 1) - j2; }
+            else continue;
+            tile[i] = 2.f * tile[r * W + (ce - (c0 - Q))] - tile[r * W + (cm - (c0 - Q))];
+        }
+        __syncthreads();
+    }
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     float acc[RS];

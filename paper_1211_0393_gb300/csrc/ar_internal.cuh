@@ -81,6 +81,9 @@ ar_status transform_apply(TransformPlan* p, const float* d32, const float* y, DI
 // Number of kernels one transform_apply launches (for launch accounting).
 int transform_launches(const TransformPlan* p, DInput din);
 
+// Device int set to 1 by a contraction kernel whose bounded wait gave up.
+int* transform_error_flag(TransformPlan* p);
+
 // ---------------------------------------------------------------- setup ---
 // FP64 eigenvalue setup on the GPU: symmetrize (eq. simmetrizzata2d), symbol
 // on the AR grid (eq. funzione_generatrice, Theorem 2), Tikhonov (eq. TikFilter).

@@ -1,4 +1,4 @@
-// The AR transform pair of Theorem 1 applied as dense contractions.
+// The AR transform pair of Theorem 1 applied as dense tensor-core contractions.
 //
 // D y = T_n diag(d) T~_n y with T_n = T_{n1} (x) T_{n2} becomes, for an image Y,
 //     D Y = T_{n1} ( d o (T~_{n1} Y T~_{n2}^T) ) T_{n2}^T,
@@ -6,26 +6,206 @@
 // alpha_m of Theorem 1 (it cancels between T and T~):
 //     T~'_m = [[1, 0, 0], [-Q p, Q, -Q J p], [0, 0, 1]]
 //     T'_m  = [[1, 0, 0], [  p,  Q,    J p], [0, 0, 1]]
-// with Q = Q_{m-2} of eq. Qn and p_j = 1 - j/(m-1).  Both are generated in
+// with Q = Q_{m-2} of eq. Qn and p_j = 1 - j/(m-1); they are generated in
 // float64 on the GPU.
 //
-// Every product is C = A B^T with both operands row-major ("K-major"), and is
-// stored transposed, so the chain needs no explicit transposes:
-//   G1: U^T  <- (Y  T~2^T)^T          A = Y   (n1 x n2),  B = T~2
-//   G2: W    <- d o (U^T T~1^T)^T     A = U^T (n2 x n1),  B = T~1
-//   G3: V^T  <- (W  T2^T)^T           A = W,              B = T2
-//   G4: out  <- (V^T T1^T)^T (or out += tau * ...)
-// This file holds the plan, the float64 matrix generator and a plain SIMT
-// float32 contraction.
+// Every product is C = A B^T with both operands K-major, stored transposed,
+// so the chain needs no explicit transposes:
+//   G1: U^T <- (Y T~2^T)^T        A = Y   (n1 x n2)   B = T~2
+//   G2: W   <- d o (U^T T~1^T)^T  A = U^T (n2 x n1)   B = T~1
+//   G3: V^T <- (W T2^T)^T         A = W               B = T2
+//   G4: out <- (V^T T1^T)^T       (or out += tau * ...)
+//
+// Precision: each operand x is split into three bfloat16 planes
+// x = x0 + x1 + x2 (x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1)),
+// and the six products a_i b_j with i + j <= 2 are accumulated in float32 in
+// tensor memory.  The dropped terms are below 2^-24 relative, so the
+// contraction is as accurate as a float32 one.
+//
+// Kernel: one 128 x 64 output tile per CTA (tcgen05.mma M = 128, N = 64,
+// K = 16), operands staged by TMA (one 3D box loads the three planes of a
+// 128-byte-swizzled K-major tile), a 3-stage mbarrier pipeline between a TMA
+// producer thread and an MMA issuer thread, the accumulator in TMEM, and an
+// epilogue in which each warp reads its 32 TMEM lanes and writes the tile
+// transposed (coalesced along the tile's M index) with the next step fused:
+// the bf16x3 split of the next operand, the filter d, or x += tau * result.
 
 #include "ar_internal.cuh"
+#include "ar_tc.cuh"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+
 #include <cstdlib>
+#include <mutex>
 #include <new>
 
 namespace ar {
 namespace {
+
+constexpr int BM = 128, BN = 64, BK = 64, STAGES = 3, PLANES = 3;
+constexpr uint32_t A_PLANE = BM * BK * 2;                 // 16 KiB
+constexpr uint32_t B_PLANE = BN * BK * 2;                 // 8 KiB
+constexpr uint32_t A_STAGE = PLANES * A_PLANE;
+constexpr uint32_t B_STAGE = PLANES * B_PLANE;
+constexpr uint32_t STAGE_BYTES = A_STAGE + B_STAGE;      // 72 KiB
+constexpr uint32_t CTRL_BYTES = 8 * (2 * STAGES + 1) + 16;
+constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + CTRL_BYTES + 1024;
+constexpr uint32_t TMEM_COLS = 64;
+
+// The six split products (a plane, b plane), smallest first.
+__constant__ int kPA[6] = {2, 1, 0, 1, 0, 0};
+__constant__ int kPB[6] = {0, 1, 2, 0, 1, 0};
+
+enum TcEpi : int { TE_SPLIT_T = 0, TE_SCALE_SPLIT_T = 1, TE_STORE_T = 2, TE_AXPY_T = 3 };
+
+struct TcEpiArgs {
+    int mode;
+    uint16_t* planes;      // split output: planes[p * pstride + col * ld + row]
+    size_t pstride;
+    int ld;
+    float* out;            // float32 output: out[col * ldo + row]
+    int ldo;
+    const float* d;        // filter: d[col * ldd + row]
+    int ldd;
+    float tau;
+};
+
+__device__ __forceinline__ void split3(float v, uint16_t& h0, uint16_t& h1, uint16_t& h2) {
+    const __nv_bfloat16 p0 = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(p0);
+    const __nv_bfloat16 p1 = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 p2 = __float2bfloat16_rn(r1 - __bfloat162float(p1));
+    h0 = __bfloat16_as_ushort(p0);
+    h1 = __bfloat16_as_ushort(p1);
+    h2 = __bfloat16_as_ushort(p2);
+}
+
+__global__ void __launch_bounds__(128, 1)
+tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   int M, int N, int K, const TcEpiArgs ep, int* err) {
+    using namespace tc;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;         // 128B-swizzled tiles need 1 KiB alignment
+    uint8_t* gbase = smem_raw + (base - raw);
+    const uint32_t bars = base + STAGES * STAGE_BYTES;
+    const uint32_t done_bar = bars + 8u * (2 * STAGES);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(gbase + STAGES * STAGE_BYTES + 8 * (2 * STAGES + 1));
+    volatile int* sflag = reinterpret_cast<volatile int*>(tslot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int nk = (K + BK - 1) / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(bars + 8u * s, 1);                 // full[s]: TMA bytes landed
+            mbar_init(bars + 8u * (STAGES + s), 1);      // empty[s]: MMAs reading it done
+        }
+        mbar_init(done_bar, 1);
+        *sflag = 0;
+        fence_mbar_init();
+        prefetch_tmap(&tmA);
+        prefetch_tmap(&tmB);
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(tslot), TMEM_COLS);
+        tmem_relinquish();
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0 && lane == 0) {
+        // ---- TMA producer
+        int issued = 0;
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % STAGES;
+            if (kb >= STAGES && !mbar_wait(bars + 8u * (STAGES + s), ((kb / STAGES) & 1) ^ 1)) {
+                *sflag = 1;
+                break;
+            }
+            if (*sflag) break;
+            const uint32_t a = base + s * STAGE_BYTES;
+            mbar_arrive_expect_tx(bars + 8u * s, STAGE_BYTES);
+            tma_load_3d(a, &tmA, kb * BK, m0, 0, bars + 8u * s);
+            tma_load_3d(a + A_STAGE, &tmB, kb * BK, n0, 0, bars + 8u * s);
+            ++issued;
+        }
+        // no load may still be in flight when the CTA exits
+        for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
+            if (!mbar_wait(bars + 8u * (kb % STAGES), (kb / STAGES) & 1)) *sflag = 1;
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer
+        const uint32_t idesc = idesc_bf16_f32(BM, BN);
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % STAGES;
+            if (!mbar_wait(bars + 8u * s, (kb / STAGES) & 1)) {
+                *sflag = 1;
+                break;
+            }
+            fence_after_sync();
+            const uint32_t a = base + s * STAGE_BYTES;
+            const uint32_t b = a + A_STAGE;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+#pragma unroll
+                for (int t = 0; t < 6; ++t) {
+                    const uint64_t ad = desc_k_sw128(a + kPA[t] * A_PLANE + kk * 32);
+                    const uint64_t bd = desc_k_sw128(b + kPB[t] * B_PLANE + kk * 32);
+                    mma_bf16(tmem, ad, bd, idesc, (kb | kk | t) != 0 ? 1u : 0u);
+                }
+            }
+            mma_commit(bars + 8u * (STAGES + s));        // frees the stage when its MMAs finish
+        }
+        mma_commit(done_bar);                           // accumulator complete
+    }
+
+    // ---- epilogue: warp w owns TMEM lanes 32w..32w+31 = tile rows m0 + 32w + lane
+    const bool ready = mbar_wait(done_bar, 0);
+    __syncwarp();
+    fence_after_sync();
+    const bool write = ready && *sflag == 0;
+    const int row = m0 + warp * 32 + lane;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int c = 0; c < BN / 16; ++c) {
+        float v[16];
+        tmem_ld16(trow + c * 16, v);
+        if (!write || row >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int col = n0 + c * 16 + j;
+            if (col >= N) break;
+            float x = v[j];
+            if (ep.mode == TE_STORE_T) {
+                ep.out[(size_t)col * ep.ldo + row] = x;
+            } else if (ep.mode == TE_AXPY_T) {
+                float* o = ep.out + (size_t)col * ep.ldo + row;
+                *o = fmaf(ep.tau, x, *o);
+            } else {
+                if (ep.mode == TE_SCALE_SPLIT_T) x *= __ldg(ep.d + (size_t)col * ep.ldd + row);
+                uint16_t h0, h1, h2;
+                split3(x, h0, h1, h2);
+                const size_t o = (size_t)col * ep.ld + row;
+                ep.planes[o] = h0;
+                ep.planes[ep.pstride + o] = h1;
+                ep.planes[2 * ep.pstride + o] = h2;
+            }
+        }
+    }
+
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after_sync();
+        tmem_dealloc(tmem, TMEM_COLS);
+    }
+    if (threadIdx.x == 0 && (!ready || *sflag)) atomicExch(err, 1);
+}
 
 // ---------------------------------------------------------------- matrices --
 __device__ __forceinline__ double q_entry(int s, int t, int m) {
@@ -35,7 +215,7 @@ __device__ __forceinline__ double q_entry(int s, int t, int m) {
     return sqrt(2.0 / (double)(m - 1)) * sinpi((double)r / (double)(m - 1));
 }
 
-// qp[s] = (Q p)_s, qjp[s] = (Q J p)_s, s = 1..m-2 (index s-1), one block per row.
+// qp[s-1] = (Q p)_s, qjp[s-1] = (Q J p)_s, s = 1..m-2, one block per row.
 __global__ void boundary_columns_kernel(int m, double* qp, double* qjp) {
     const int s = blockIdx.x + 1;
     double a = 0.0, b = 0.0;
@@ -62,9 +242,19 @@ __global__ void boundary_columns_kernel(int m, double* qp, double* qjp) {
     }
 }
 
-// Fills T~'_m (analysis) and T'_m (synthesis) as float32 row-major m x m.
-__global__ void fill_transforms_f32_kernel(int m, const double* qp, const double* qjp,
-                                           float* Tt, float* T) {
+__device__ __forceinline__ void split3_f64(double v, uint16_t& h0, uint16_t& h1, uint16_t& h2) {
+    const __nv_bfloat16 p0 = __double2bfloat16(v);
+    const double r1 = v - (double)__bfloat162float(p0);
+    const __nv_bfloat16 p1 = __double2bfloat16(r1);
+    const __nv_bfloat16 p2 = __double2bfloat16(r1 - (double)__bfloat162float(p1));
+    h0 = __bfloat16_as_ushort(p0);
+    h1 = __bfloat16_as_ushort(p1);
+    h2 = __bfloat16_as_ushort(p2);
+}
+
+// T~'_m (analysis) and T'_m (synthesis) as bf16x3 planes, row pitch ld.
+__global__ void fill_transforms_kernel(int m, int ld, const double* qp, const double* qjp,
+                                       uint16_t* Tt, uint16_t* T) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)m * m) return;
     const int s = (int)(idx / m), t = (int)(idx % m);
@@ -80,92 +270,113 @@ __global__ void fill_transforms_f32_kernel(int m, const double* qp, const double
     } else {
         vt = v = q_entry(s, t, m);
     }
-    Tt[idx] = (float)vt;
-    T[idx] = (float)v;
+    const size_t ps = (size_t)m * ld, o = (size_t)s * ld + t;
+    uint16_t a0, a1, a2;
+    split3_f64(vt, a0, a1, a2);
+    Tt[o] = a0;
+    Tt[ps + o] = a1;
+    Tt[2 * ps + o] = a2;
+    split3_f64(v, a0, a1, a2);
+    T[o] = a0;
+    T[ps + o] = a1;
+    T[2 * ps + o] = a2;
 }
 
-// ----------------------------------------------------- SIMT contraction --
-enum Epi : int { EPI_T = 0, EPI_T_SCALE = 1, EPI_T_AXPY = 2 };
-
-constexpr int BM = 64, BN = 64, BK = 16;
-
-// C(i, j) = sum_k A[i, k] B[j, k]; stored transposed at out[j * ldc + i].
-template <int EPI>
-__global__ void __launch_bounds__(256)
-gemm_nt_simt_kernel(const float* __restrict__ A, int lda, const float* __restrict__ B, int ldb,
-                    int M, int N, int K, float* __restrict__ out, int ldc,
-                    const float* __restrict__ dscale, float tau) {
-    __shared__ float As[BK][BM + 4];
-    __shared__ float Bs[BK][BN + 4];
-    const int tid = threadIdx.x;
-    const int ti = tid % 16, tj = tid / 16;
-    const int i0 = blockIdx.x * BM, j0 = blockIdx.y * BN;
-    float acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += BK) {
-        for (int e = tid; e < BM * BK; e += 256) {
-            const int r = e / BK, k = e % BK;
-            const int gi = i0 + r, gk = k0 + k;
-            As[k][r] = (gi < M && gk < K) ? __ldg(A + (size_t)gi * lda + gk) : 0.f;
-            const int gj = j0 + r;
-            Bs[k][r] = (gj < N && gk < K) ? __ldg(B + (size_t)gj * ldb + gk) : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < BK; ++k) {
-            float a[4], b[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                a[u] = As[k][ti * 4 + u];
-                b[u] = Bs[k][tj * 4 + u];
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        const int j = j0 + tj * 4 + v;
-        if (j >= N) continue;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = i0 + ti * 4 + u;
-            if (i >= M) continue;
-            const size_t o = (size_t)j * ldc + i;
-            if (EPI == EPI_T) out[o] = acc[u][v];
-            else if (EPI == EPI_T_SCALE) out[o] = __ldg(dscale + o) * acc[u][v];
-            else out[o] = fmaf(tau, acc[u][v], out[o]);
-        }
-    }
+// float32 image -> bf16x3 planes (row pitch ld).
+__global__ void split_image_kernel(const float* __restrict__ y, int n1, int n2, int ld,
+                                   uint16_t* planes, size_t pstride) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)n1 * n2) return;
+    const int i = (int)(idx / n2), j = (int)(idx % n2);
+    uint16_t h0, h1, h2;
+    split3(__ldg(y + idx), h0, h1, h2);
+    const size_t o = (size_t)i * ld + j;
+    planes[o] = h0;
+    planes[pstride + o] = h1;
+    planes[2 * pstride + o] = h2;
 }
 
-template <int EPI>
-cudaError_t gemm_simt(const float* A, int lda, const float* B, int ldb, int M, int N, int K,
-                      float* out, int ldc, const float* d, float tau, cudaStream_t s) {
-    dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
-    gemm_nt_simt_kernel<EPI><<<grid, 256, 0, s>>>(A, lda, B, ldb, M, N, K, out, ldc, d, tau);
-    count_launch();
-    return cudaGetLastError();
+// ------------------------------------------------------------ host side --
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
 }
 
-ar_status make_transforms(int m, float** Tt, float** T, cudaStream_t stream) {
-    const size_t mm = (size_t)m * m;
+int round_up8(int v) { return (v + 7) & ~7; }
+
+// 3D map over bf16x3 planes: {K (inner), rows, 3 planes}, box {64, box_rows, 3}.
+ar_status make_map(CUtensorMap* map, const uint16_t* planes, int K, int rows, int ld,
+                   int box_rows) {
+    auto enc = encode_fn();
+    if (!enc) return fail(AR_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
+    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)PLANES};
+    cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)rows * ld * 2};
+    cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, (cuuint32_t)PLANES};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(planes), dims,
+                     strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(AR_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return AR_OK;
+}
+
+struct Operand {               // bf16x3 planes of a rows x K matrix and its TMA map
+    uint16_t* planes = nullptr;
+    int rows = 0, K = 0, ld = 0;
+    size_t pstride = 0;
+    CUtensorMap map;
+};
+
+ar_status alloc_operand(Operand& o, int rows, int K, int box_rows, cudaStream_t s) {
+    o.rows = rows;
+    o.K = K;
+    o.ld = round_up8(K);
+    o.pstride = (size_t)rows * o.ld;
+    AR_CUDA(cudaMallocAsync((void**)&o.planes, PLANES * o.pstride * sizeof(uint16_t), s));
+    return make_map(&o.map, o.planes, K, rows, o.ld, box_rows);
+}
+
+ar_status make_transforms(int m, Operand& Tt, Operand& T, cudaStream_t s) {
+    AR_TRY(alloc_operand(Tt, m, m, BN, s));
+    AR_TRY(alloc_operand(T, m, m, BN, s));
     double* tmp = nullptr;
-    AR_CUDA(cudaMallocAsync((void**)Tt, mm * sizeof(float), stream));
-    AR_CUDA(cudaMallocAsync((void**)T, mm * sizeof(float), stream));
-    AR_CUDA(cudaMallocAsync((void**)&tmp, 2 * (size_t)m * sizeof(double), stream));
+    AR_CUDA(cudaMallocAsync((void**)&tmp, 2 * (size_t)m * sizeof(double), s));
     if (m > 2) {
-        boundary_columns_kernel<<<m - 2, 256, 0, stream>>>(m, tmp, tmp + m);
+        boundary_columns_kernel<<<m - 2, 256, 0, s>>>(m, tmp, tmp + m);
         count_launch();
         AR_CUDA(cudaGetLastError());
     }
-    fill_transforms_f32_kernel<<<(unsigned)((mm + 255) / 256), 256, 0, stream>>>(m, tmp, tmp + m,
-                                                                                *Tt, *T);
+    const size_t mm = (size_t)m * m;
+    fill_transforms_kernel<<<(unsigned)((mm + 255) / 256), 256, 0, s>>>(m, Tt.ld, tmp, tmp + m,
+                                                                       Tt.planes, T.planes);
     count_launch();
     AR_CUDA(cudaGetLastError());
-    AR_CUDA(cudaFreeAsync(tmp, stream));
+    AR_CUDA(cudaFreeAsync(tmp, s));
+    return AR_OK;
+}
+
+ar_status contract(const Operand& A, const Operand& B, const TcEpiArgs& ep, int* err,
+                   cudaStream_t s) {
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(tc_contract_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)SMEM_BYTES);
+    });
+    if (attr != cudaSuccess) return cuda_fail(attr, "tc_contract_kernel smem attribute");
+    dim3 grid((A.rows + BM - 1) / BM, (B.rows + BN - 1) / BN);
+    tc_contract_kernel<<<grid, 128, SMEM_BYTES, s>>>(A.map, B.map, A.rows, B.rows, A.K, ep, err);
+    count_launch();
+    AR_CUDA(cudaGetLastError());
     return AR_OK;
 }
 
@@ -173,33 +384,34 @@ ar_status make_transforms(int m, float** Tt, float** T, cudaStream_t stream) {
 
 struct TransformPlan {
     int n1, n2;
-    float* Tt1 = nullptr;
-    float* T1 = nullptr;
-    float* Tt2 = nullptr;
-    float* T2 = nullptr;
-    float* bufA = nullptr;
-    float* bufB = nullptr;
+    Operand Tt1, T1, Tt2, T2;  // constant operands (B side)
+    Operand P;                 // n1 x n2 images: Y, then W          (A side)
+    Operand Qo;                // n2 x n1 images: U^T, then V^T      (A side)
+    int* err = nullptr;
+    bool shared2 = false;
 };
 
-ar_status transform_plan_create(int n1, int n2, cudaStream_t stream, TransformPlan** out) {
+ar_status transform_plan_create(int n1, int n2, cudaStream_t s, TransformPlan** out) {
     TransformPlan* p = new (std::nothrow) TransformPlan();
     if (!p) return fail(AR_ERR_ALLOC, "host allocation of the transform plan");
     p->n1 = n1;
     p->n2 = n2;
-    ar_status st = make_transforms(n1, &p->Tt1, &p->T1, stream);
+    ar_status st = make_transforms(n1, p->Tt1, p->T1, s);
     if (st == AR_OK) {
         if (n2 == n1) {
             p->Tt2 = p->Tt1;
             p->T2 = p->T1;
+            p->shared2 = true;
         } else {
-            st = make_transforms(n2, &p->Tt2, &p->T2, stream);
+            st = make_transforms(n2, p->Tt2, p->T2, s);
         }
     }
-    const size_t n = (size_t)n1 * n2;
-    if (st == AR_OK && cudaMallocAsync((void**)&p->bufA, n * sizeof(float), stream) != cudaSuccess)
-        st = fail(AR_ERR_ALLOC, "transform scratch");
-    if (st == AR_OK && cudaMallocAsync((void**)&p->bufB, n * sizeof(float), stream) != cudaSuccess)
-        st = fail(AR_ERR_ALLOC, "transform scratch");
+    if (st == AR_OK) st = alloc_operand(p->P, n1, n2, BM, s);
+    if (st == AR_OK) st = alloc_operand(p->Qo, n2, n1, BM, s);
+    if (st == AR_OK && cudaMallocAsync((void**)&p->err, sizeof(int), s) != cudaSuccess)
+        st = fail(AR_ERR_ALLOC, "transform error flag");
+    if (st == AR_OK && cudaMemsetAsync(p->err, 0, sizeof(int), s) != cudaSuccess)
+        st = fail(AR_ERR_CUDA, "transform error flag init");
     if (st != AR_OK) {
         transform_plan_destroy(p);
         return st;
@@ -210,39 +422,66 @@ ar_status transform_plan_create(int n1, int n2, cudaStream_t stream, TransformPl
 
 void transform_plan_destroy(TransformPlan* p) {
     if (!p) return;
-    if (p->Tt2 && p->Tt2 != p->Tt1) cudaFree(p->Tt2);
-    if (p->T2 && p->T2 != p->T1) cudaFree(p->T2);
-    cudaFree(p->Tt1);
-    cudaFree(p->T1);
-    cudaFree(p->bufA);
-    cudaFree(p->bufB);
+    if (!p->shared2) {
+        cudaFree(p->Tt2.planes);
+        cudaFree(p->T2.planes);
+    }
+    cudaFree(p->Tt1.planes);
+    cudaFree(p->T1.planes);
+    cudaFree(p->P.planes);
+    cudaFree(p->Qo.planes);
+    cudaFree(p->err);
     delete p;
 }
 
-uint16_t* transform_input_planes(TransformPlan*, size_t* plane_stride, int* ld) {
-    if (plane_stride) *plane_stride = 0;
-    if (ld) *ld = 0;
-    return nullptr;
+uint16_t* transform_input_planes(TransformPlan* p, size_t* plane_stride, int* ld) {
+    if (plane_stride) *plane_stride = p->P.pstride;
+    if (ld) *ld = p->P.ld;
+    return p->P.planes;
 }
 
-int transform_launches(const TransformPlan*, DInput) { return 4; }
+int* transform_error_flag(TransformPlan* p) { return p->err; }
+
+int transform_launches(const TransformPlan*, DInput din) { return din == DIN_FP32 ? 5 : 4; }
 
 ar_status transform_apply(TransformPlan* p, const float* d32, const float* y, DInput din,
                           float* out, DOutput dout, float tau, cudaStream_t s) {
-    if (din != DIN_FP32) return fail(AR_ERR_UNSUPPORTED, "split operand input not built");
     const int n1 = p->n1, n2 = p->n2;
-    cudaError_t e;
-    e = gemm_simt<EPI_T>(y, n2, p->Tt2, n2, n1, n2, n2, p->bufA, n1, nullptr, 0.f, s);
-    if (e != cudaSuccess) return cuda_fail(e, "transform G1");
-    e = gemm_simt<EPI_T_SCALE>(p->bufA, n1, p->Tt1, n1, n2, n1, n1, p->bufB, n2, d32, 0.f, s);
-    if (e != cudaSuccess) return cuda_fail(e, "transform G2");
-    e = gemm_simt<EPI_T>(p->bufB, n2, p->T2, n2, n1, n2, n2, p->bufA, n1, nullptr, 0.f, s);
-    if (e != cudaSuccess) return cuda_fail(e, "transform G3");
-    if (dout == DOUT_STORE)
-        e = gemm_simt<EPI_T>(p->bufA, n1, p->T1, n1, n2, n1, n1, out, n2, nullptr, 0.f, s);
-    else
-        e = gemm_simt<EPI_T_AXPY>(p->bufA, n1, p->T1, n1, n2, n1, n1, out, n2, nullptr, tau, s);
-    if (e != cudaSuccess) return cuda_fail(e, "transform G4");
+    if (din == DIN_FP32) {
+        const size_t n = (size_t)n1 * n2;
+        split_image_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(y, n1, n2, p->P.ld,
+                                                                       p->P.planes, p->P.pstride);
+        count_launch();
+        AR_CUDA(cudaGetLastError());
+    }
+    TcEpiArgs e{};
+    // G1: U^T = (Y T~2^T)^T  -> Q planes
+    e.mode = TE_SPLIT_T;
+    e.planes = p->Qo.planes;
+    e.pstride = p->Qo.pstride;
+    e.ld = p->Qo.ld;
+    AR_TRY(contract(p->P, p->Tt2, e, p->err, s));
+    // G2: W = d o (U^T T~1^T)^T -> P planes
+    e.mode = TE_SCALE_SPLIT_T;
+    e.planes = p->P.planes;
+    e.pstride = p->P.pstride;
+    e.ld = p->P.ld;
+    e.d = d32;
+    e.ldd = n2;
+    AR_TRY(contract(p->Qo, p->Tt1, e, p->err, s));
+    // G3: V^T = (W T2^T)^T -> Q planes
+    e.mode = TE_SPLIT_T;
+    e.planes = p->Qo.planes;
+    e.pstride = p->Qo.pstride;
+    e.ld = p->Qo.ld;
+    e.d = nullptr;
+    AR_TRY(contract(p->P, p->T2, e, p->err, s));
+    // G4: out (=|+= tau) (V^T T1^T)^T
+    e.mode = dout == DOUT_STORE ? TE_STORE_T : TE_AXPY_T;
+    e.out = out;
+    e.ldo = n2;
+    e.tau = tau;
+    AR_TRY(contract(p->Qo, p->T1, e, p->err, s));
     return AR_OK;
 }
 
