@@ -355,13 +355,15 @@ ar_status ar_restore(const float* g, const double* psf_host, int n1, int n2, int
             reblur.mode = CONV_AXPY;
             reblur.tau = (float)tau;
         }
+        reblur.f = f_true;
         for (int it = 0; st == AR_OK && it < iters; ++it) {
+            // the RRE numerator ||x_{k+1} - f||^2 is accumulated by the kernel that writes x_{k+1}
             st = conv_launch(blur, s);                           // r = g - A x_k
+            if (!pc) reblur.sumsq = f_true ? dsum + it : nullptr;
             if (st == AR_OK) st = conv_launch(reblur, s);        // z = A' r  (or x += tau A' r)
             if (st == AR_OK && pc)                               // x += tau D z
                 st = transform_apply(P->plan, P->d32, nullptr, DIN_SPLIT, x_out, DOUT_AXPY,
-                                     (float)tau, s);
-            if (st == AR_OK && f_true) st = reduce_diff_sq(x_out, f_true, n, dsum + it, s);
+                                     (float)tau, s, f_true, f_true ? dsum + it : nullptr);
         }
         if (st == AR_OK) st = count_nonfinite(x_out, n, dbad, s);
         if (st == AR_OK) {

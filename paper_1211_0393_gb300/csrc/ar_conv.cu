@@ -69,14 +69,30 @@ __device__ __forceinline__ void split3_store(uint16_t* planes, size_t pstride, s
     planes[2 * pstride + off] = __bfloat16_as_ushort(p2);
 }
 
-__device__ __forceinline__ void conv_epilogue(const ConvArgs& a, int row, int col, float v) {
+// Writes one output; returns (x_new - f)^2 for CONV_AXPY with a true image, else 0.
+__device__ __forceinline__ double conv_epilogue(const ConvArgs& a, int row, int col, float v) {
     const size_t o = (size_t)row * a.n2 + col;
     switch (a.mode) {
         case CONV_STORE: a.out[o] = v; break;
         case CONV_RESIDUAL: a.out[o] = __ldg(a.aux + o) - v; break;
-        case CONV_AXPY: a.out[o] = fmaf(a.tau, v, a.out[o]); break;
+        case CONV_AXPY: {
+            const float xn = fmaf(a.tau, v, a.out[o]);
+            a.out[o] = xn;
+            if (a.f) {
+                const double e = (double)xn - (double)__ldg(a.f + o);
+                return e * e;
+            }
+            break;
+        }
         default: split3_store(a.planes, a.plane_stride, (size_t)row * a.ld + col, v); break;
     }
+    return 0.0;
+}
+
+__device__ __forceinline__ void add_sumsq(double* sumsq, double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(sumsq, v);
 }
 
 // Fast path: support padded to Q x Q (Q = max(q1, q2) <= 15, zero taps outside
@@ -180,13 +196,15 @@ conv_fast_kernel(const ConvArgs a) {
     }
 
     const int col = c0 + tx;
+    double sq = 0.0;
     if (col < a.n2) {
 #pragma unroll
         for (int r = 0; r < RS; ++r) {
             const int row = r0 + ty * RS + r;
-            if (row < a.n1) conv_epilogue(a, row, col, acc[r]);
+            if (row < a.n1) sq += conv_epilogue(a, row, col, acc[r]);
         }
     }
+    if (a.sumsq) add_sumsq(a.sumsq, sq);
 }
 
 // Generic path for large supports: one output per thread, taps read straight
@@ -195,17 +213,21 @@ __global__ void __launch_bounds__(256)
 conv_generic_kernel(const ConvArgs a) {
     const int col = blockIdx.x * 32 + threadIdx.x;
     const int row = blockIdx.y * 8 + threadIdx.y;
-    if (row >= a.n1 || col >= a.n2) return;
+    const bool in = row < a.n1 && col < a.n2;
     const int kw = 2 * a.q2 + 1;
     float acc = 0.f;
-    for (int s2 = -a.q2; s2 <= a.q2; ++s2) {
-        for (int s1 = -a.q1; s1 <= a.q1; ++s1) {
-            const int t1 = a.flip ? -s1 : s1, t2 = a.flip ? -s2 : s2;
-            const float hv = __ldg(a.psf + (t1 + a.q1) * kw + (t2 + a.q2));
-            acc = fmaf(hv, ext_value(a.x, a.n1, a.n2, a.q1, a.q2, row - s1, col - s2), acc);
+    double sq = 0.0;
+    if (in) {
+        for (int s2 = -a.q2; s2 <= a.q2; ++s2) {
+            for (int s1 = -a.q1; s1 <= a.q1; ++s1) {
+                const int t1 = a.flip ? -s1 : s1, t2 = a.flip ? -s2 : s2;
+                const float hv = __ldg(a.psf + (t1 + a.q1) * kw + (t2 + a.q2));
+                acc = fmaf(hv, ext_value(a.x, a.n1, a.n2, a.q1, a.q2, row - s1, col - s2), acc);
+            }
         }
+        sq = conv_epilogue(a, row, col, acc);
     }
-    conv_epilogue(a, row, col, acc);
+    if (a.sumsq) add_sumsq(a.sumsq, sq);
 }
 
 template <int Q>

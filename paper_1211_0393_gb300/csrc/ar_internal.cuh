@@ -47,6 +47,8 @@ struct ConvArgs {
     int flip;            // 1: use h_{-s} (reblur A')
     int mode;
     float tau;
+    const float* f;      // CONV_AXPY: true image or null
+    double* sumsq;       // CONV_AXPY with f: += sum (x_new - f)^2 (float64)
 };
 
 // Launches the AR stencil on `stream` (validated arguments).
@@ -75,8 +77,11 @@ enum DOutput : int {
 // Pointer to the operand planes the stencil must fill for DIN_SPLIT.
 uint16_t* transform_input_planes(TransformPlan* p, size_t* plane_stride, int* ld);
 
+// With dout == DOUT_AXPY and f non-null, sum (x_new - f)^2 is added to *sumsq
+// (float64) in the same kernel that updates x.
 ar_status transform_apply(TransformPlan* p, const float* d32, const float* y, DInput din,
-                          float* out, DOutput dout, float tau, cudaStream_t stream);
+                          float* out, DOutput dout, float tau, cudaStream_t stream,
+                          const float* f = nullptr, double* sumsq = nullptr);
 
 // Number of kernels one transform_apply launches (for launch accounting).
 int transform_launches(const TransformPlan* p, DInput din);

@@ -22,13 +22,17 @@
 // tensor memory.  The dropped terms are below 2^-24 relative, so the
 // contraction is as accurate as a float32 one.
 //
-// Kernel: one 128 x 64 output tile per CTA (tcgen05.mma M = 128, N = 64,
-// K = 16), operands staged by TMA (one 3D box loads the three planes of a
-// 128-byte-swizzled K-major tile), a 3-stage mbarrier pipeline between a TMA
-// producer thread and an MMA issuer thread, the accumulator in TMEM, and an
-// epilogue in which each warp reads its 32 TMEM lanes and writes the tile
-// transposed (coalesced along the tile's M index) with the next step fused:
-// the bf16x3 split of the next operand, the filter d, or x += tau * result.
+// Kernel: one 128 x 128 output tile per pair of CTAs (a cluster of two that
+// splits K in halves; tcgen05.mma M = 128, N = 128, K = 16; four TMEM
+// accumulators taking the k-blocks in turn), operands staged by TMA (one 3D
+// box loads the three planes of a 128-byte-swizzled K-major tile), a 2-stage
+// mbarrier pipeline between a TMA producer thread and an MMA issuer thread,
+// and an epilogue in which each CTA sends the peer's half of its partial tile
+// through distributed shared memory, adds the half it receives, and writes its
+// half transposed (coalesced along the tile's M index) with the next step
+// fused: the bf16x3 split of the next operand, the filter d, or
+// x += tau * result.  Full-rate MMA at M = 128 needs N >= 128: with smaller N
+// the six products' operand reads exceed the shared-memory bandwidth.
 
 #include "ar_internal.cuh"
 #include "ar_tc.cuh"
@@ -38,21 +42,34 @@
 #include <cuda_bf16.h>
 
 #include <cstdlib>
+#include <map>
 #include <mutex>
 #include <new>
+#include <utility>
 
 namespace ar {
 namespace {
 
-constexpr int BM = 128, BN = 64, BK = 64, STAGES = 3, PLANES = 3;
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 2, PLANES = 3;
 constexpr uint32_t A_PLANE = BM * BK * 2;                 // 16 KiB
-constexpr uint32_t B_PLANE = BN * BK * 2;                 // 8 KiB
+constexpr uint32_t B_PLANE = BN * BK * 2;                 // 16 KiB
 constexpr uint32_t A_STAGE = PLANES * A_PLANE;
 constexpr uint32_t B_STAGE = PLANES * B_PLANE;
-constexpr uint32_t STAGE_BYTES = A_STAGE + B_STAGE;      // 72 KiB
+constexpr uint32_t STAGE_BYTES = A_STAGE + B_STAGE;      // 96 KiB
+// Split-K over the two CTAs of a cluster: CTA r accumulates its half of the
+// k-blocks, then finishes columns [r*HALF, (r+1)*HALF) of the tile after
+// receiving the peer's partial sums for them through distributed shared memory.
+constexpr int SPLITK = 2;
+constexpr int HALF = BN / SPLITK;
+constexpr uint32_t RECV_BYTES = HALF * BM * 4;            // 32 KiB, column-major [HALF][BM]
+// k-blocks are spread round-robin over NACC accumulators of BN columns each,
+// summed with round-to-nearest float32 adds in the epilogue: the tensor core's
+// float32 accumulation loses up to an ulp per accumulate step, so fewer steps
+// per accumulator keep a K = 1024 contraction at float32-grade accuracy.
+constexpr int NACC = 4;
+constexpr uint32_t TMEM_COLS = NACC * BN;                 // 512: the whole TMEM of the SM
 constexpr uint32_t CTRL_BYTES = 8 * (2 * STAGES + 1) + 16;
-constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + CTRL_BYTES + 1024;
-constexpr uint32_t TMEM_COLS = 64;
+constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + RECV_BYTES + CTRL_BYTES + 1024;
 
 // The six split products (a plane, b plane), smallest first.
 __constant__ int kPA[6] = {2, 1, 0, 1, 0, 0};
@@ -70,6 +87,8 @@ struct TcEpiArgs {
     const float* d;        // filter: d[col * ldd + row]
     int ldd;
     float tau;
+    const float* f;        // TE_AXPY_T: true image (same layout as out) or null
+    double* sumsq;         // TE_AXPY_T with f: += sum (x_new - f)^2
 };
 
 __device__ __forceinline__ void split3(float v, uint16_t& h0, uint16_t& h1, uint16_t& h2) {
@@ -82,7 +101,47 @@ __device__ __forceinline__ void split3(float v, uint16_t& h0, uint16_t& h1, uint
     h2 = __bfloat16_as_ushort(p2);
 }
 
-__global__ void __launch_bounds__(128, 1)
+// Sum of the first `nacc` accumulators at 16 consecutive columns (zeros if none).
+__device__ __forceinline__ void acc_sum16(uint32_t trow, int col0, int nacc, float (&v)[16]) {
+    using namespace tc;
+    float a[16], b[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = 0.f;
+    if (nacc <= 0) return;
+    tmem_ld16x2(trow + col0, trow + BN + col0, a, b);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = nacc > 1 ? a[j] + b[j] : a[j];
+    if (nacc <= 2) return;
+    tmem_ld16x2(trow + 2 * BN + col0, trow + 3 * BN + col0, a, b);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = nacc > 3 ? (v[j] + a[j]) + b[j] : v[j] + a[j];
+}
+
+// Returns the squared error (x_new - f)^2 of an AXPY store when f is given, else 0.
+__device__ __forceinline__ double epilogue_store(const TcEpiArgs& ep, int row, int col, float x) {
+    if (ep.mode == TE_STORE_T) {
+        ep.out[(size_t)col * ep.ldo + row] = x;
+    } else if (ep.mode == TE_AXPY_T) {
+        const size_t o = (size_t)col * ep.ldo + row;
+        const float xn = fmaf(ep.tau, x, ep.out[o]);
+        ep.out[o] = xn;
+        if (ep.f) {
+            const double e = (double)xn - (double)__ldg(ep.f + o);
+            return e * e;
+        }
+    } else {
+        if (ep.mode == TE_SCALE_SPLIT_T) x *= __ldg(ep.d + (size_t)col * ep.ldd + row);
+        uint16_t h0, h1, h2;
+        split3(x, h0, h1, h2);
+        const size_t o = (size_t)col * ep.ld + row;
+        ep.planes[o] = h0;
+        ep.planes[ep.pstride + o] = h1;
+        ep.planes[2 * ep.pstride + o] = h2;
+    }
+    return 0.0;
+}
+
+__global__ void __cluster_dims__(1, 1, SPLITK) __launch_bounds__(128, 1)
 tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    int M, int N, int K, const TcEpiArgs ep, int* err) {
     using namespace tc;
@@ -90,14 +149,21 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;         // 128B-swizzled tiles need 1 KiB alignment
     uint8_t* gbase = smem_raw + (base - raw);
-    const uint32_t bars = base + STAGES * STAGE_BYTES;
+    const uint32_t recv = base + STAGES * STAGE_BYTES;
+    const float* recv_ptr = reinterpret_cast<const float*>(gbase + STAGES * STAGE_BYTES);
+    const uint32_t bars = recv + RECV_BYTES;
     const uint32_t done_bar = bars + 8u * (2 * STAGES);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(gbase + STAGES * STAGE_BYTES + 8 * (2 * STAGES + 1));
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(gbase + STAGES * STAGE_BYTES + RECV_BYTES +
+                                                  8 * (2 * STAGES + 1));
     volatile int* sflag = reinterpret_cast<volatile int*>(tslot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-    const int nk = (K + BK - 1) / BK;
+    const uint32_t rank = cluster_ctarank();
+    const int nk_all = (K + BK - 1) / BK;
+    const int nk_first = (nk_all + 1) / 2;
+    const int kb_begin = rank == 0 ? 0 : nk_first;
+    const int nk = rank == 0 ? nk_first : nk_all - nk_first;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -131,8 +197,8 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             if (*sflag) break;
             const uint32_t a = base + s * STAGE_BYTES;
             mbar_arrive_expect_tx(bars + 8u * s, STAGE_BYTES);
-            tma_load_3d(a, &tmA, kb * BK, m0, 0, bars + 8u * s);
-            tma_load_3d(a + A_STAGE, &tmB, kb * BK, n0, 0, bars + 8u * s);
+            tma_load_3d(a, &tmA, (kb_begin + kb) * BK, m0, 0, bars + 8u * s);
+            tma_load_3d(a + A_STAGE, &tmB, (kb_begin + kb) * BK, n0, 0, bars + 8u * s);
             ++issued;
         }
         // no load may still be in flight when the CTA exits
@@ -150,52 +216,65 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             fence_after_sync();
             const uint32_t a = base + s * STAGE_BYTES;
             const uint32_t b = a + A_STAGE;
+            const uint32_t d = tmem + (uint32_t)(kb % NACC) * BN;
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
 #pragma unroll
                 for (int t = 0; t < 6; ++t) {
                     const uint64_t ad = desc_k_sw128(a + kPA[t] * A_PLANE + kk * 32);
                     const uint64_t bd = desc_k_sw128(b + kPB[t] * B_PLANE + kk * 32);
-                    mma_bf16(tmem, ad, bd, idesc, (kb | kk | t) != 0 ? 1u : 0u);
+                    mma_bf16(d, ad, bd, idesc, (kb >= NACC || kk != 0 || t != 0) ? 1u : 0u);
                 }
             }
             mma_commit(bars + 8u * (STAGES + s));        // frees the stage when its MMAs finish
         }
-        mma_commit(done_bar);                           // accumulator complete
+        if (nk > 0) {
+            mma_commit(done_bar);                        // accumulators complete
+        } else {
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(done_bar) : "memory");
+        }
     }
 
     // ---- epilogue: warp w owns TMEM lanes 32w..32w+31 = tile rows m0 + 32w + lane
     const bool ready = mbar_wait(done_bar, 0);
     __syncwarp();
     fence_after_sync();
-    const bool write = ready && *sflag == 0;
-    const int row = m0 + warp * 32 + lane;
+    const bool ok = ready && *sflag == 0;
+    const int nacc = ok ? (nk < NACC ? nk : NACC) : 0;
+    const int lrow = warp * 32 + lane;
+    const int row = m0 + lrow;
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t peer = rank ^ 1u;
+
+    // 1) the peer's half of the columns -> the peer's receive buffer
+    const uint32_t rrecv = mapa(recv, peer);
 #pragma unroll 1
-    for (int c = 0; c < BN / 16; ++c) {
+    for (int c = 0; c < HALF / 16; ++c) {
         float v[16];
-        tmem_ld16(trow + c * 16, v);
-        if (!write || row >= M) continue;
+        acc_sum16(trow, (int)peer * HALF + c * 16, nacc, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) st_cluster_f32(rrecv + 4u * ((c * 16 + j) * BM + lrow), v[j]);
+    }
+    cluster_sync();
+
+    // 2) own half: own partial sums + the peer's, then the fused next step
+    double sq = 0.0;
+#pragma unroll 1
+    for (int c = 0; c < HALF / 16; ++c) {
+        float v[16];
+        acc_sum16(trow, (int)rank * HALF + c * 16, nacc, v);
+        if (!ok || row >= M) continue;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            const int col = n0 + c * 16 + j;
+            const int col = n0 + (int)rank * HALF + c * 16 + j;
             if (col >= N) break;
-            float x = v[j];
-            if (ep.mode == TE_STORE_T) {
-                ep.out[(size_t)col * ep.ldo + row] = x;
-            } else if (ep.mode == TE_AXPY_T) {
-                float* o = ep.out + (size_t)col * ep.ldo + row;
-                *o = fmaf(ep.tau, x, *o);
-            } else {
-                if (ep.mode == TE_SCALE_SPLIT_T) x *= __ldg(ep.d + (size_t)col * ep.ldd + row);
-                uint16_t h0, h1, h2;
-                split3(x, h0, h1, h2);
-                const size_t o = (size_t)col * ep.ld + row;
-                ep.planes[o] = h0;
-                ep.planes[ep.pstride + o] = h1;
-                ep.planes[2 * ep.pstride + o] = h2;
-            }
+            sq += epilogue_store(ep, row, col, v[j] + recv_ptr[(c * 16 + j) * BM + lrow]);
         }
+    }
+    if (ep.sumsq) {                                      // fused ||x_{k+1} - f||^2 (float64)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
+        if (lane == 0 && sq != 0.0) atomicAdd(ep.sumsq, sq);
     }
 
     fence_before_sync();
@@ -204,23 +283,27 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         fence_after_sync();
         tmem_dealloc(tmem, TMEM_COLS);
     }
-    if (threadIdx.x == 0 && (!ready || *sflag)) atomicExch(err, 1);
+    if (threadIdx.x == 0 && !ok) atomicExch(err, 1);
 }
 
 // ---------------------------------------------------------------- matrices --
-__device__ __forceinline__ double q_entry(int s, int t, int m) {
-    // Q_{m-2}[s, t] = sqrt(2/(m-1)) sin(s t pi/(m-1)), s, t = 1..m-2
-    const long long per = 2LL * (m - 1);
-    const long long r = ((long long)s * t) % per;
-    return sqrt(2.0 / (double)(m - 1)) * sinpi((double)r / (double)(m - 1));
+// Q_{m-2}[s, t] = sqrt(2/(m-1)) sin(s t pi/(m-1)) depends only on
+// r = (s t) mod 2(m-1): tab[r] holds the 2(m-1) distinct values, in float64.
+__global__ void sine_table_kernel(int m, double* tab) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < 2 * (m - 1)) tab[r] = sqrt(2.0 / (double)(m - 1)) * sinpi((double)r / (double)(m - 1));
+}
+
+__device__ __forceinline__ double q_entry(const double* tab, int s, int t, int m) {
+    return tab[((long long)s * t) % (2LL * (m - 1))];
 }
 
 // qp[s-1] = (Q p)_s, qjp[s-1] = (Q J p)_s, s = 1..m-2, one block per row.
-__global__ void boundary_columns_kernel(int m, double* qp, double* qjp) {
+__global__ void boundary_columns_kernel(int m, const double* tab, double* qp, double* qjp) {
     const int s = blockIdx.x + 1;
     double a = 0.0, b = 0.0;
     for (int t = 1 + threadIdx.x; t <= m - 2; t += blockDim.x) {
-        const double q = q_entry(s, t, m);
+        const double q = q_entry(tab, s, t, m);
         const double pt = 1.0 - (double)t / (double)(m - 1);
         a += q * pt;
         b += q * (1.0 - pt);          // (J p)_t = p_{m-1-t} = t/(m-1)
@@ -253,8 +336,8 @@ __device__ __forceinline__ void split3_f64(double v, uint16_t& h0, uint16_t& h1,
 }
 
 // T~'_m (analysis) and T'_m (synthesis) as bf16x3 planes, row pitch ld.
-__global__ void fill_transforms_kernel(int m, int ld, const double* qp, const double* qjp,
-                                       uint16_t* Tt, uint16_t* T) {
+__global__ void fill_transforms_kernel(int m, int ld, const double* tab, const double* qp,
+                                       const double* qjp, uint16_t* Tt, uint16_t* T) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)m * m) return;
     const int s = (int)(idx / m), t = (int)(idx % m);
@@ -268,7 +351,7 @@ __global__ void fill_transforms_kernel(int m, int ld, const double* qp, const do
         vt = -qjp[s - 1];
         v = (double)s / (double)(m - 1);
     } else {
-        vt = v = q_entry(s, t, m);
+        vt = v = q_entry(tab, s, t, m);
     }
     const size_t ps = (size_t)m * ld, o = (size_t)s * ld + t;
     uint16_t a0, a1, a2;
@@ -336,31 +419,68 @@ struct Operand {               // bf16x3 planes of a rows x K matrix and its TMA
     CUtensorMap map;
 };
 
-ar_status alloc_operand(Operand& o, int rows, int K, int box_rows, cudaStream_t s) {
+ar_status alloc_operand(Operand& o, int rows, int K, int box_rows, cudaStream_t s,
+                        bool permanent = false) {
     o.rows = rows;
     o.K = K;
     o.ld = round_up8(K);
     o.pstride = (size_t)rows * o.ld;
-    AR_CUDA(cudaMallocAsync((void**)&o.planes, PLANES * o.pstride * sizeof(uint16_t), s));
+    const size_t bytes = PLANES * o.pstride * sizeof(uint16_t);
+    if (permanent) AR_CUDA(cudaMalloc((void**)&o.planes, bytes));
+    else AR_CUDA(cudaMallocAsync((void**)&o.planes, bytes, s));
     return make_map(&o.map, o.planes, K, rows, o.ld, box_rows);
 }
 
-ar_status make_transforms(int m, Operand& Tt, Operand& T, cudaStream_t s) {
-    AR_TRY(alloc_operand(Tt, m, m, BN, s));
-    AR_TRY(alloc_operand(T, m, m, BN, s));
+// Builds T~'_m and T'_m on `s` and waits for them.
+ar_status build_transforms(int m, Operand& Tt, Operand& T, cudaStream_t s) {
+    AR_TRY(alloc_operand(Tt, m, m, BN, s, true));
+    AR_TRY(alloc_operand(T, m, m, BN, s, true));
     double* tmp = nullptr;
-    AR_CUDA(cudaMallocAsync((void**)&tmp, 2 * (size_t)m * sizeof(double), s));
+    const int ntab = 2 * (m - 1);
+    AR_CUDA(cudaMallocAsync((void**)&tmp, (2 * (size_t)m + ntab) * sizeof(double), s));
+    double* tab = tmp + 2 * m;
+    sine_table_kernel<<<(ntab + 255) / 256, 256, 0, s>>>(m, tab);
+    count_launch();
+    AR_CUDA(cudaGetLastError());
     if (m > 2) {
-        boundary_columns_kernel<<<m - 2, 256, 0, s>>>(m, tmp, tmp + m);
+        boundary_columns_kernel<<<m - 2, 256, 0, s>>>(m, tab, tmp, tmp + m);
         count_launch();
         AR_CUDA(cudaGetLastError());
     }
     const size_t mm = (size_t)m * m;
-    fill_transforms_kernel<<<(unsigned)((mm + 255) / 256), 256, 0, s>>>(m, Tt.ld, tmp, tmp + m,
+    fill_transforms_kernel<<<(unsigned)((mm + 255) / 256), 256, 0, s>>>(m, Tt.ld, tab, tmp, tmp + m,
                                                                        Tt.planes, T.planes);
     count_launch();
     AR_CUDA(cudaGetLastError());
     AR_CUDA(cudaFreeAsync(tmp, s));
+    AR_CUDA(cudaStreamSynchronize(s));
+    return AR_OK;
+}
+
+// The transform operands depend only on the side length: they are built once
+// per (device, m) and kept for the life of the process.
+struct TransformPair {
+    Operand Tt, T;
+};
+
+ar_status cached_transforms(int m, cudaStream_t s, TransformPair* out) {
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, TransformPair> cache;
+    int dev = 0;
+    AR_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find({dev, m});
+    if (it == cache.end()) {
+        TransformPair tp;
+        ar_status st = build_transforms(m, tp.Tt, tp.T, s);
+        if (st != AR_OK) {
+            cudaFree(tp.Tt.planes);
+            cudaFree(tp.T.planes);
+            return st;
+        }
+        it = cache.emplace(std::make_pair(dev, m), tp).first;
+    }
+    *out = it->second;
     return AR_OK;
 }
 
@@ -373,7 +493,7 @@ ar_status contract(const Operand& A, const Operand& B, const TcEpiArgs& ep, int*
                                     (int)SMEM_BYTES);
     });
     if (attr != cudaSuccess) return cuda_fail(attr, "tc_contract_kernel smem attribute");
-    dim3 grid((A.rows + BM - 1) / BM, (B.rows + BN - 1) / BN);
+    dim3 grid((A.rows + BM - 1) / BM, (B.rows + BN - 1) / BN, SPLITK);
     tc_contract_kernel<<<grid, 128, SMEM_BYTES, s>>>(A.map, B.map, A.rows, B.rows, A.K, ep, err);
     count_launch();
     AR_CUDA(cudaGetLastError());
@@ -384,11 +504,10 @@ ar_status contract(const Operand& A, const Operand& B, const TcEpiArgs& ep, int*
 
 struct TransformPlan {
     int n1, n2;
-    Operand Tt1, T1, Tt2, T2;  // constant operands (B side)
+    Operand Tt1, T1, Tt2, T2;  // constant operands (B side), owned by the process-wide cache
     Operand P;                 // n1 x n2 images: Y, then W          (A side)
     Operand Qo;                // n2 x n1 images: U^T, then V^T      (A side)
     int* err = nullptr;
-    bool shared2 = false;
 };
 
 ar_status transform_plan_create(int n1, int n2, cudaStream_t s, TransformPlan** out) {
@@ -396,15 +515,14 @@ ar_status transform_plan_create(int n1, int n2, cudaStream_t s, TransformPlan** 
     if (!p) return fail(AR_ERR_ALLOC, "host allocation of the transform plan");
     p->n1 = n1;
     p->n2 = n2;
-    ar_status st = make_transforms(n1, p->Tt1, p->T1, s);
+    TransformPair t1, t2;
+    ar_status st = cached_transforms(n1, s, &t1);
+    if (st == AR_OK) st = cached_transforms(n2, s, &t2);
     if (st == AR_OK) {
-        if (n2 == n1) {
-            p->Tt2 = p->Tt1;
-            p->T2 = p->T1;
-            p->shared2 = true;
-        } else {
-            st = make_transforms(n2, p->Tt2, p->T2, s);
-        }
+        p->Tt1 = t1.Tt;
+        p->T1 = t1.T;
+        p->Tt2 = t2.Tt;
+        p->T2 = t2.T;
     }
     if (st == AR_OK) st = alloc_operand(p->P, n1, n2, BM, s);
     if (st == AR_OK) st = alloc_operand(p->Qo, n2, n1, BM, s);
@@ -422,12 +540,6 @@ ar_status transform_plan_create(int n1, int n2, cudaStream_t s, TransformPlan** 
 
 void transform_plan_destroy(TransformPlan* p) {
     if (!p) return;
-    if (!p->shared2) {
-        cudaFree(p->Tt2.planes);
-        cudaFree(p->T2.planes);
-    }
-    cudaFree(p->Tt1.planes);
-    cudaFree(p->T1.planes);
     cudaFree(p->P.planes);
     cudaFree(p->Qo.planes);
     cudaFree(p->err);
@@ -445,7 +557,8 @@ int* transform_error_flag(TransformPlan* p) { return p->err; }
 int transform_launches(const TransformPlan*, DInput din) { return din == DIN_FP32 ? 5 : 4; }
 
 ar_status transform_apply(TransformPlan* p, const float* d32, const float* y, DInput din,
-                          float* out, DOutput dout, float tau, cudaStream_t s) {
+                          float* out, DOutput dout, float tau, cudaStream_t s,
+                          const float* f, double* sumsq) {
     const int n1 = p->n1, n2 = p->n2;
     if (din == DIN_FP32) {
         const size_t n = (size_t)n1 * n2;
@@ -481,6 +594,10 @@ ar_status transform_apply(TransformPlan* p, const float* d32, const float* y, DI
     e.out = out;
     e.ldo = n2;
     e.tau = tau;
+    if (dout == DOUT_AXPY) {
+        e.f = f;
+        e.sumsq = f ? sumsq : nullptr;
+    }
     AR_TRY(contract(p->Qo, p->T1, e, p->err, s));
     return AR_OK;
 }
