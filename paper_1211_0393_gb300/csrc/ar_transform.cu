@@ -117,33 +117,13 @@ __device__ __forceinline__ void acc_sum16(uint32_t trow, int col0, int nacc, flo
     for (int j = 0; j < 16; ++j) v[j] = nacc > 3 ? (v[j] + a[j]) + b[j] : v[j] + a[j];
 }
 
-// Returns the squared error (x_new - f)^2 of an AXPY store when f is given, else 0.
-__device__ __forceinline__ double epilogue_store(const TcEpiArgs& ep, int row, int col, float x) {
-    if (ep.mode == TE_STORE_T) {
-        ep.out[(size_t)col * ep.ldo + row] = x;
-    } else if (ep.mode == TE_AXPY_T) {
-        const size_t o = (size_t)col * ep.ldo + row;
-        const float xn = fmaf(ep.tau, x, ep.out[o]);
-        ep.out[o] = xn;
-        if (ep.f) {
-            const double e = (double)xn - (double)__ldg(ep.f + o);
-            return e * e;
-        }
-    } else {
-        if (ep.mode == TE_SCALE_SPLIT_T) x *= __ldg(ep.d + (size_t)col * ep.ldd + row);
-        uint16_t h0, h1, h2;
-        split3(x, h0, h1, h2);
-        const size_t o = (size_t)col * ep.ld + row;
-        ep.planes[o] = h0;
-        ep.planes[ep.pstride + o] = h1;
-        ep.planes[2 * ep.pstride + o] = h2;
-    }
-    return 0.0;
-}
+constexpr int NTHREADS = 256;           // 8 warps: two per TMEM lane quarter in the epilogue
+constexpr int WCOLS = HALF / 2;         // columns of the CTA's half handled by one warp
 
-__global__ void __cluster_dims__(1, 1, SPLITK) __launch_bounds__(128, 1)
+__global__ void __cluster_dims__(1, 1, SPLITK) __launch_bounds__(NTHREADS, 1)
 tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   int M, int N, int K, const TcEpiArgs ep, int* err) {
+                   const __grid_constant__ CUtensorMap tmO, int M, int N, int K, const TcEpiArgs ep,
+                   int* err) {
     using namespace tc;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -156,8 +136,11 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     uint32_t* tslot = reinterpret_cast<uint32_t*>(gbase + STAGES * STAGE_BYTES + RECV_BYTES +
                                                   8 * (2 * STAGES + 1));
     volatile int* sflag = reinterpret_cast<volatile int*>(tslot + 1);
+    // after the main loop the stage area stages the bf16x3 output tile [3][HALF][BM]
+    uint16_t* stage_out = reinterpret_cast<uint16_t*>(gbase);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int quarter = warp & 3, sub = warp >> 2;
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
     const uint32_t rank = cluster_ctarank();
     const int nk_all = (K + BK - 1) / BK;
@@ -235,46 +218,99 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         }
     }
 
-    // ---- epilogue: warp w owns TMEM lanes 32w..32w+31 = tile rows m0 + 32w + lane
+    // ---- epilogue.  Warp w reads TMEM lanes 32(w%4).. (tile rows m0 + 32(w%4) + lane) and
+    // handles WCOLS of the CTA's HALF columns; its inputs are fetched while the MMAs run.
+    const int lrow = quarter * 32 + lane;
+    const int row = m0 + lrow;
+    const uint32_t peer = rank ^ 1u;
+    const int ocol0 = (int)rank * HALF + sub * WCOLS;    // tile-relative own columns
+    const int pcol0 = (int)peer * HALF + sub * WCOLS;    // tile-relative peer columns
+    float pre[WCOLS];
+    float pref[WCOLS];
+#pragma unroll
+    for (int j = 0; j < WCOLS; ++j) {
+        const int col = n0 + ocol0 + j;
+        const bool in = row < M && col < N;
+        pre[j] = 0.f;
+        pref[j] = 0.f;
+        if (ep.mode == TE_SCALE_SPLIT_T) {
+            if (in) pre[j] = __ldg(ep.d + (size_t)col * ep.ldd + row);
+        } else if (ep.mode == TE_AXPY_T) {
+            if (in) {
+                pre[j] = ep.out[(size_t)col * ep.ldo + row];
+                if (ep.f) pref[j] = __ldg(ep.f + (size_t)col * ep.ldo + row);
+            }
+        }
+    }
+
     const bool ready = mbar_wait(done_bar, 0);
     __syncwarp();
     fence_after_sync();
     const bool ok = ready && *sflag == 0;
     const int nacc = ok ? (nk < NACC ? nk : NACC) : 0;
-    const int lrow = warp * 32 + lane;
-    const int row = m0 + lrow;
-    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-    const uint32_t peer = rank ^ 1u;
+    const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
 
-    // 1) the peer's half of the columns -> the peer's receive buffer
+    // 1) the peer's columns -> the peer's receive buffer [HALF][BM]
     const uint32_t rrecv = mapa(recv, peer);
-#pragma unroll 1
-    for (int c = 0; c < HALF / 16; ++c) {
-        float v[16];
-        acc_sum16(trow, (int)peer * HALF + c * 16, nacc, v);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) st_cluster_f32(rrecv + 4u * ((c * 16 + j) * BM + lrow), v[j]);
+    for (int c = 0; c < WCOLS / 16; ++c) {
+        float v[16];
+        acc_sum16(trow, pcol0 + c * 16, nacc, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            st_cluster_f32(rrecv + 4u * ((sub * WCOLS + c * 16 + j) * BM + lrow), v[j]);
     }
     cluster_sync();
 
-    // 2) own half: own partial sums + the peer's, then the fused next step
+    // 2) own columns: own partial sums + the peer's, then the fused next step
+    const bool split_out = ep.mode == TE_SPLIT_T || ep.mode == TE_SCALE_SPLIT_T;
     double sq = 0.0;
-#pragma unroll 1
-    for (int c = 0; c < HALF / 16; ++c) {
+#pragma unroll
+    for (int c = 0; c < WCOLS / 16; ++c) {
         float v[16];
-        acc_sum16(trow, (int)rank * HALF + c * 16, nacc, v);
-        if (!ok || row >= M) continue;
+        acc_sum16(trow, ocol0 + c * 16, nacc, v);
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            const int col = n0 + (int)rank * HALF + c * 16 + j;
-            if (col >= N) break;
-            sq += epilogue_store(ep, row, col, v[j] + recv_ptr[(c * 16 + j) * BM + lrow]);
+            const int jj = c * 16 + j;                  // 0..WCOLS-1
+            const int hc = sub * WCOLS + jj;            // column within the CTA's half
+            float x = v[j] + recv_ptr[hc * BM + lrow];
+            if (split_out) {
+                if (ep.mode == TE_SCALE_SPLIT_T) x *= pre[jj];
+                uint16_t h0, h1, h2;
+                split3(x, h0, h1, h2);
+                stage_out[(0 * HALF + hc) * BM + lrow] = h0;
+                stage_out[(1 * HALF + hc) * BM + lrow] = h1;
+                stage_out[(2 * HALF + hc) * BM + lrow] = h2;
+            } else if (ok && row < M && n0 + ocol0 + jj < N) {
+                const size_t o = (size_t)(n0 + ocol0 + jj) * ep.ldo + row;
+                if (ep.mode == TE_STORE_T) {
+                    ep.out[o] = x;
+                } else {
+                    const float xn = fmaf(ep.tau, x, pre[jj]);
+                    ep.out[o] = xn;
+                    if (ep.f) {
+                        const double e = (double)xn - (double)pref[jj];
+                        sq += e * e;
+                    }
+                }
+            }
         }
     }
     if (ep.sumsq) {                                      // fused ||x_{k+1} - f||^2 (float64)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
         if (lane == 0 && sq != 0.0) atomicAdd(ep.sumsq, sq);
+    }
+    if (split_out) {
+        // the staged [3][HALF][BM] tile leaves in one TMA store (rows past M and
+        // columns past N are clipped by the tensor map)
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0 && ok) {
+            tma_store_3d(&tmO, m0, n0 + (int)rank * HALF, 0, base);
+            bulk_commit();
+            bulk_wait_read();
+        }
     }
 
     fence_before_sync();
@@ -396,27 +432,30 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 int round_up8(int v) { return (v + 7) & ~7; }
 
-// 3D map over bf16x3 planes: {K (inner), rows, 3 planes}, box {64, box_rows, 3}.
-ar_status make_map(CUtensorMap* map, const uint16_t* planes, int K, int rows, int ld,
-                   int box_rows) {
+// 3D map over bf16x3 planes {K (inner), rows, 3 planes} with box
+// {box_k, box_rows, 3}: 128-byte swizzle for operand loads, none for stores.
+ar_status make_map(CUtensorMap* map, const uint16_t* planes, int K, int rows, int ld, int box_k,
+                   int box_rows, bool swizzle) {
     auto enc = encode_fn();
     if (!enc) return fail(AR_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
     cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)PLANES};
     cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)rows * ld * 2};
-    cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, (cuuint32_t)PLANES};
+    cuuint32_t box[3] = {(cuuint32_t)box_k, (cuuint32_t)box_rows, (cuuint32_t)PLANES};
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(planes), dims,
-                     strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(AR_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return AR_OK;
 }
 
-struct Operand {               // bf16x3 planes of a rows x K matrix and its TMA map
+struct Operand {               // bf16x3 planes of a rows x K matrix and its TMA maps
     uint16_t* planes = nullptr;
     int rows = 0, K = 0, ld = 0;
     size_t pstride = 0;
-    CUtensorMap map;
+    CUtensorMap map;           // operand loads: box {BK, box_rows, 3}, 128B swizzle
+    CUtensorMap omap;          // epilogue stores (image operands): box {BM, HALF, 3}
 };
 
 ar_status alloc_operand(Operand& o, int rows, int K, int box_rows, cudaStream_t s,
@@ -428,7 +467,9 @@ ar_status alloc_operand(Operand& o, int rows, int K, int box_rows, cudaStream_t 
     const size_t bytes = PLANES * o.pstride * sizeof(uint16_t);
     if (permanent) AR_CUDA(cudaMalloc((void**)&o.planes, bytes));
     else AR_CUDA(cudaMallocAsync((void**)&o.planes, bytes, s));
-    return make_map(&o.map, o.planes, K, rows, o.ld, box_rows);
+    AR_TRY(make_map(&o.map, o.planes, K, rows, o.ld, BK, box_rows, true));
+    if (!permanent) AR_TRY(make_map(&o.omap, o.planes, K, rows, o.ld, BM, HALF, false));
+    return AR_OK;
 }
 
 // Builds T~'_m and T'_m on `s` and waits for them.
@@ -484,8 +525,9 @@ ar_status cached_transforms(int m, cudaStream_t s, TransformPair* out) {
     return AR_OK;
 }
 
-ar_status contract(const Operand& A, const Operand& B, const TcEpiArgs& ep, int* err,
-                   cudaStream_t s) {
+// C = A B^T with the epilogue `ep`; O receives the split output planes.
+ar_status contract(const Operand& A, const Operand& B, const Operand* O, const TcEpiArgs& ep,
+                   int* err, cudaStream_t s) {
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] {
@@ -494,7 +536,8 @@ ar_status contract(const Operand& A, const Operand& B, const TcEpiArgs& ep, int*
     });
     if (attr != cudaSuccess) return cuda_fail(attr, "tc_contract_kernel smem attribute");
     dim3 grid((A.rows + BM - 1) / BM, (B.rows + BN - 1) / BN, SPLITK);
-    tc_contract_kernel<<<grid, 128, SMEM_BYTES, s>>>(A.map, B.map, A.rows, B.rows, A.K, ep, err);
+    tc_contract_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(A.map, B.map, O ? O->omap : A.map, A.rows,
+                                                          B.rows, A.K, ep, err);
     count_launch();
     AR_CUDA(cudaGetLastError());
     return AR_OK;
@@ -573,7 +616,7 @@ ar_status transform_apply(TransformPlan* p, const float* d32, const float* y, DI
     e.planes = p->Qo.planes;
     e.pstride = p->Qo.pstride;
     e.ld = p->Qo.ld;
-    AR_TRY(contract(p->P, p->Tt2, e, p->err, s));
+    AR_TRY(contract(p->P, p->Tt2, &p->Qo, e, p->err, s));
     // G2: W = d o (U^T T~1^T)^T -> P planes
     e.mode = TE_SCALE_SPLIT_T;
     e.planes = p->P.planes;
@@ -581,14 +624,14 @@ ar_status transform_apply(TransformPlan* p, const float* d32, const float* y, DI
     e.ld = p->P.ld;
     e.d = d32;
     e.ldd = n2;
-    AR_TRY(contract(p->Qo, p->Tt1, e, p->err, s));
+    AR_TRY(contract(p->Qo, p->Tt1, &p->P, e, p->err, s));
     // G3: V^T = (W T2^T)^T -> Q planes
     e.mode = TE_SPLIT_T;
     e.planes = p->Qo.planes;
     e.pstride = p->Qo.pstride;
     e.ld = p->Qo.ld;
     e.d = nullptr;
-    AR_TRY(contract(p->P, p->T2, e, p->err, s));
+    AR_TRY(contract(p->P, p->T2, &p->Qo, e, p->err, s));
     // G4: out (=|+= tau) (V^T T1^T)^T
     e.mode = dout == DOUT_STORE ? TE_STORE_T : TE_AXPY_T;
     e.out = out;
@@ -598,7 +641,7 @@ ar_status transform_apply(TransformPlan* p, const float* d32, const float* y, DI
         e.f = f;
         e.sumsq = f ? sumsq : nullptr;
     }
-    AR_TRY(contract(p->Qo, p->T1, e, p->err, s));
+    AR_TRY(contract(p->Qo, p->T1, nullptr, e, p->err, s));
     return AR_OK;
 }
 
