@@ -160,6 +160,20 @@ AR_API const char* ar_status_string(ar_status s);
  * until the next failing call on the same thread. */
 AR_API const char* ar_last_error_detail(void);
 
+/*
+ * Per-kernel-class device timing for benchmarks.  Between ar_profile_begin()
+ * and ar_profile_end(), every kernel the library launches is bracketed by a
+ * CUDA event pair on its launch stream; ar_profile_end() synchronizes those
+ * events and returns, per class, the summed milliseconds and the number of
+ * launches (arrays of nkinds entries, classes beyond nkinds are dropped).
+ * Recording events between kernels serializes them: a profiled run measures
+ * each kernel alone, without the overlap of dependent launches.
+ */
+enum { AR_PROF_STENCIL = 0, AR_PROF_CONTRACTION = 1, AR_PROF_SETUP = 2, AR_PROF_OTHER = 3,
+       AR_PROF_KINDS = 4 };
+AR_API ar_status ar_profile_begin(void);
+AR_API ar_status ar_profile_end(double* ms, unsigned long long* launches, int nkinds);
+
 /* Number of kernels this library has launched in this process (all devices,
  * all threads), for launch accounting by benchmarks. */
 AR_API unsigned long long ar_kernel_launches(void);

@@ -28,7 +28,10 @@ EXPORTS = [
     "ar_blur_apply", "ar_reblur_apply", "ar_symprec_setup", "ar_symprec_solve",
     "ar_symprec_eigenvalues", "ar_symprec_shape", "ar_symprec_destroy", "ar_restore",
     "ar_status_string", "ar_last_error_detail", "ar_version", "ar_kernel_launches",
+    "ar_profile_begin", "ar_profile_end",
 ]
+
+PROF_KINDS = ("stencil", "contraction", "setup", "other")
 
 
 class ARError(RuntimeError):
@@ -72,6 +75,10 @@ def lib() -> ctypes.CDLL:
         for name in ("ar_last_error_detail", "ar_version"):
             getattr(L, name).argtypes = []
             getattr(L, name).restype = ctypes.c_char_p
+        L.ar_profile_begin.argtypes = []
+        L.ar_profile_begin.restype = _i
+        L.ar_profile_end.argtypes = [_vp, _vp, _i]
+        L.ar_profile_end.restype = _i
         L.ar_kernel_launches.argtypes = []
         L.ar_kernel_launches.restype = ctypes.c_ulonglong
         _lib = L
@@ -221,6 +228,20 @@ def ar_restore(g: torch.Tensor, psf, alpha: float, tau: float = 1.0, iters: int 
         ctypes.addressof(best) if want else None,
         _stream(stream)), "ar_restore")
     return x_out, (tr[:iters] if want else None), (best.value if want else None)
+
+
+def ar_profile_begin() -> None:
+    """Start per-kernel-class event timing (see ``ar_profile_end``)."""
+    _check(lib().ar_profile_begin(), "ar_profile_begin")
+
+
+def ar_profile_end() -> dict:
+    """Stop timing; returns ``{class: (milliseconds, launches)}``."""
+    n = len(PROF_KINDS)
+    ms = np.zeros(n, dtype=np.float64)
+    cnt = np.zeros(n, dtype=np.uint64)
+    _check(lib().ar_profile_end(ms.ctypes.data, cnt.ctypes.data, n), "ar_profile_end")
+    return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(PROF_KINDS)}
 
 
 def kernel_launches() -> int:

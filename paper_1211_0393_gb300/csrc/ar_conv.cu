@@ -111,6 +111,7 @@ conv_fast_kernel(const ConvArgs a) {
     const int c0 = blockIdx.x * TX;
     const int kw = 2 * a.q2 + 1;
 
+    pdl_wait();                          // the input image comes from the previous kernel
     for (int i = tid; i < K * K; i += TX * TY) {
         const int b = i / K, aa = i % K;
         const int s1 = aa - Q, s2 = b - Q;      // tap offsets in the padded support
@@ -195,6 +196,7 @@ conv_fast_kernel(const ConvArgs a) {
         }
     }
 
+    pdl_trigger();
     const int col = c0 + tx;
     double sq = 0.0;
     if (col < a.n2) {
@@ -233,15 +235,15 @@ conv_generic_kernel(const ConvArgs a) {
 template <int Q>
 cudaError_t launch_fast(const ConvArgs& a, cudaStream_t s) {
     dim3 grid((a.n2 + TX - 1) / TX, (a.n1 + TH - 1) / TH);
-    conv_fast_kernel<Q><<<grid, dim3(TX, TY), 0, s>>>(a);
     count_launch();
-    return cudaGetLastError();
+    return launch_pdl(conv_fast_kernel<Q>, grid, dim3(TX, TY), 0, s, a);
 }
 
 }  // namespace
 
 ar_status conv_launch(const ConvArgs& a, cudaStream_t s) {
     if (a.n1 <= 0 || a.n2 <= 0) return AR_OK;
+    ProfScope prof(AR_PROF_STENCIL, s);
     const int q = a.q1 > a.q2 ? a.q1 : a.q2;
     cudaError_t e;
     switch (q) {

@@ -9,6 +9,35 @@
 
 namespace ar {
 
+// ------------------------------------------------ programmatic dependent launch
+// Kernels of the iteration are launched with programmatic stream serialization:
+// a kernel may begin (prologue, constant-operand loads) while its predecessor in
+// the stream drains.  pdl_wait() blocks the calling thread until the
+// predecessor grid has completed and its memory operations are visible;
+// pdl_trigger() lets the successor be scheduled.  A kernel triggers only after
+// its own pdl_wait(), so every grid before the predecessor is complete when a
+// kernel starts.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // ---------------------------------------------------------------- errors ---
 // Records a human-readable detail for ar_last_error_detail() and returns s.
 ar_status fail(ar_status s, const char* fmt, ...);
@@ -109,6 +138,17 @@ int sm_count();
 
 // Launch accounting: every kernel launch site calls count_launch(k).
 void count_launch(unsigned k = 1);
+
+// Profiling (ar_profile_begin/end): bracket a launch with prof_begin/prof_end.
+int prof_begin(int kind, cudaStream_t s);
+void prof_end(int idx, cudaStream_t s);
+
+struct ProfScope {
+    int idx;
+    cudaStream_t s;
+    ProfScope(int kind, cudaStream_t st) : idx(prof_begin(kind, st)), s(st) {}
+    ~ProfScope() { prof_end(idx, s); }
+};
 
 }  // namespace ar
 

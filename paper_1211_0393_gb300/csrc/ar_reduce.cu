@@ -56,6 +56,7 @@ unsigned grid_for(size_t n) {
 }  // namespace
 
 ar_status reduce_diff_sq(const float* x, const float* f, size_t n, double* acc, cudaStream_t s) {
+    ProfScope prof(AR_PROF_OTHER, s);
     diff_sq_kernel<<<grid_for(n), RB, 0, s>>>(x, f, n, acc);
     count_launch();
     AR_CUDA(cudaGetLastError());
@@ -63,6 +64,7 @@ ar_status reduce_diff_sq(const float* x, const float* f, size_t n, double* acc, 
 }
 
 ar_status reduce_sq(const float* f, size_t n, double* acc, cudaStream_t s) {
+    ProfScope prof(AR_PROF_OTHER, s);
     diff_sq_kernel<<<grid_for(n), RB, 0, s>>>(f, nullptr, n, acc);
     count_launch();
     AR_CUDA(cudaGetLastError());
@@ -70,6 +72,7 @@ ar_status reduce_sq(const float* f, size_t n, double* acc, cudaStream_t s) {
 }
 
 ar_status count_nonfinite(const float* x, size_t n, unsigned long long* cnt, cudaStream_t s) {
+    ProfScope prof(AR_PROF_OTHER, s);
     nonfinite_kernel<<<grid_for(n), RB, 0, s>>>(x, n, cnt);
     count_launch();
     AR_CUDA(cudaGetLastError());

@@ -83,6 +83,7 @@ ar_status setup_eigen(const double* psf_dev64, int q1, int q2, int n1, int n2, d
     double* s = scratch;
     double* t = s + (size_t)(q1 + 1) * (q2 + 1);
     double* c1 = t + (size_t)(q1 + 1) * n2;
+    ProfScope prof(AR_PROF_SETUP, stream);
     symmetrize_kernel<<<1, 256, 0, stream>>>(psf_dev64, q1, q2, s);
     count_launch();
     AR_CUDA(cudaGetLastError());

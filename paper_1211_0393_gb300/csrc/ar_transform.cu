@@ -169,11 +169,21 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     const uint32_t tmem = *tslot;
 
     if (warp == 0 && lane == 0) {
-        // ---- TMA producer
-        int issued = 0;
-        for (int kb = 0; kb < nk; ++kb) {
+        // ---- TMA producer.  The constant B operand of the first stages is
+        // requested before waiting for the previous kernel, which writes A.
+        const int npre = nk < STAGES ? nk : STAGES;
+        for (int kb = 0; kb < npre; ++kb) {
+            const uint32_t a = base + kb * STAGE_BYTES;
+            mbar_arrive_expect_tx(bars + 8u * kb, STAGE_BYTES);
+            tma_load_3d(a + A_STAGE, &tmB, (kb_begin + kb) * BK, n0, 0, bars + 8u * kb);
+        }
+        pdl_wait();
+        for (int kb = 0; kb < npre; ++kb)
+            tma_load_3d(base + kb * STAGE_BYTES, &tmA, (kb_begin + kb) * BK, m0, 0, bars + 8u * kb);
+        int issued = npre;
+        for (int kb = npre; kb < nk; ++kb) {
             const int s = kb % STAGES;
-            if (kb >= STAGES && !mbar_wait(bars + 8u * (STAGES + s), ((kb / STAGES) & 1) ^ 1)) {
+            if (!mbar_wait(bars + 8u * (STAGES + s), ((kb / STAGES) & 1) ^ 1)) {
                 *sflag = 1;
                 break;
             }
@@ -243,9 +253,11 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         }
     }
 
+    pdl_wait();                          // before this kernel writes what the previous one read
     const bool ready = mbar_wait(done_bar, 0);
     __syncwarp();
     fence_after_sync();
+    pdl_trigger();
     const bool ok = ready && *sflag == 0;
     const int nacc = ok ? (nk < NACC ? nk : NACC) : 0;
     const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
@@ -536,10 +548,10 @@ ar_status contract(const Operand& A, const Operand& B, const Operand* O, const T
     });
     if (attr != cudaSuccess) return cuda_fail(attr, "tc_contract_kernel smem attribute");
     dim3 grid((A.rows + BM - 1) / BM, (B.rows + BN - 1) / BN, SPLITK);
-    tc_contract_kernel<<<grid, NTHREADS, SMEM_BYTES, s>>>(A.map, B.map, O ? O->omap : A.map, A.rows,
-                                                          B.rows, A.K, ep, err);
+    ProfScope prof(AR_PROF_CONTRACTION, s);
     count_launch();
-    AR_CUDA(cudaGetLastError());
+    AR_CUDA(launch_pdl(tc_contract_kernel, grid, dim3(NTHREADS), SMEM_BYTES, s, A.map, B.map,
+                       O ? O->omap : A.map, A.rows, B.rows, A.K, ep, err));
     return AR_OK;
 }
 
@@ -605,6 +617,7 @@ ar_status transform_apply(TransformPlan* p, const float* d32, const float* y, DI
     const int n1 = p->n1, n2 = p->n2;
     if (din == DIN_FP32) {
         const size_t n = (size_t)n1 * n2;
+        ProfScope prof(AR_PROF_OTHER, s);
         split_image_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(y, n1, n2, p->P.ld,
                                                                        p->P.planes, p->P.pstride);
         count_launch();
