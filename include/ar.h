@@ -153,6 +153,36 @@ AR_API ar_status ar_restore(const float* g, const double* psf_host,
                      const float* x0, const float* f_true, float* x_out,
                      double* rre_trace, int* best_iter, void* stream);
 
+/*
+ * Plain Landweber restoration (D = I) that allocates no memory.  The paper has
+ * no counterpart: this entry point exists for callers that cannot let a
+ * library allocate device memory, e.g. a framework that has reserved the
+ * whole GPU for its own pool, or a fixed-budget service that must never call
+ * into the CUDA allocator while it runs.  It computes exactly what
+ * ar_restore(..., precondition = 0, ...) computes, with the same kernels in
+ * the same order, and takes the same arguments except alpha and precondition.
+ *
+ * Its scratch (the residual image, the float32 PSF copy and the float64 RRE
+ * accumulators) lives in one file-scope static device array of about 4.1 MiB
+ * that every GPU loading this library keeps until the process exits; no
+ * cudaMalloc, cudaFree or other allocating routine is called.  Limits:
+ * n1*n2 <= AR_STATIC_MAX_PIXELS, (2q1+1)(2q2+1) <= AR_STATIC_MAX_PSF,
+ * iters <= AR_STATIC_MAX_ITERS; larger requests return AR_ERR_INVALID_ARG
+ * with a detail naming the limit.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current:
+ * make that first call before any stream capture.  All calls on a device
+ * share the array and the call clears what must start at zero; calls whose
+ * GPU work overlaps (different streams or host threads) race.
+ * Synchronizes `stream` before returning.
+ */
+#define AR_STATIC_MAX_PIXELS (1u << 20)
+#define AR_STATIC_MAX_PSF 4096u
+#define AR_STATIC_MAX_ITERS 4096u
+AR_API ar_status ar_restore_plain_static(const float* g, const double* psf_host, int n1, int n2,
+                                         int q1, int q2, double tau, int iters,
+                                         const float* x0, const float* f_true, float* x_out,
+                                         double* rre_trace, int* best_iter, void* stream);
+
 /* Static name of a status code ("AR_OK", ...; "AR_UNKNOWN" otherwise). */
 AR_API const char* ar_status_string(ar_status s);
 

@@ -28,7 +28,7 @@ EXPORTS = [
     "ar_blur_apply", "ar_reblur_apply", "ar_symprec_setup", "ar_symprec_solve",
     "ar_symprec_eigenvalues", "ar_symprec_shape", "ar_symprec_destroy", "ar_restore",
     "ar_status_string", "ar_last_error_detail", "ar_version", "ar_kernel_launches",
-    "ar_profile_begin", "ar_profile_end",
+    "ar_profile_begin", "ar_profile_end", "ar_restore_plain_static",
 ]
 
 PROF_KINDS = ("stencil", "contraction", "setup", "other")
@@ -62,6 +62,8 @@ def lib() -> ctypes.CDLL:
             "ar_symprec_eigenvalues": [_vp, _vp, _vp],
             "ar_symprec_shape": [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)],
             "ar_restore": [_vp, _vp, _i, _i, _i, _i, _d, _d, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp],
+            "ar_restore_plain_static": [_vp, _vp, _i, _i, _i, _i, _d, _i, _vp, _vp, _vp, _vp, _vp,
+                                        _vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -242,6 +244,36 @@ def ar_profile_end() -> dict:
     cnt = np.zeros(n, dtype=np.uint64)
     _check(lib().ar_profile_end(ms.ctypes.data, cnt.ctypes.data, n), "ar_profile_end")
     return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(PROF_KINDS)}
+
+
+def ar_restore_plain_static(g: torch.Tensor, psf, tau: float = 1.0, iters: int = 20,
+                            x0: torch.Tensor | None = None, f_true: torch.Tensor | None = None,
+                            x_out: torch.Tensor | None = None, trace: bool = True, stream=None):
+    """Plain Landweber restoration with no memory allocated by the library.
+
+    Same result as ``ar_restore(..., precondition=False)``; the library's scratch
+    is a static device array (see ``include/ar.h`` for the size limits).  The
+    caller provides ``x_out`` (allocated here only when omitted).
+    """
+    _image(g, "g")
+    h = _host_psf(psf)
+    q1, q2 = _support(h.shape)
+    n1, n2 = g.shape
+    if x_out is None:
+        x_out = torch.empty_like(g)
+    _image(x_out, "x_out")
+    want = f_true is not None and trace
+    tr = np.zeros(max(iters, 1), dtype=np.float64) if want else None
+    best = _i(0)
+    _check(lib().ar_restore_plain_static(
+        g.data_ptr(), h.ctypes.data, n1, n2, q1, q2, float(tau), int(iters),
+        _image(x0, "x0").data_ptr() if x0 is not None else None,
+        _image(f_true, "f_true").data_ptr() if f_true is not None else None,
+        x_out.data_ptr(),
+        tr.ctypes.data if want else None,
+        ctypes.addressof(best) if want else None,
+        _stream(stream)), "ar_restore_plain_static")
+    return x_out, (tr[:iters] if want else None), (best.value if want else None)
 
 
 def kernel_launches() -> int:
