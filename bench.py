@@ -286,14 +286,14 @@ def kernel_rooflines(ar, torch, dev, step):
         ach = contraction_flops / t_ct / 1e12
         roof = {"kernel": "tc_contract_kernel (AR transform contraction, bf16x3, 6 products)",
                 "bound": "tensor", "achieved": round(ach, 2), "peak": bf16, "unit": "TFLOP/s",
-                "frac": round(ach / bf16, 4), "traffic": None,
+                "frac": round(ach / bf16, 4), "traffic": measured_traffic("contraction"),
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; kernel timed alone)",
                 "work_per_launch": "6 x 2 x 1024^3 bf16 flops"}
     else:
         ach = stencil_flops / t_st / 1e12
         roof = {"kernel": "conv_fast_kernel<7> (AR pad + 15x15 convolution)", "bound": "alu",
                 "achieved": round(ach, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
-                "frac": round(ach / fp32_peak, 4), "traffic": None,
+                "frac": round(ach / fp32_peak, 4), "traffic": measured_traffic("stencil"),
                 "peak_source": "derived: SMs x 128 FP32 lanes x 2 x sm_max_mhz of MEASURED_PEAKS.json",
                 "work_per_launch": "2 x 225 x 1024^2 flops"}
     return roof, kernels
@@ -301,6 +301,29 @@ def kernel_rooflines(ar, torch, dev, step):
 
 def ar_psf_shape():
     return W.psf_config2().shape
+
+
+PROFILES = {
+    "contraction": ("profiles/tc_contract_kernel_ellipses1024.md", "paper_1211_0393_gb300/csrc/ar_transform.cu"),
+    "stencil": ("profiles/conv_fast_kernel_q7_ellipses1024.md", "paper_1211_0393_gb300/csrc/ar_conv.cu"),
+}
+
+
+def measured_traffic(kind):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel's source changed since those counters were taken."""
+    import hashlib
+    prof, src = PROFILES[kind]
+    try:
+        text = open(os.path.join(ROOT, prof)).read()
+        fields = dict(line.split(": ", 1) for line in text.splitlines()
+                      if line.startswith(("dram_bytes_per_launch:", "source_sha256_prefix:")))
+        sha = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()
+        if sha.startswith(fields["source_sha256_prefix:".rstrip(":")].strip()):
+            return int(fields["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
 
 
 def quality_vs_plain(ar, torch, g_d, f_d, h):
