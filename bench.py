@@ -239,6 +239,9 @@ def run_own(args):
         }
         if not args.no_quality:
             out["quality"] = quality_vs_plain(ar, torch, g_d, f_d, h)
+            x_ref = x_d.clone()
+            out["forms"] = {"bf16x2": precision_form(ar, torch, stream, g_d, f_d, h, flush,
+                                                     max(args.steps // 2, 3), x_ref)}
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(h, g, f)
     if world > 1:
@@ -324,6 +327,33 @@ def measured_traffic(kind):
     except Exception:
         pass
     return None
+
+
+def precision_form(ar, torch, stream, g_d, f_d, h, flush, steps, x_ref):
+    """The bf16x2 precision mode on the same workload: throughput, the RRE it
+    reaches, and its deviation from the float32-grade iterate after 50 steps."""
+    x_fast = torch.empty_like(g_d)
+
+    def step():
+        return ar.ar_restore(g_d, h, ALPHA, TAU, ITERS, True, f_true=f_d, x_out=x_fast,
+                             precision="bf16x2")
+
+    for _ in range(3):
+        step()
+    tot = 0.0
+    for i in range(steps):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, tr, best = step()
+        b.record(stream)
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    dev_rel = float(torch.linalg.vector_norm(x_fast - x_ref) / torch.linalg.vector_norm(x_ref))
+    return {"precision": "bf16x2 (two bf16 planes, three products)",
+            "value": round(N1 * N2 * ITERS * steps / 1e6 / (tot / 1e3), 2), "unit": UNIT,
+            "ms_per_step": round(tot / steps, 4), "rre_best": round(float(np.min(tr)), 6),
+            "best_iter": best, "rel_l2_vs_fp32_grade_x50": dev_rel}
 
 
 def quality_vs_plain(ar, torch, g_d, f_d, h):

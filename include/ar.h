@@ -54,6 +54,15 @@ typedef enum ar_status {
     AR_ERR_UNSUPPORTED = 8         /* valid request this build cannot serve (e.g. no sm_103a GPU) */
 } ar_status;
 
+/* Arithmetic of the AR transform contractions (tensor cores).
+ *  AR_PRECISION_FP32:   operands split into three bfloat16 planes, the six
+ *                       products with i + j <= 2 accumulated in float32:
+ *                       float32-grade (the default).
+ *  AR_PRECISION_BF16X2: two planes, the three products with i + j <= 1:
+ *                       about 2^-16 relative per contraction, roughly half
+ *                       the tensor work and two thirds of the operand bytes. */
+typedef enum ar_precision { AR_PRECISION_FP32 = 0, AR_PRECISION_BF16X2 = 1 } ar_precision;
+
 /* Opaque preconditioner: the symmetrized-PSF eigenvalues and Tikhonov filter
  * for one (PSF, n1, n2, alpha), plus the AR transform operands and scratch
  * used by ar_symprec_solve.  Owned by the library; free with
@@ -99,6 +108,12 @@ AR_API ar_status ar_reblur_apply(const float* x, float* y, int n1, int n2,
  */
 AR_API ar_status ar_symprec_setup(const double* psf_host, int q1, int q2, int n1, int n2,
                            double alpha, void* stream, ar_prec** out);
+
+/* ar_symprec_setup with an explicit ar_precision for the transform
+ * contractions (ar_symprec_setup uses AR_PRECISION_FP32).  An unknown
+ * precision returns AR_ERR_INVALID_ARG. */
+AR_API ar_status ar_symprec_setup_ex(const double* psf_host, int q1, int q2, int n1, int n2,
+                                     double alpha, int precision, void* stream, ar_prec** out);
 
 /*
  * z = D y = T_n diag(d) T~_n y (Theorem 1 with the filtered eigenvalues).
@@ -182,6 +197,15 @@ AR_API ar_status ar_restore_plain_static(const float* g, const double* psf_host,
                                          int q1, int q2, double tau, int iters,
                                          const float* x0, const float* f_true, float* x_out,
                                          double* rre_trace, int* best_iter, void* stream);
+
+/* ar_restore with an explicit ar_precision for the preconditioner's
+ * contractions (ignored when precondition == 0).  ar_restore is
+ * ar_restore_ex(..., AR_PRECISION_FP32, ...). */
+AR_API ar_status ar_restore_ex(const float* g, const double* psf_host,
+                               int n1, int n2, int q1, int q2, double alpha, double tau,
+                               int iters, int precondition, int precision,
+                               const float* x0, const float* f_true, float* x_out,
+                               double* rre_trace, int* best_iter, void* stream);
 
 /* Static name of a status code ("AR_OK", ...; "AR_UNKNOWN" otherwise). */
 AR_API const char* ar_status_string(ar_status s);

@@ -28,8 +28,11 @@ EXPORTS = [
     "ar_blur_apply", "ar_reblur_apply", "ar_symprec_setup", "ar_symprec_solve",
     "ar_symprec_eigenvalues", "ar_symprec_shape", "ar_symprec_destroy", "ar_restore",
     "ar_status_string", "ar_last_error_detail", "ar_version", "ar_kernel_launches",
-    "ar_profile_begin", "ar_profile_end", "ar_restore_plain_static",
+    "ar_profile_begin", "ar_profile_end", "ar_restore_plain_static", "ar_symprec_setup_ex",
+    "ar_restore_ex",
 ]
+
+PRECISION = {"fp32": 0, "bf16x2": 1}
 
 PROF_KINDS = ("stencil", "contraction", "setup", "other")
 
@@ -58,6 +61,9 @@ def lib() -> ctypes.CDLL:
             "ar_blur_apply": [_vp, _vp, _i, _i, _vp, _i, _i, _vp],
             "ar_reblur_apply": [_vp, _vp, _i, _i, _vp, _i, _i, _vp],
             "ar_symprec_setup": [_vp, _i, _i, _i, _i, _d, _vp, ctypes.POINTER(_vp)],
+            "ar_symprec_setup_ex": [_vp, _i, _i, _i, _i, _d, _i, _vp, ctypes.POINTER(_vp)],
+            "ar_restore_ex": [_vp, _vp, _i, _i, _i, _i, _d, _d, _i, _i, _i, _vp, _vp, _vp, _vp, _vp,
+                              _vp],
             "ar_symprec_solve": [_vp, _vp, _vp, _vp],
             "ar_symprec_eigenvalues": [_vp, _vp, _vp],
             "ar_symprec_shape": [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i)],
@@ -166,13 +172,18 @@ class Prec:
             pass
 
 
-def ar_symprec_setup(psf, n1: int, n2: int, alpha: float, stream=None) -> Prec:
-    """Build the symmetrized-PSF AR preconditioner (float64 setup on the GPU)."""
+def ar_symprec_setup(psf, n1: int, n2: int, alpha: float, stream=None,
+                     precision: str = "fp32") -> Prec:
+    """Build the symmetrized-PSF AR preconditioner (float64 setup on the GPU).
+
+    ``precision``: "fp32" (three bf16 planes, six products) or "bf16x2" (two
+    planes, three products) for the transform contractions."""
     h = _host_psf(psf)
     q1, q2 = _support(h.shape)
     out = _vp()
-    _check(lib().ar_symprec_setup(h.ctypes.data, q1, q2, n1, n2, float(alpha), _stream(stream),
-                                  ctypes.byref(out)), "ar_symprec_setup")
+    _check(lib().ar_symprec_setup_ex(h.ctypes.data, q1, q2, n1, n2, float(alpha),
+                                     PRECISION[precision], _stream(stream), ctypes.byref(out)),
+           "ar_symprec_setup_ex")
     return Prec(out.value, n1, n2)
 
 
@@ -208,7 +219,7 @@ def ar_symprec_shape(P: Prec) -> tuple[int, int]:
 def ar_restore(g: torch.Tensor, psf, alpha: float, tau: float = 1.0, iters: int = 20,
                precondition: bool = True, x0: torch.Tensor | None = None,
                f_true: torch.Tensor | None = None, x_out: torch.Tensor | None = None,
-               trace: bool = True, stream=None):
+               trace: bool = True, stream=None, precision: str = "fp32"):
     """(D-)Landweber restoration.  Returns ``(x, rre_trace or None, best_iter or None)``."""
     _image(g, "g")
     h = _host_psf(psf)
@@ -220,9 +231,9 @@ def ar_restore(g: torch.Tensor, psf, alpha: float, tau: float = 1.0, iters: int 
     want = f_true is not None and trace
     tr = np.zeros(max(iters, 1), dtype=np.float64) if want else None
     best = _i(0)
-    _check(lib().ar_restore(
+    _check(lib().ar_restore_ex(
         g.data_ptr(), h.ctypes.data, n1, n2, q1, q2, float(alpha), float(tau), int(iters),
-        1 if precondition else 0,
+        1 if precondition else 0, PRECISION[precision],
         _image(x0, "x0").data_ptr() if x0 is not None else None,
         _image(f_true, "f_true").data_ptr() if f_true is not None else None,
         x_out.data_ptr(),

@@ -141,7 +141,7 @@ ar_status apply_common(const float* x, float* y, int n1, int n2, const float* ps
 
 // Builds the preconditioner's device data on `s` without synchronizing.
 ar_status prec_build(const double* psf_host, int q1, int q2, int n1, int n2, double alpha,
-                     cudaStream_t s, bool keep64, ar_prec** out) {
+                     int precision, cudaStream_t s, bool keep64, ar_prec** out) {
     set_pool_threshold_once();
     ar_prec* P = new (std::nothrow) ar_prec();
     if (!P) return fail(AR_ERR_ALLOC, "host allocation of ar_prec");
@@ -151,6 +151,7 @@ ar_status prec_build(const double* psf_host, int q1, int q2, int n1, int n2, dou
     P->q1 = q1;
     P->q2 = q2;
     P->alpha = alpha;
+    P->precision = precision;
     cudaGetDevice(&P->device);
     const size_t n = (size_t)n1 * n2;
     const size_t k = (size_t)(2 * q1 + 1) * (2 * q2 + 1);
@@ -174,7 +175,7 @@ ar_status prec_build(const double* psf_host, int q1, int q2, int n1, int n2, dou
         if (st == AR_OK && cudaMallocAsync((void**)&P->d32, n * sizeof(float), s) != cudaSuccess)
             st = fail(AR_ERR_ALLOC, "filter buffer");
         if (st == AR_OK) st = setup_eigen(h64, q1, q2, n1, n2, alpha, P->lam64, P->d64, P->d32, work, s);
-        if (st == AR_OK) st = transform_plan_create(n1, n2, s, &P->plan);
+        if (st == AR_OK) st = transform_plan_create(n1, n2, precision, s, &P->plan);
     }
     if (st != AR_OK) {
         ar_symprec_destroy(P);
@@ -221,7 +222,14 @@ ar_status ar_reblur_apply(const float* x, float* y, int n1, int n2, const float*
 
 ar_status ar_symprec_setup(const double* psf_host, int q1, int q2, int n1, int n2, double alpha,
                            void* stream, ar_prec** out) {
+    return ar_symprec_setup_ex(psf_host, q1, q2, n1, n2, alpha, AR_PRECISION_FP32, stream, out);
+}
+
+ar_status ar_symprec_setup_ex(const double* psf_host, int q1, int q2, int n1, int n2, double alpha,
+                              int precision, void* stream, ar_prec** out) {
     if (!psf_host || !out) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
+    if (precision != AR_PRECISION_FP32 && precision != AR_PRECISION_BF16X2)
+        return fail(AR_ERR_INVALID_ARG, "unknown precision %d", precision);
     AR_TRY(check_image_sizes(n1, n2, 3));
     AR_TRY(check_support(n1, n2, q1, q2, 3));
     if (!(alpha > 0.0) || !std::isfinite(alpha))
@@ -229,7 +237,7 @@ ar_status ar_symprec_setup(const double* psf_host, int q1, int q2, int n1, int n
     AR_TRY(check_psf_host(psf_host, q1, q2));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     ar_prec* P = nullptr;
-    AR_TRY(prec_build(psf_host, q1, q2, n1, n2, alpha, s, true, &P));
+    AR_TRY(prec_build(psf_host, q1, q2, n1, n2, alpha, precision, s, true, &P));
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         ar_symprec_destroy(P);
@@ -277,7 +285,17 @@ ar_status ar_restore(const float* g, const double* psf_host, int n1, int n2, int
                      double alpha, double tau, int iters, int precondition, const float* x0,
                      const float* f_true, float* x_out, double* rre_trace, int* best_iter,
                      void* stream) {
+    return ar_restore_ex(g, psf_host, n1, n2, q1, q2, alpha, tau, iters, precondition,
+                         AR_PRECISION_FP32, x0, f_true, x_out, rre_trace, best_iter, stream);
+}
+
+ar_status ar_restore_ex(const float* g, const double* psf_host, int n1, int n2, int q1, int q2,
+                        double alpha, double tau, int iters, int precondition, int precision,
+                        const float* x0, const float* f_true, float* x_out, double* rre_trace,
+                        int* best_iter, void* stream) {
     if (!g || !psf_host || !x_out) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
+    if (precision != AR_PRECISION_FP32 && precision != AR_PRECISION_BF16X2)
+        return fail(AR_ERR_INVALID_ARG, "unknown precision %d", precision);
     const bool pc = precondition != 0;
     AR_TRY(check_image_sizes(n1, n2, pc ? 3 : 1));
     AR_TRY(check_support(n1, n2, q1, q2, pc ? 3 : 1));
@@ -327,7 +345,8 @@ ar_status ar_restore(const float* g, const double* psf_host, int n1, int n2, int
             }
             if (e != cudaSuccess) st = cuda_fail(e, "restore initialisation");
         }
-        if (st == AR_OK && pc) st = prec_build(psf_host, q1, q2, n1, n2, alpha, s, false, &P);
+        if (st == AR_OK && pc)
+            st = prec_build(psf_host, q1, q2, n1, n2, alpha, precision, s, false, &P);
         if (st == AR_OK && f_true) st = reduce_sq(f_true, n, dsum + iters, s);
 
         ConvArgs blur{};

@@ -88,7 +88,10 @@ ar_status conv_launch(const ConvArgs& a, cudaStream_t stream);
 // contractions.  Implemented in ar_transform.cu.
 struct TransformPlan;
 
-ar_status transform_plan_create(int n1, int n2, cudaStream_t stream, TransformPlan** out);
+// precision: AR_PRECISION_FP32 (three bf16 planes, six products) or
+// AR_PRECISION_BF16X2 (two planes, three products).
+ar_status transform_plan_create(int n1, int n2, int precision, cudaStream_t stream,
+                                TransformPlan** out);
 void transform_plan_destroy(TransformPlan* p);
 
 // Where the input of D comes from.
@@ -155,6 +158,7 @@ struct ProfScope {
 struct ar_prec {
     int n1, n2, q1, q2;
     double alpha;
+    int precision;
     int device;
     double* lam64;
     double* d64;

@@ -50,12 +50,10 @@
 namespace ar {
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 2, PLANES = 3;
+constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int MAX_PLANES = 3;                             // operand buffers hold three bf16 planes
 constexpr uint32_t A_PLANE = BM * BK * 2;                 // 16 KiB
 constexpr uint32_t B_PLANE = BN * BK * 2;                 // 16 KiB
-constexpr uint32_t A_STAGE = PLANES * A_PLANE;
-constexpr uint32_t B_STAGE = PLANES * B_PLANE;
-constexpr uint32_t STAGE_BYTES = A_STAGE + B_STAGE;      // 96 KiB
 // Split-K over the two CTAs of a cluster: CTA r accumulates its half of the
 // k-blocks, then finishes columns [r*HALF, (r+1)*HALF) of the tile after
 // receiving the peer's partial sums for them through distributed shared memory.
@@ -68,12 +66,31 @@ constexpr uint32_t RECV_BYTES = HALF * BM * 4;            // 32 KiB, column-majo
 // per accumulator keep a K = 1024 contraction at float32-grade accuracy.
 constexpr int NACC = 4;
 constexpr uint32_t TMEM_COLS = NACC * BN;                 // 512: the whole TMEM of the SM
-constexpr uint32_t CTRL_BYTES = 8 * (2 * STAGES + 1) + 16;
-constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + RECV_BYTES + CTRL_BYTES + 1024;
 
-// The six split products (a plane, b plane), smallest first.
-__constant__ int kPA[6] = {2, 1, 0, 1, 0, 0};
-__constant__ int kPB[6] = {0, 1, 2, 0, 1, 0};
+// Precision modes.  NP = 3: three bf16 planes per operand, the six products
+// a_i b_j with i + j <= 2 (float32-grade).  NP = 2: two planes, the three
+// products with i + j <= 1 (about 2^-16 relative; the smaller stages leave
+// room for a third pipeline stage).
+template <int NP>
+struct TcMode {
+    static constexpr int PLANES = NP;
+    static constexpr int NPROD = NP == 3 ? 6 : 3;
+    static constexpr int STAGES = NP == 3 ? 2 : 3;
+    static constexpr uint32_t A_STAGE = PLANES * A_PLANE;
+    static constexpr uint32_t B_STAGE = PLANES * B_PLANE;
+    static constexpr uint32_t STAGE_BYTES = A_STAGE + B_STAGE;   // 96 KiB / 64 KiB
+    static constexpr uint32_t CTRL_BYTES = 8 * (2 * STAGES + 1) + 16;
+    static constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + RECV_BYTES + CTRL_BYTES + 1024;
+    // product t uses plane pa(t) of A and pb(t) of B, smallest terms first
+    __host__ __device__ static constexpr int pa(int t) {
+        return NP == 3 ? (t == 0 ? 2 : t == 1 ? 1 : t == 2 ? 0 : t == 3 ? 1 : 0) : (t == 0 ? 1 : 0);
+    }
+    __host__ __device__ static constexpr int pb(int t) {
+        return NP == 3 ? (t == 0 ? 0 : t == 1 ? 1 : t == 2 ? 2 : t == 3 ? 0 : t == 4 ? 1 : 0)
+                       : (t == 1 ? 1 : 0);
+    }
+};
+static_assert(TcMode<3>::SMEM_BYTES <= 232448 && TcMode<2>::SMEM_BYTES <= 232448, "smem budget");
 
 enum TcEpi : int { TE_SPLIT_T = 0, TE_SCALE_SPLIT_T = 1, TE_STORE_T = 2, TE_AXPY_T = 3 };
 
@@ -120,11 +137,16 @@ __device__ __forceinline__ void acc_sum16(uint32_t trow, int col0, int nacc, flo
 constexpr int NTHREADS = 256;           // 8 warps: two per TMEM lane quarter in the epilogue
 constexpr int WCOLS = HALF / 2;         // columns of the CTA's half handled by one warp
 
+template <int NP>
 __global__ void __cluster_dims__(1, 1, SPLITK) __launch_bounds__(NTHREADS, 1)
 tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmO, int M, int N, int K, const TcEpiArgs ep,
                    int* err) {
     using namespace tc;
+    using Mode = TcMode<NP>;
+    constexpr int STAGES = Mode::STAGES;
+    constexpr uint32_t A_STAGE = Mode::A_STAGE;
+    constexpr uint32_t STAGE_BYTES = Mode::STAGE_BYTES;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;         // 128B-swizzled tiles need 1 KiB alignment
@@ -136,7 +158,7 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     uint32_t* tslot = reinterpret_cast<uint32_t*>(gbase + STAGES * STAGE_BYTES + RECV_BYTES +
                                                   8 * (2 * STAGES + 1));
     volatile int* sflag = reinterpret_cast<volatile int*>(tslot + 1);
-    // after the main loop the stage area stages the bf16x3 output tile [3][HALF][BM]
+    // after the main loop the stage area stages the split output tile [NP][HALF][BM]
     uint16_t* stage_out = reinterpret_cast<uint16_t*>(gbase);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -213,9 +235,9 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
 #pragma unroll
-                for (int t = 0; t < 6; ++t) {
-                    const uint64_t ad = desc_k_sw128(a + kPA[t] * A_PLANE + kk * 32);
-                    const uint64_t bd = desc_k_sw128(b + kPB[t] * B_PLANE + kk * 32);
+                for (int t = 0; t < Mode::NPROD; ++t) {
+                    const uint64_t ad = desc_k_sw128(a + Mode::pa(t) * A_PLANE + kk * 32);
+                    const uint64_t bd = desc_k_sw128(b + Mode::pb(t) * B_PLANE + kk * 32);
                     mma_bf16(d, ad, bd, idesc, (kb >= NACC || kk != 0 || t != 0) ? 1u : 0u);
                 }
             }
@@ -292,7 +314,7 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 split3(x, h0, h1, h2);
                 stage_out[(0 * HALF + hc) * BM + lrow] = h0;
                 stage_out[(1 * HALF + hc) * BM + lrow] = h1;
-                stage_out[(2 * HALF + hc) * BM + lrow] = h2;
+                if (NP == 3) stage_out[(2 * HALF + hc) * BM + lrow] = h2;
             } else if (ok && row < M && n0 + ocol0 + jj < N) {
                 const size_t o = (size_t)(n0 + ocol0 + jj) * ep.ldo + row;
                 if (ep.mode == TE_STORE_T) {
@@ -314,7 +336,7 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         if (lane == 0 && sq != 0.0) atomicAdd(ep.sumsq, sq);
     }
     if (split_out) {
-        // the staged [3][HALF][BM] tile leaves in one TMA store (rows past M and
+        // the staged [NP][HALF][BM] tile leaves in one TMA store (rows past M and
         // columns past N are clipped by the tensor map)
         fence_proxy_async_smem();
         __syncthreads();
@@ -447,12 +469,12 @@ int round_up8(int v) { return (v + 7) & ~7; }
 // 3D map over bf16x3 planes {K (inner), rows, 3 planes} with box
 // {box_k, box_rows, 3}: 128-byte swizzle for operand loads, none for stores.
 ar_status make_map(CUtensorMap* map, const uint16_t* planes, int K, int rows, int ld, int box_k,
-                   int box_rows, bool swizzle) {
+                   int box_rows, int nplanes, bool swizzle) {
     auto enc = encode_fn();
     if (!enc) return fail(AR_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
-    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)PLANES};
+    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)nplanes};
     cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)rows * ld * 2};
-    cuuint32_t box[3] = {(cuuint32_t)box_k, (cuuint32_t)box_rows, (cuuint32_t)PLANES};
+    cuuint32_t box[3] = {(cuuint32_t)box_k, (cuuint32_t)box_rows, (cuuint32_t)nplanes};
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(planes), dims,
                      strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -462,13 +484,15 @@ ar_status make_map(CUtensorMap* map, const uint16_t* planes, int K, int rows, in
     return AR_OK;
 }
 
-struct Operand {               // bf16x3 planes of a rows x K matrix and its TMA maps
+struct Operand {               // bf16 planes of a rows x K matrix and its TMA maps
     uint16_t* planes = nullptr;
     int rows = 0, K = 0, ld = 0;
     size_t pstride = 0;
-    CUtensorMap map;           // operand loads: box {BK, box_rows, 3}, 128B swizzle
-    CUtensorMap omap;          // epilogue stores (image operands): box {BM, HALF, 3}
+    CUtensorMap map[2];        // operand loads, [0]: 3 planes, [1]: 2 planes; box {BK, box_rows, np}, 128B swizzle
+    CUtensorMap omap[2];       // epilogue stores (image operands): box {BM, HALF, np}
 };
+
+inline int mode_index(int np) { return np == 3 ? 0 : 1; }
 
 ar_status alloc_operand(Operand& o, int rows, int K, int box_rows, cudaStream_t s,
                         bool permanent = false) {
@@ -476,11 +500,14 @@ ar_status alloc_operand(Operand& o, int rows, int K, int box_rows, cudaStream_t 
     o.K = K;
     o.ld = round_up8(K);
     o.pstride = (size_t)rows * o.ld;
-    const size_t bytes = PLANES * o.pstride * sizeof(uint16_t);
+    const size_t bytes = MAX_PLANES * o.pstride * sizeof(uint16_t);
     if (permanent) AR_CUDA(cudaMalloc((void**)&o.planes, bytes));
     else AR_CUDA(cudaMallocAsync((void**)&o.planes, bytes, s));
-    AR_TRY(make_map(&o.map, o.planes, K, rows, o.ld, BK, box_rows, true));
-    if (!permanent) AR_TRY(make_map(&o.omap, o.planes, K, rows, o.ld, BM, HALF, false));
+    for (int np = 3; np >= 2; --np) {
+        AR_TRY(make_map(&o.map[mode_index(np)], o.planes, K, rows, o.ld, BK, box_rows, np, true));
+        if (!permanent)
+            AR_TRY(make_map(&o.omap[mode_index(np)], o.planes, K, rows, o.ld, BM, HALF, np, false));
+    }
     return AR_OK;
 }
 
@@ -537,39 +564,50 @@ ar_status cached_transforms(int m, cudaStream_t s, TransformPair* out) {
     return AR_OK;
 }
 
-// C = A B^T with the epilogue `ep`; O receives the split output planes.
-ar_status contract(const Operand& A, const Operand& B, const Operand* O, const TcEpiArgs& ep,
-                   int* err, cudaStream_t s) {
+template <int NP>
+ar_status contract_np(const Operand& A, const Operand& B, const Operand* O, const TcEpiArgs& ep,
+                      int* err, cudaStream_t s) {
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] {
-        attr = cudaFuncSetAttribute(tc_contract_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)SMEM_BYTES);
+        attr = cudaFuncSetAttribute(tc_contract_kernel<NP>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)TcMode<NP>::SMEM_BYTES);
     });
     if (attr != cudaSuccess) return cuda_fail(attr, "tc_contract_kernel smem attribute");
     dim3 grid((A.rows + BM - 1) / BM, (B.rows + BN - 1) / BN, SPLITK);
     ProfScope prof(AR_PROF_CONTRACTION, s);
+    const int mi = mode_index(NP);
     count_launch();
-    AR_CUDA(launch_pdl(tc_contract_kernel, grid, dim3(NTHREADS), SMEM_BYTES, s, A.map, B.map,
-                       O ? O->omap : A.map, A.rows, B.rows, A.K, ep, err));
+    AR_CUDA(launch_pdl(tc_contract_kernel<NP>, grid, dim3(NTHREADS), (size_t)TcMode<NP>::SMEM_BYTES,
+                       s, A.map[mi], B.map[mi], O ? O->omap[mi] : A.map[mi], A.rows, B.rows, A.K,
+                       ep, err));
     return AR_OK;
+}
+
+// C = A B^T with the epilogue `ep`; O receives the split output planes.
+ar_status contract(int np, const Operand& A, const Operand& B, const Operand* O,
+                   const TcEpiArgs& ep, int* err, cudaStream_t s) {
+    return np == 2 ? contract_np<2>(A, B, O, ep, err, s) : contract_np<3>(A, B, O, ep, err, s);
 }
 
 }  // namespace
 
 struct TransformPlan {
     int n1, n2;
+    int np;                    // bf16 planes per operand: 3 (float32-grade) or 2 (fast)
     Operand Tt1, T1, Tt2, T2;  // constant operands (B side), owned by the process-wide cache
     Operand P;                 // n1 x n2 images: Y, then W          (A side)
     Operand Qo;                // n2 x n1 images: U^T, then V^T      (A side)
     int* err = nullptr;
 };
 
-ar_status transform_plan_create(int n1, int n2, cudaStream_t s, TransformPlan** out) {
+ar_status transform_plan_create(int n1, int n2, int precision, cudaStream_t s, TransformPlan** out) {
     TransformPlan* p = new (std::nothrow) TransformPlan();
     if (!p) return fail(AR_ERR_ALLOC, "host allocation of the transform plan");
     p->n1 = n1;
     p->n2 = n2;
+    p->np = precision == AR_PRECISION_BF16X2 ? 2 : 3;
     TransformPair t1, t2;
     ar_status st = cached_transforms(n1, s, &t1);
     if (st == AR_OK) st = cached_transforms(n2, s, &t2);
@@ -629,7 +667,7 @@ ar_status transform_apply(TransformPlan* p, const float* d32, const float* y, DI
     e.planes = p->Qo.planes;
     e.pstride = p->Qo.pstride;
     e.ld = p->Qo.ld;
-    AR_TRY(contract(p->P, p->Tt2, &p->Qo, e, p->err, s));
+    AR_TRY(contract(p->np, p->P, p->Tt2, &p->Qo, e, p->err, s));
     // G2: W = d o (U^T T~1^T)^T -> P planes
     e.mode = TE_SCALE_SPLIT_T;
     e.planes = p->P.planes;
@@ -637,14 +675,14 @@ ar_status transform_apply(TransformPlan* p, const float* d32, const float* y, DI
     e.ld = p->P.ld;
     e.d = d32;
     e.ldd = n2;
-    AR_TRY(contract(p->Qo, p->Tt1, &p->P, e, p->err, s));
+    AR_TRY(contract(p->np, p->Qo, p->Tt1, &p->P, e, p->err, s));
     // G3: V^T = (W T2^T)^T -> Q planes
     e.mode = TE_SPLIT_T;
     e.planes = p->Qo.planes;
     e.pstride = p->Qo.pstride;
     e.ld = p->Qo.ld;
     e.d = nullptr;
-    AR_TRY(contract(p->P, p->T2, &p->Qo, e, p->err, s));
+    AR_TRY(contract(p->np, p->P, p->T2, &p->Qo, e, p->err, s));
     // G4: out (=|+= tau) (V^T T1^T)^T
     e.mode = dout == DOUT_STORE ? TE_STORE_T : TE_AXPY_T;
     e.out = out;
@@ -654,7 +692,7 @@ ar_status transform_apply(TransformPlan* p, const float* d32, const float* y, DI
         e.f = f;
         e.sumsq = f ? sumsq : nullptr;
     }
-    AR_TRY(contract(p->Qo, p->T1, nullptr, e, p->err, s));
+    AR_TRY(contract(p->np, p->Qo, p->T1, nullptr, e, p->err, s));
     return AR_OK;
 }
 

@@ -11,6 +11,9 @@ Tolerances (derived from the arithmetic; see the design notes):
   TikFilter amplifies them by up to max(d) = 1/alpha against the d ~ 1 signal
   band, so rel-L2 <= tol(alpha) = max(1e-5, 3 u / alpha) per iterate: 1e-5 for
   alpha >= 0.018, 1.8e-5 at alpha = 0.01.
+* the bf16x2 precision mode (two planes, three products) keeps 16 significant
+  bits per operand: the same argument with u = 2^-16 gives
+  tol_fast(alpha) = max(1e-4, 3 * 2^-16 / alpha).
 """
 
 import numpy as np
@@ -38,10 +41,16 @@ def rel_l2(a, b):
 
 
 U32 = 2.0 ** -24
+U_BF16X2 = 2.0 ** -16     # two bf16 planes keep 16 significant bits; the a1*b1 product is dropped
 
 
 def tol_alpha(alpha):
     return max(1e-5, 3 * U32 / alpha)
+
+
+def tol_fast(alpha):
+    """Same derivation as tol_alpha with the two-plane split's unit 2^-16."""
+    return max(1e-4, 3 * U_BF16X2 / alpha)
 
 
 def dev(a):
@@ -232,3 +241,48 @@ def test_restore_rejects_unnormalized_psf(ar):
     with pytest.raises(ar.ARError) as ei:
         ar.ar_restore(g, h, 0.03, 1.0, 2, True)
     assert ei.value.name == "AR_ERR_PSF_NOT_NORMALIZED"
+
+
+FAST_SOLVE_CASES = [(64, 64, 4, 4, 0.03), (130, 257, 7, 7, 0.3), (1024, 1024, 7, 7, 0.3), (9, 8, 2, 1, 0.1)]
+
+
+@pytest.mark.parametrize("n1,n2,q1,q2,alpha", FAST_SOLVE_CASES)
+def test_solve_bf16x2_mode_matches_oracle(ar, n1, n2, q1, q2, alpha):
+    rng = np.random.default_rng(n1 + 3 * n2 + q1)
+    h = rand_psf(rng, q1, q2)
+    y = rng.standard_normal((n1, n2)).astype(np.float32)
+    P = ar.ar_symprec_setup(h, n1, n2, alpha, precision="bf16x2")
+    z = ar.ar_symprec_solve(P, dev(y)).cpu().numpy()
+    want = O.symprec_solve(O.symprec_setup(h, n1, n2, alpha), y.astype(np.float64))
+    err = rel_l2(z, want)
+    assert err <= tol_fast(alpha)
+    # the fast mode is really a different (coarser) arithmetic than the default
+    P3 = ar.ar_symprec_setup(h, n1, n2, alpha)
+    z3 = ar.ar_symprec_solve(P3, dev(y)).cpu().numpy()
+    assert rel_l2(z3, want) <= tol_alpha(alpha)
+    P.close()
+    P3.close()
+
+
+@pytest.mark.parametrize("n,psf,scene,cidx,nu,alpha,iters", [
+    (64, "config1", "blocks", 0, 0.01, 0.03, 20),
+    (200, "config2", "ellipses", 1, 0.005, 0.3, 10),
+])
+def test_restore_bf16x2_mode_matches_oracle(ar, n, psf, scene, cidx, nu, alpha, iters):
+    h = W.psf_named(psf)
+    g, f = _workload(n, h, scene, cidx, nu)
+    x, tr, best = ar.ar_restore(dev(g), h, alpha, 1.0, iters, True, f_true=dev(f),
+                                precision="bf16x2")
+    xo, to, bo = O.restore(g.astype(np.float64), h, alpha, 1.0, iters, True,
+                           f_true=f.astype(np.float64))
+    tol = tol_fast(alpha)
+    assert rel_l2(x.cpu().numpy(), xo) <= tol
+    np.testing.assert_allclose(tr, to, rtol=tol)
+
+
+def test_unknown_precision_is_rejected(ar):
+    import ctypes
+    h = np.ascontiguousarray(W.psf_config1())
+    out = ctypes.c_void_p()
+    st = ar.lib().ar_symprec_setup_ex(h.ctypes.data, 4, 4, 16, 16, 0.1, 7, None, ctypes.byref(out))
+    assert st == 1 and out.value is None
