@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-quality", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
 
@@ -242,6 +243,8 @@ def run_own(args):
             x_ref = x_d.clone()
             out["forms"] = {"bf16x2": precision_form(ar, torch, stream, g_d, f_d, h, flush,
                                                      max(args.steps // 2, 3), x_ref)}
+            if not args.no_batch:
+                out["forms"]["batched"] = batched_form(ar, torch, dev, stream, flush, 3)
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(h, g, f)
     if world > 1:
@@ -354,6 +357,65 @@ def precision_form(ar, torch, stream, g_d, f_d, h, flush, steps, x_ref):
             "value": round(N1 * N2 * ITERS * steps / 1e6 / (tot / 1e3), 2), "unit": UNIT,
             "ms_per_step": round(tot / steps, 4), "rre_best": round(float(np.min(tr)), 6),
             "best_iter": best, "rel_l2_vs_fp32_grade_x50": dev_rel}
+
+
+BATCH_COUNT = 96
+BATCH_ALPHA = 1.0     # |h^| <= 1 for a non-negative unit-sum PSF: alpha >= 0.5 keeps tau = 1 stable for any PSF
+
+
+def batched_form(ar, torch, dev, stream, flush, runs):
+    """The uneven-batch workload (96 images, sides from {128..1024} per axis,
+    own PSF each, 0.5% noise): one CUDA-graph launch per restoration of the whole
+    batch, against restoring the same images one by one with ar_restore."""
+    specs = W.batch_specs(BATCH_COUNT)
+    ims = []
+    for sp in specs:
+        ext, f, e = W.batch_inputs(sp)
+        h = sp["psf"]
+        q1, q2 = (h.shape[0] - 1) // 2, (h.shape[1] - 1) // 2
+        blurred = ar.ar_blur_apply(torch.from_numpy(ext.astype(np.float32)).to(dev),
+                                   torch.from_numpy(h.astype(np.float32)).to(dev))
+        g = W.add_noise(W.crop(blurred.cpu().numpy().astype(np.float64), q1, q2), e, NU)
+        ims.append({"g": torch.from_numpy(g.astype(np.float32)).to(dev), "psf": h,
+                    "alpha": BATCH_ALPHA, "f_true": torch.from_numpy(f.astype(np.float32)).to(dev),
+                    "x_out": torch.empty(sp["n1"], sp["n2"], device=dev)})
+    mpx_iter = sum(im["g"].numel() for im in ims) * ITERS / 1e6
+    t0 = time.perf_counter()
+    B = ar.Batch(ims, tau=TAU, iters=ITERS, precondition=True, concurrency=16)
+    t_create = time.perf_counter() - t0
+
+    def timed(fn):
+        tot = 0.0
+        for i in range(runs):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / runs
+
+    B.run()
+    B.results()
+    t_batch = timed(B.run)
+    tr, best, kpr = B.results()
+    xb = [im["x_out"].clone() for im in ims]
+    t_seq = timed(lambda: [ar.ar_restore(im["g"], im["psf"], im["alpha"], TAU, ITERS, True,
+                                         f_true=im["f_true"], x_out=im["x_out"], trace=False)
+                           for im in ims])
+    same = all(torch.equal(a, im["x_out"]) for a, im in zip(xb, ims))
+    B.close()
+    return {"workload": f"{BATCH_COUNT} images, sides from {list(W.BATCH_SIDES)} per axis, own "
+                        f"PSF 5x5..31x31 each, alpha {BATCH_ALPHA}, {ITERS} iterations",
+            "total_mpixel": round(mpx_iter / ITERS, 3),
+            "batched": {"value": round(mpx_iter / (t_batch / 1e3), 2), "unit": UNIT,
+                        "ms_per_batch": round(t_batch, 3), "kernels_per_run": kpr,
+                        "plan_create_s": round(t_create, 2)},
+            "sequential": {"value": round(mpx_iter / (t_seq / 1e3), 2), "unit": UNIT,
+                           "ms_per_batch": round(t_seq, 3)},
+            "speedup": round(t_seq / t_batch, 2), "identical_results": bool(same),
+            "median_best_iter": int(np.median(best))}
 
 
 def quality_vs_plain(ar, torch, g_d, f_d, h):

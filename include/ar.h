@@ -207,6 +207,43 @@ AR_API ar_status ar_restore_ex(const float* g, const double* psf_host,
                                const float* x0, const float* f_true, float* x_out,
                                double* rre_trace, int* best_iter, void* stream);
 
+/*
+ * Batched restoration of many independent images (each with its own size,
+ * PSF and alpha).  ar_batch_create builds every image's preconditioner
+ * (as ar_symprec_setup) and scratch, then captures the whole restoration of
+ * every image -- x_0 = 0, `iters` iterations of eq. DLandweberMeth with the
+ * reblurred A' (plain Landweber when precondition == 0), the RRE of every
+ * iterate when f_true is given -- into one CUDA graph whose per-image kernel
+ * chains run on `concurrency` (1..64) parallel branches.  The images' device
+ * pointers are bound at creation and must stay valid for the life of the plan.
+ * Creation synchronizes `stream`.  ar_batch_run launches the graph on
+ * `stream` (asynchronous: every x_out is overwritten); ar_batch_results waits
+ * for the last run and copies the RRE traces (count x iters doubles, may be
+ * NULL), the best iterations (count ints, may be NULL) and the number of
+ * kernels one run launches.  Results of a run equal those of ar_restore_ex
+ * with the same arguments, image by image.
+ * Errors: AR_ERR_INVALID_ARG (item index in the detail), AR_ERR_ALIAS (an
+ * output overlapping any input or output of the batch),
+ * AR_ERR_PSF_NOT_NORMALIZED, AR_ERR_ALLOC, AR_ERR_CUDA; ar_batch_results:
+ * AR_ERR_NONFINITE, AR_ERR_TIMEOUT.
+ */
+typedef struct ar_batch_item {
+    const float* g;            /* device n1*n2 observed image */
+    const double* psf_host;    /* host (2q1+1)*(2q2+1) PSF summing to 1 */
+    int n1, n2, q1, q2;
+    double alpha;              /* Tikhonov parameter (> 0 when preconditioned) */
+    const float* f_true;       /* device n1*n2 true image or NULL */
+    float* x_out;              /* device n1*n2 result */
+} ar_batch_item;
+typedef struct ar_batch ar_batch;
+AR_API ar_status ar_batch_create(const ar_batch_item* items, int count, double tau, int iters,
+                                 int precondition, int precision, int concurrency, void* stream,
+                                 ar_batch** out);
+AR_API ar_status ar_batch_run(ar_batch* B, void* stream);
+AR_API ar_status ar_batch_results(ar_batch* B, double* rre_traces, int* best_iters,
+                                  unsigned long long* kernels_per_run);
+AR_API void ar_batch_destroy(ar_batch* B);
+
 /* Static name of a status code ("AR_OK", ...; "AR_UNKNOWN" otherwise). */
 AR_API const char* ar_status_string(ar_status s);
 

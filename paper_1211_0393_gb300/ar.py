@@ -29,8 +29,15 @@ EXPORTS = [
     "ar_symprec_eigenvalues", "ar_symprec_shape", "ar_symprec_destroy", "ar_restore",
     "ar_status_string", "ar_last_error_detail", "ar_version", "ar_kernel_launches",
     "ar_profile_begin", "ar_profile_end", "ar_restore_plain_static", "ar_symprec_setup_ex",
-    "ar_restore_ex",
+    "ar_restore_ex", "ar_batch_create", "ar_batch_run", "ar_batch_results", "ar_batch_destroy",
 ]
+
+
+class BatchItem(ctypes.Structure):
+    """Mirror of ``ar_batch_item``."""
+    _fields_ = [("g", ctypes.c_void_p), ("psf_host", ctypes.c_void_p), ("n1", ctypes.c_int),
+                ("n2", ctypes.c_int), ("q1", ctypes.c_int), ("q2", ctypes.c_int),
+                ("alpha", ctypes.c_double), ("f_true", ctypes.c_void_p), ("x_out", ctypes.c_void_p)]
 
 PRECISION = {"fp32": 0, "bf16x2": 1}
 
@@ -83,6 +90,14 @@ def lib() -> ctypes.CDLL:
         for name in ("ar_last_error_detail", "ar_version"):
             getattr(L, name).argtypes = []
             getattr(L, name).restype = ctypes.c_char_p
+        L.ar_batch_create.argtypes = [_vp, _i, _d, _i, _i, _i, _i, _vp, ctypes.POINTER(_vp)]
+        L.ar_batch_create.restype = _i
+        L.ar_batch_run.argtypes = [_vp, _vp]
+        L.ar_batch_run.restype = _i
+        L.ar_batch_results.argtypes = [_vp, _vp, _vp, _vp]
+        L.ar_batch_results.restype = _i
+        L.ar_batch_destroy.argtypes = [_vp]
+        L.ar_batch_destroy.restype = None
         L.ar_profile_begin.argtypes = []
         L.ar_profile_begin.restype = _i
         L.ar_profile_end.argtypes = [_vp, _vp, _i]
@@ -285,6 +300,62 @@ def ar_restore_plain_static(g: torch.Tensor, psf, tau: float = 1.0, iters: int =
         ctypes.addressof(best) if want else None,
         _stream(stream)), "ar_restore_plain_static")
     return x_out, (tr[:iters] if want else None), (best.value if want else None)
+
+
+class Batch:
+    """Owner of an ``ar_batch*``: many images restored by one CUDA-graph launch.
+
+    ``images`` is a list of dicts with keys g, psf, alpha, x_out and optional
+    f_true (device float32 tensors; psf a host array).  The tensors must stay
+    alive while the batch exists."""
+
+    def __init__(self, images, tau=1.0, iters=50, precondition=True, precision="fp32",
+                 concurrency=8, stream=None):
+        self.count = len(images)
+        self.iters = int(iters)
+        self._keep = []
+        arr = (BatchItem * self.count)()
+        for j, im in enumerate(images):
+            g = _image(im["g"], "g")
+            x = _image(im["x_out"], "x_out")
+            h = _host_psf(im["psf"])
+            q1, q2 = _support(h.shape)
+            f = im.get("f_true")
+            self._keep += [g, x, h, f]
+            arr[j] = BatchItem(g.data_ptr(), h.ctypes.data, g.shape[0], g.shape[1], q1, q2,
+                               float(im.get("alpha", 0.0)),
+                               _image(f, "f_true").data_ptr() if f is not None else None,
+                               x.data_ptr())
+        self._items = arr
+        out = _vp()
+        _check(lib().ar_batch_create(arr, self.count, float(tau), self.iters,
+                                     1 if precondition else 0, PRECISION[precision],
+                                     int(concurrency), _stream(stream), ctypes.byref(out)),
+               "ar_batch_create")
+        self.handle = out.value
+
+    def run(self, stream=None) -> None:
+        _check(lib().ar_batch_run(self.handle, _stream(stream)), "ar_batch_run")
+
+    def results(self):
+        """(rre traces [count, iters], best iterations [count], kernels per run)."""
+        tr = np.zeros((self.count, max(self.iters, 1)), dtype=np.float64)
+        best = np.zeros(self.count, dtype=np.int32)
+        kpr = ctypes.c_ulonglong(0)
+        _check(lib().ar_batch_results(self.handle, tr.ctypes.data, best.ctypes.data,
+                                      ctypes.byref(kpr)), "ar_batch_results")
+        return tr[:, :self.iters], best, int(kpr.value)
+
+    def close(self) -> None:
+        if self.handle:
+            lib().ar_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def kernel_launches() -> int:

@@ -50,7 +50,7 @@ int sm_count() {
 
 using namespace ar;
 
-namespace {
+namespace ar {
 
 bool overlaps(const void* a, size_t abytes, const void* b, size_t bbytes) {
     const char* pa = static_cast<const char*>(a);
@@ -185,7 +185,7 @@ ar_status prec_build(const double* psf_host, int q1, int q2, int n1, int n2, dou
     return AR_OK;
 }
 
-}  // namespace
+}  // namespace ar
 
 extern "C" {
 

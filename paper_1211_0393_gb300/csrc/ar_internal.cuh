@@ -139,6 +139,17 @@ ar_status count_nonfinite(const float* x, size_t n, unsigned long long* cnt, cud
 
 int sm_count();
 
+// ------------------------------------------------------ shared host helpers
+bool overlaps(const void* a, size_t abytes, const void* b, size_t bbytes);
+ar_status check_image_sizes(int n1, int n2, int nmin);
+ar_status check_support(int n1, int n2, int q1, int q2, int margin);
+ar_status check_psf_host(const double* h, int q1, int q2);
+void set_pool_threshold_once();
+// Builds a preconditioner on `s` without synchronizing (keep64: also keep the
+// float64 eigenvalues and filter).
+ar_status prec_build(const double* psf_host, int q1, int q2, int n1, int n2, double alpha,
+                     int precision, cudaStream_t s, bool keep64, ar_prec** out);
+
 // Launch accounting: every kernel launch site calls count_launch(k).
 void count_launch(unsigned k = 1);
 

@@ -38,6 +38,9 @@ cudaEvent_t get_event() {
 
 int prof_begin(int kind, cudaStream_t s) {
     if (!g_on.load(std::memory_order_relaxed)) return -1;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+        return -1;                        // a captured graph is not timed kernel by kernel
     std::lock_guard<std::mutex> lock(g_mu);
     Rec r{kind, get_event(), get_event()};
     cudaEventRecord(r.a, s);

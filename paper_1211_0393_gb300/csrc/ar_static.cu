@@ -58,12 +58,6 @@ ar_status scratch_base(unsigned char** out) {
     return AR_OK;
 }
 
-bool overlaps(const void* a, size_t abytes, const void* b, size_t bbytes) {
-    const char* pa = static_cast<const char*>(a);
-    const char* pb = static_cast<const char*>(b);
-    return pa < pb + bbytes && pb < pa + abytes;
-}
-
 }  // namespace
 }  // namespace ar
 

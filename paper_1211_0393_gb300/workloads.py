@@ -165,14 +165,16 @@ def psf_random(q1: int, q2: int, rng: np.random.Generator) -> np.ndarray:
     """A random mixture (Gaussian / motion / asymmetric Gaussian) of the given support."""
     kind = int(rng.integers(0, 3))
     qm = min(q1, q2)
+    s_hi = max(0.61, 0.5 + qm / 2)       # the bounds only bite for q = 0
+    a_hi = max(0.61, 0.4 + qm / 2)
     if kind == 0:
-        return psf_gaussian(q1, q2, rng.uniform(0.6, 0.5 + qm / 2), None, 0.0,
+        return psf_gaussian(q1, q2, rng.uniform(0.6, s_hi), None, 0.0,
                             rng.uniform(-0.5, 0.5), rng.uniform(-0.5, 0.5))
     if kind == 1:
-        m = psf_motion(q1, q2, rng.uniform(1.5, 2 * qm), rng.uniform(0, 180))
+        m = psf_motion(q1, q2, rng.uniform(1.5, max(1.51, 2 * qm)), rng.uniform(0, 180))
         g = psf_gaussian(q1, q2, 1.0, None, 0.0, 0.0, 0.0)
         return normalize(0.85 * m + 0.15 * g)
-    return psf_gaussian(q1, q2, rng.uniform(0.6, 0.4 + qm / 2), rng.uniform(0.6, 0.4 + qm / 2),
+    return psf_gaussian(q1, q2, rng.uniform(0.6, a_hi), rng.uniform(0.6, a_hi),
                         rng.uniform(0, 180), rng.uniform(-1, 1), rng.uniform(-1, 1))
 
 
@@ -221,6 +223,33 @@ def make_inputs(n1: int, n2: int, h: np.ndarray, scene: str, config_idx: int):
     gen = scene_blocks if scene == "blocks" else scene_ellipses
     ext = gen(n1 + 2 * q1, n2 + 2 * q2, rng)
     e = noise_field(n1, n2, rng)
+    return ext, crop(ext, q1, q2), e
+
+
+BATCH_SIDES = (128, 192, 256, 384, 512, 768, 1024)
+
+
+def batch_specs(count: int = 96, config_idx: int = 2, sides=BATCH_SIDES, qmin: int = 2,
+                qmax: int = 15):
+    """Uneven batch: per image, sides drawn independently from ``sides`` and an
+    own random PSF (Gaussian / motion / asymmetric Gaussian) of odd size
+    5x5..31x31.  Returns a list of dicts with n1, n2, psf and a per-image seed."""
+    rng = rng_for(config_idx)
+    out = []
+    for j in range(count):
+        n1, n2 = int(rng.choice(sides)), int(rng.choice(sides))
+        q = int(rng.integers(qmin, qmax + 1))
+        out.append({"n1": n1, "n2": n2, "psf": psf_random(q, q, rng), "seed": int(rng.integers(1 << 30))})
+    return out
+
+
+def batch_inputs(spec: dict):
+    """Extended scene, FOV crop and noise field of one batch image (seeded)."""
+    h = spec["psf"]
+    q1, q2 = (h.shape[0] - 1) // 2, (h.shape[1] - 1) // 2
+    rng = np.random.default_rng(spec["seed"])
+    ext = scene_ellipses(spec["n1"] + 2 * q1, spec["n2"] + 2 * q2, rng)
+    e = noise_field(spec["n1"], spec["n2"], rng)
     return ext, crop(ext, q1, q2), e
 
 
