@@ -40,6 +40,10 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = [
+    "BC_AR", "BC_REFLECTIVE", "BC_PERIODIC",
+    "pad_bc", "blur_bc", "reblur_bc", "matrix_dense_bc", "extension_1d_bc",
+    "dct_matrix", "eigenvalues_bc", "symprec_setup_bc", "symprec_solve_bc",
+    "restore_bc",
     "psf_support",
     "ar_extension_1d",
     "ar_pad",
@@ -475,4 +479,137 @@ def restore(g, h, alpha, tau=1.0, iters=20, precondition=True, x0=None, f_true=N
     best = None
     if trace is not None and trace:
         best = int(np.argmin(np.asarray(trace))) + 1
+    return x, (np.asarray(trace) if trace is not None else None), best
+
+
+# --------------------------------------------------------------------------
+# Comparison boundary conditions (Section 2.1 Reflective; periodic, Section 2)
+# --------------------------------------------------------------------------
+
+BC_AR, BC_REFLECTIVE, BC_PERIODIC = 0, 1, 2
+
+
+def extension_1d_bc(n: int, q: int, bc: int) -> np.ndarray:
+    """``(n+2q) x n`` extension matrix of one axis for the three BCs.
+
+    Reflective (Section 2.1): ``f_{1-i} = f_i``, ``f_{n+i} = f_{n+1-i}``.
+    Periodic: ``f_{1-i} = f_{n+1-i}``, ``f_{n+i} = f_i``.  AR: Section 2.2.
+    """
+    if bc == BC_AR:
+        return ar_extension_1d(n, q)
+    E = np.zeros((n + 2 * q, n))
+    for r in range(n + 2 * q):
+        j = r - q
+        if 0 <= j < n:
+            E[r, j] = 1.0
+        elif bc == BC_REFLECTIVE:
+            E[r, -j - 1 if j < 0 else 2 * n - 1 - j] = 1.0
+        else:
+            E[r, j % n] = 1.0
+    return E
+
+
+def pad_bc(x: np.ndarray, q1: int, q2: int, bc: int) -> np.ndarray:
+    """Extend an image by the rules of ``bc`` (rows first, then columns)."""
+    if bc == BC_AR:
+        return ar_pad(x, q1, q2)
+    x = np.asarray(x, dtype=np.float64)
+    n1, n2 = x.shape
+    if q1 > n1 or q2 > n2:
+        raise ValueError("extension needs q_j <= n_j")
+    return extension_1d_bc(n1, q1, bc) @ x @ extension_1d_bc(n2, q2, bc).T
+
+
+def blur_bc(x: np.ndarray, h: np.ndarray, bc: int) -> np.ndarray:
+    """``y_i = sum_s h_s xt_{i-s}`` (eq. modello_discreto) over the ``bc`` extension."""
+    h = np.asarray(h, dtype=np.float64)
+    q1, q2 = psf_support(h)
+    n1, n2 = np.asarray(x).shape
+    xp = pad_bc(x, q1, q2, bc)
+    y = np.zeros((n1, n2))
+    for s1 in range(-q1, q1 + 1):
+        for s2 in range(-q2, q2 + 1):
+            y += h[s1 + q1, s2 + q2] * xp[q1 - s1:q1 - s1 + n1, q2 - s2:q2 - s2 + n2]
+    return y
+
+
+def reblur_bc(x: np.ndarray, h: np.ndarray, bc: int) -> np.ndarray:
+    """The matrix of the PSF rotated by 180 degrees under the same BC (Section 4)."""
+    return blur_bc(x, np.asarray(h)[::-1, ::-1], bc)
+
+
+def matrix_dense_bc(h: np.ndarray, n1: int, n2: int, bc: int) -> np.ndarray:
+    """Dense ``A_n = A~ (E_{n1} (x) E_{n2})`` for the BC."""
+    q1, q2 = psf_support(h)
+    E = np.kron(extension_1d_bc(n1, q1, bc), extension_1d_bc(n2, q2, bc))
+    return toeplitz_extended_2d(h, n1, n2) @ E
+
+
+def dct_matrix(m: int) -> np.ndarray:
+    """Orthogonal ``R_m`` of eq. Rn with columns the DCT-III basis vectors:
+    ``R[t, k] = sqrt((2 - delta_{k,0})/m) cos(k (t + 1/2) pi / m)`` (0-based);
+    reflective matrices of strongly symmetric PSFs are ``R diag(lambda) R^T``."""
+    t = np.arange(m)[:, None]
+    k = np.arange(m)[None, :]
+    R = np.sqrt(2.0 / m) * np.cos(k * (t + 0.5) * np.pi / m)
+    R[:, 0] = np.sqrt(1.0 / m)
+    return R
+
+
+def eigenvalues_bc(h: np.ndarray, n1: int, n2: int, bc: int) -> np.ndarray:
+    """Eigenvalue magnitudes used by the preconditioner of each BC (Section 4).
+
+    AR and Reflective: the symbol of the symmetrized PSF (eq. simmetrizzata2d,
+    eq. funzione_generatrice) on the AR grid (Theorem 2) or on ``k pi / m``
+    (Section 2.1).  Periodic: ``|lambda|`` of the circulant of the PSF itself,
+    ``lambda(w) = sum_s h_s exp(-i s . w)`` at ``w = 2 pi k / m``.
+    """
+    if bc == BC_AR:
+        return eigenvalues(symmetrize(h), n1, n2)
+    if bc == BC_REFLECTIVE:
+        return symbol(symmetrize(h), np.arange(n1) * np.pi / n1, np.arange(n2) * np.pi / n2)
+    h = np.asarray(h, dtype=np.float64)
+    q1, q2 = psf_support(h)
+    w1 = 2.0 * np.pi * np.arange(n1) / n1
+    w2 = 2.0 * np.pi * np.arange(n2) / n2
+    lam = np.zeros((n1, n2), dtype=complex)
+    for a in range(-q1, q1 + 1):
+        for b in range(-q2, q2 + 1):
+            lam += h[a + q1, b + q2] * np.exp(-1j * (a * w1[:, None] + b * w2[None, :]))
+    return np.abs(lam)
+
+
+def symprec_setup_bc(h: np.ndarray, n1: int, n2: int, alpha: float, bc: int) -> dict:
+    lam = eigenvalues_bc(h, n1, n2, bc)
+    return {"lam": lam, "d": tikhonov(lam, alpha), "bc": bc, "n1": n1, "n2": n2}
+
+
+def symprec_solve_bc(prec: dict, y: np.ndarray) -> np.ndarray:
+    """``D y`` in the BC's algebra: AR ``T diag(d) T~`` (Theorem 1), Reflective
+    ``R diag(d) R^T`` (eq. Rn), Periodic ``F^* diag(d) F`` (numpy FFT)."""
+    bc, d = prec["bc"], prec["d"]
+    y = np.asarray(y, dtype=np.float64)
+    if bc == BC_AR:
+        return symprec_solve(prec, y)
+    if bc == BC_REFLECTIVE:
+        R1, R2 = dct_matrix(y.shape[0]), dct_matrix(y.shape[1])
+        return R1 @ (d * (R1.T @ y @ R2)) @ R2.T
+    return np.real(np.fft.ifft2(d * np.fft.fft2(y)))
+
+
+def restore_bc(g, h, alpha, bc, tau=1.0, iters=20, precondition=True, f_true=None):
+    """(D-)Landweber with reblurring under the BC (eqs. LandweberMeth / DLandweberMeth)."""
+    g = np.asarray(g, dtype=np.float64)
+    n1, n2 = g.shape
+    prec = symprec_setup_bc(h, n1, n2, alpha, bc) if precondition else None
+    x = np.zeros((n1, n2))
+    trace = [] if f_true is not None else None
+    for _ in range(iters):
+        z = reblur_bc(g - blur_bc(x, h, bc), h, bc)
+        if precondition:
+            z = symprec_solve_bc(prec, z)
+        x = x + tau * z
+        if trace is not None:
+            trace.append(rre(x, f_true))
+    best = int(np.argmin(trace)) + 1 if trace else None
     return x, (np.asarray(trace) if trace is not None else None), best
