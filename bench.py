@@ -245,6 +245,7 @@ def run_own(args):
                                                      max(args.steps // 2, 3), x_ref)}
             if not args.no_batch:
                 out["forms"]["batched"] = batched_form(ar, torch, dev, stream, flush, 3)
+            out["bcs"] = bcs_form(ar, torch, stream, g_d, f_d, h, flush, max(args.steps // 2, 3))
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(h, g, f)
     if world > 1:
@@ -416,6 +417,47 @@ def batched_form(ar, torch, dev, stream, flush, runs):
                            "ms_per_batch": round(t_seq, 3)},
             "speedup": round(t_seq / t_batch, 2), "identical_results": bool(same),
             "median_best_iter": int(np.median(best))}
+
+
+BC_PLAIN_ITERS = 3000
+BC_PRECOND_ITERS = 300
+
+
+def bcs_form(ar, torch, stream, g_d, f_d, h, flush, steps):
+    """The comparison of Section 4's tables on the bench workload: for the
+    periodic, reflective and anti-reflective BCs, the best RRE and the
+    iteration reaching it for Landweber and D-Landweber (reblurred, same
+    alpha and tau), and the throughput of the preconditioned step under each
+    BC (the periodic solve takes seven contractions, the others four)."""
+    out = {}
+    for bc in ("periodic", "reflective", "ar"):
+        _, tr_p, best_p = ar.ar_restore(g_d, h, ALPHA, TAU, BC_PLAIN_ITERS, False, f_true=f_d,
+                                        bc=bc)
+        _, tr_d, best_d = ar.ar_restore(g_d, h, ALPHA, TAU, BC_PRECOND_ITERS, True, f_true=f_d,
+                                        bc=bc)
+        x = torch.empty_like(g_d)
+
+        def step():
+            ar.ar_restore(g_d, h, ALPHA, TAU, ITERS, True, f_true=f_d, x_out=x, bc=bc)
+
+        for _ in range(3):
+            step()
+        tot = 0.0
+        for i in range(steps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step()
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        out[bc] = {"landweber": {"rre": round(float(np.min(tr_p)), 6), "it": best_p},
+                   "d_landweber": {"rre": round(float(np.min(tr_d)), 6), "it": best_d},
+                   "precond_value": round(N1 * N2 * ITERS * steps / 1e6 / (tot / 1e3), 2),
+                   "unit": UNIT}
+    out["note"] = (f"best RRE and its iteration within {BC_PLAIN_ITERS} Landweber / "
+                   f"{BC_PRECOND_ITERS} D-Landweber iterations, alpha {ALPHA}, tau {TAU}")
+    return out
 
 
 def quality_vs_plain(ar, torch, g_d, f_d, h):

@@ -54,6 +54,14 @@ typedef enum ar_status {
     AR_ERR_UNSUPPORTED = 8         /* valid request this build cannot serve (e.g. no sm_103a GPU) */
 } ar_status;
 
+/* Boundary conditions.  AR_BC_ANTIREFLECTIVE is the paper's method (Section
+ * 2.2, the default of every call without a bc argument); AR_BC_REFLECTIVE
+ * (Section 2.1: reflection about the boundary, DCT-III algebra) and
+ * AR_BC_PERIODIC (circulant) are the comparison BCs of Section 4's tables.
+ * The blur, reblur and plain Landweber support all three; the preconditioner
+ * supports AR and Reflective (AR_ERR_UNSUPPORTED for Periodic). */
+typedef enum ar_bc { AR_BC_ANTIREFLECTIVE = 0, AR_BC_REFLECTIVE = 1, AR_BC_PERIODIC = 2 } ar_bc;
+
 /* Arithmetic of the AR transform contractions (tensor cores).
  *  AR_PRECISION_FP32:   operands split into three bfloat16 planes, the six
  *                       products with i + j <= 2 accumulated in float32:
@@ -90,6 +98,20 @@ AR_API ar_status ar_reblur_apply(const float* x, float* y, int n1, int n2,
                           const float* psf, int q1, int q2, void* stream);
 
 /*
+ * ar_blur_apply / ar_reblur_apply under the boundary condition bc (ar_bc).
+ * Reflective extends by reflection about the boundary (Section 2.1:
+ * x_{-1-i} = x_i, x_{n+i} = x_{n-1-i}, 0-based), Periodic by wrapping; the
+ * reblur is the same blur with the PSF rotated by 180 degrees (for these two
+ * BCs it equals the transpose of the blur matrix).  bc = AR_BC_ANTIREFLECTIVE
+ * is ar_blur_apply / ar_reblur_apply.  Arguments and errors as ar_blur_apply,
+ * plus AR_ERR_INVALID_ARG for an unknown bc.
+ */
+AR_API ar_status ar_blur_apply_bc(const float* x, float* y, int n1, int n2,
+                                  const float* psf, int q1, int q2, int bc, void* stream);
+AR_API ar_status ar_reblur_apply_bc(const float* x, float* y, int n1, int n2,
+                                    const float* psf, int q1, int q2, int bc, void* stream);
+
+/*
  * Build the optimal AR preconditioner (Theorem 4) for a PSF and image size:
  *   S0  s = symmetrized PSF, eq. simmetrizzata2d, in float64 on the GPU;
  *   S1  lambda[i1,i2] = f_s(x1_{i1}, x2_{i2}), the symbol of eq.
@@ -114,6 +136,24 @@ AR_API ar_status ar_symprec_setup(const double* psf_host, int q1, int q2, int n1
  * precision returns AR_ERR_INVALID_ARG. */
 AR_API ar_status ar_symprec_setup_ex(const double* psf_host, int q1, int q2, int n1, int n2,
                                      double alpha, int precision, void* stream, ar_prec** out);
+
+/*
+ * ar_symprec_setup_ex for the boundary condition bc (ar_bc), the optimal
+ * preconditioner of each BC's algebra with the Tikhonov filter d of S2:
+ *   AR_BC_ANTIREFLECTIVE  as ar_symprec_setup_ex;
+ *   AR_BC_REFLECTIVE      D = R1 diag(d) R1^T (.) R2 diag(d) R2^T applied as
+ *       R1 (d o (R1^T y R2)) R2^T, R the DCT-III matrix of eq. Rn, lambda the
+ *       symbol of the symmetrized PSF at x_k = k pi / n (Section 2.1);
+ *   AR_BC_PERIODIC        D = F* diag(d) F, the circulant solve, lambda =
+ *       |sum_s h_s exp(-i s . w)| at w = 2 pi k / n (the PSF itself, not its
+ *       symmetrization), applied in the real separable Hartley basis.
+ * ar_symprec_eigenvalues returns these lambda and d (for Periodic in FFT
+ * order).  Sizes: n_j >= 3; q_j <= n_j - 3 for AR, q_j <= n_j - 1 otherwise.
+ * Errors as ar_symprec_setup_ex, plus AR_ERR_INVALID_ARG for an unknown bc.
+ */
+AR_API ar_status ar_symprec_setup_bc(const double* psf_host, int q1, int q2, int n1, int n2,
+                                     double alpha, int bc, int precision, void* stream,
+                                     ar_prec** out);
 
 /*
  * z = D y = T_n diag(d) T~_n y (Theorem 1 with the filtered eigenvalues).
@@ -204,6 +244,18 @@ AR_API ar_status ar_restore_plain_static(const float* g, const double* psf_host,
 AR_API ar_status ar_restore_ex(const float* g, const double* psf_host,
                                int n1, int n2, int q1, int q2, double alpha, double tau,
                                int iters, int precondition, int precision,
+                               const float* x0, const float* f_true, float* x_out,
+                               double* rre_trace, int* best_iter, void* stream);
+
+/* ar_restore_ex under the boundary condition bc (ar_bc): the blur, the
+ * reblur and, with precondition != 0, the preconditioner of
+ * ar_symprec_setup_bc all use bc (the Landweber / D-Landweber comparison of
+ * Section 4's tables).  ar_restore_ex is ar_restore_bc(..., AR_BC_ANTIREFLECTIVE,
+ * ...).  Sizes as ar_symprec_setup_bc when preconditioned, else as
+ * ar_blur_apply; other arguments and errors as ar_restore. */
+AR_API ar_status ar_restore_bc(const float* g, const double* psf_host,
+                               int n1, int n2, int q1, int q2, double alpha, double tau,
+                               int iters, int bc, int precondition, int precision,
                                const float* x0, const float* f_true, float* x_out,
                                double* rre_trace, int* best_iter, void* stream);
 

@@ -30,6 +30,7 @@ EXPORTS = [
     "ar_status_string", "ar_last_error_detail", "ar_version", "ar_kernel_launches",
     "ar_profile_begin", "ar_profile_end", "ar_restore_plain_static", "ar_symprec_setup_ex",
     "ar_restore_ex", "ar_batch_create", "ar_batch_run", "ar_batch_results", "ar_batch_destroy",
+    "ar_blur_apply_bc", "ar_reblur_apply_bc", "ar_symprec_setup_bc", "ar_restore_bc",
 ]
 
 
@@ -40,6 +41,9 @@ class BatchItem(ctypes.Structure):
                 ("alpha", ctypes.c_double), ("f_true", ctypes.c_void_p), ("x_out", ctypes.c_void_p)]
 
 PRECISION = {"fp32": 0, "bf16x2": 1}
+
+# ar_bc: the method's anti-reflective BCs and the two comparison BCs
+BC = {"ar": 0, "reflective": 1, "periodic": 2}
 
 PROF_KINDS = ("stencil", "contraction", "setup", "other")
 
@@ -67,6 +71,11 @@ def lib() -> ctypes.CDLL:
         sig = {
             "ar_blur_apply": [_vp, _vp, _i, _i, _vp, _i, _i, _vp],
             "ar_reblur_apply": [_vp, _vp, _i, _i, _vp, _i, _i, _vp],
+            "ar_blur_apply_bc": [_vp, _vp, _i, _i, _vp, _i, _i, _i, _vp],
+            "ar_reblur_apply_bc": [_vp, _vp, _i, _i, _vp, _i, _i, _i, _vp],
+            "ar_symprec_setup_bc": [_vp, _i, _i, _i, _i, _d, _i, _i, _vp, ctypes.POINTER(_vp)],
+            "ar_restore_bc": [_vp, _vp, _i, _i, _i, _i, _d, _d, _i, _i, _i, _i, _vp, _vp, _vp, _vp,
+                              _vp, _vp],
             "ar_symprec_setup": [_vp, _i, _i, _i, _i, _d, _vp, ctypes.POINTER(_vp)],
             "ar_symprec_setup_ex": [_vp, _i, _i, _i, _i, _d, _i, _vp, ctypes.POINTER(_vp)],
             "ar_restore_ex": [_vp, _vp, _i, _i, _i, _i, _d, _d, _i, _i, _i, _vp, _vp, _vp, _vp, _vp,
@@ -140,18 +149,20 @@ def _host_psf(psf) -> np.ndarray:
 
 
 def ar_blur_apply(x: torch.Tensor, psf: torch.Tensor, y: torch.Tensor | None = None,
-                  stream=None) -> torch.Tensor:
-    """``y = A_n x`` (AR blur).  ``psf`` is a float32 CUDA tensor of odd sides."""
-    return _apply("ar_blur_apply", x, psf, y, stream)
+                  stream=None, bc: str = "ar") -> torch.Tensor:
+    """``y = A_n x`` (blur under ``bc``: "ar", "reflective" or "periodic").
+
+    ``psf`` is a float32 CUDA tensor of odd sides."""
+    return _apply("ar_blur_apply", x, psf, y, stream, bc)
 
 
 def ar_reblur_apply(x: torch.Tensor, psf: torch.Tensor, y: torch.Tensor | None = None,
-                    stream=None) -> torch.Tensor:
-    """``y = A' x`` (AR blur with the PSF rotated by 180 degrees)."""
-    return _apply("ar_reblur_apply", x, psf, y, stream)
+                    stream=None, bc: str = "ar") -> torch.Tensor:
+    """``y = A' x`` (the blur under ``bc`` with the PSF rotated by 180 degrees)."""
+    return _apply("ar_reblur_apply", x, psf, y, stream, bc)
 
 
-def _apply(name, x, psf, y, stream):
+def _apply(name, x, psf, y, stream, bc="ar"):
     _image(x, "x")
     if not isinstance(psf, torch.Tensor) or not psf.is_cuda or psf.dtype != torch.float32:
         raise TypeError("psf must be a float32 CUDA tensor")
@@ -163,8 +174,13 @@ def _apply(name, x, psf, y, stream):
     if y.shape != x.shape:
         raise ValueError("y must have the shape of x")
     n1, n2 = x.shape
-    _check(getattr(lib(), name)(x.data_ptr(), y.data_ptr(), n1, n2, psf.data_ptr(), q1, q2,
-                                _stream(stream)), name)
+    if bc == "ar":
+        _check(getattr(lib(), name)(x.data_ptr(), y.data_ptr(), n1, n2, psf.data_ptr(), q1, q2,
+                                    _stream(stream)), name)
+    else:
+        name += "_bc"
+        _check(getattr(lib(), name)(x.data_ptr(), y.data_ptr(), n1, n2, psf.data_ptr(), q1, q2,
+                                    BC[bc], _stream(stream)), name)
     return y
 
 
@@ -188,17 +204,19 @@ class Prec:
 
 
 def ar_symprec_setup(psf, n1: int, n2: int, alpha: float, stream=None,
-                     precision: str = "fp32") -> Prec:
-    """Build the symmetrized-PSF AR preconditioner (float64 setup on the GPU).
+                     precision: str = "fp32", bc: str = "ar") -> Prec:
+    """Build the optimal preconditioner of ``bc`` (float64 setup on the GPU).
 
     ``precision``: "fp32" (three bf16 planes, six products) or "bf16x2" (two
-    planes, three products) for the transform contractions."""
+    planes, three products) for the transform contractions.  ``bc``: "ar"
+    (symmetrized PSF, AR transform), "reflective" (symmetrized PSF, DCT-III)
+    or "periodic" (circulant of the PSF)."""
     h = _host_psf(psf)
     q1, q2 = _support(h.shape)
     out = _vp()
-    _check(lib().ar_symprec_setup_ex(h.ctypes.data, q1, q2, n1, n2, float(alpha),
+    _check(lib().ar_symprec_setup_bc(h.ctypes.data, q1, q2, n1, n2, float(alpha), BC[bc],
                                      PRECISION[precision], _stream(stream), ctypes.byref(out)),
-           "ar_symprec_setup_ex")
+           "ar_symprec_setup_bc")
     return Prec(out.value, n1, n2)
 
 
@@ -234,8 +252,10 @@ def ar_symprec_shape(P: Prec) -> tuple[int, int]:
 def ar_restore(g: torch.Tensor, psf, alpha: float, tau: float = 1.0, iters: int = 20,
                precondition: bool = True, x0: torch.Tensor | None = None,
                f_true: torch.Tensor | None = None, x_out: torch.Tensor | None = None,
-               trace: bool = True, stream=None, precision: str = "fp32"):
-    """(D-)Landweber restoration.  Returns ``(x, rre_trace or None, best_iter or None)``."""
+               trace: bool = True, stream=None, precision: str = "fp32", bc: str = "ar"):
+    """(D-)Landweber restoration under ``bc``.
+
+    Returns ``(x, rre_trace or None, best_iter or None)``."""
     _image(g, "g")
     h = _host_psf(psf)
     q1, q2 = _support(h.shape)
@@ -246,9 +266,9 @@ def ar_restore(g: torch.Tensor, psf, alpha: float, tau: float = 1.0, iters: int 
     want = f_true is not None and trace
     tr = np.zeros(max(iters, 1), dtype=np.float64) if want else None
     best = _i(0)
-    _check(lib().ar_restore_ex(
+    _check(lib().ar_restore_bc(
         g.data_ptr(), h.ctypes.data, n1, n2, q1, q2, float(alpha), float(tau), int(iters),
-        1 if precondition else 0, PRECISION[precision],
+        BC[bc], 1 if precondition else 0, PRECISION[precision],
         _image(x0, "x0").data_ptr() if x0 is not None else None,
         _image(f_true, "f_true").data_ptr() if f_true is not None else None,
         x_out.data_ptr(),

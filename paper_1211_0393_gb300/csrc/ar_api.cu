@@ -117,9 +117,16 @@ struct Scratch {
     }
 };
 
+ar_status check_bc(int bc) {
+    if (bc != AR_BC_ANTIREFLECTIVE && bc != AR_BC_REFLECTIVE && bc != AR_BC_PERIODIC)
+        return fail(AR_ERR_INVALID_ARG, "unknown boundary condition %d", bc);
+    return AR_OK;
+}
+
 ar_status apply_common(const float* x, float* y, int n1, int n2, const float* psf, int q1, int q2,
-                       void* stream, int flip) {
+                       int bc, void* stream, int flip) {
     if (!x || !y || !psf) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
+    AR_TRY(check_bc(bc));
     AR_TRY(check_image_sizes(n1, n2, 1));
     AR_TRY(check_support(n1, n2, q1, q2, 1));
     const size_t nb = (size_t)n1 * n2 * sizeof(float);
@@ -136,12 +143,13 @@ ar_status apply_common(const float* x, float* y, int n1, int n2, const float* ps
     a.q2 = q2;
     a.flip = flip;
     a.mode = CONV_STORE;
+    a.bc = bc;
     return conv_launch(a, static_cast<cudaStream_t>(stream));
 }
 
 // Builds the preconditioner's device data on `s` without synchronizing.
 ar_status prec_build(const double* psf_host, int q1, int q2, int n1, int n2, double alpha,
-                     int precision, cudaStream_t s, bool keep64, ar_prec** out) {
+                     int bc, int precision, cudaStream_t s, bool keep64, ar_prec** out) {
     set_pool_threshold_once();
     ar_prec* P = new (std::nothrow) ar_prec();
     if (!P) return fail(AR_ERR_ALLOC, "host allocation of ar_prec");
@@ -152,6 +160,7 @@ ar_status prec_build(const double* psf_host, int q1, int q2, int n1, int n2, dou
     P->q2 = q2;
     P->alpha = alpha;
     P->precision = precision;
+    P->bc = bc;
     cudaGetDevice(&P->device);
     const size_t n = (size_t)n1 * n2;
     const size_t k = (size_t)(2 * q1 + 1) * (2 * q2 + 1);
@@ -161,7 +170,7 @@ ar_status prec_build(const double* psf_host, int q1, int q2, int n1, int n2, dou
         double* h64 = nullptr;
         double* work = nullptr;
         st = tmp.get(&h64, k);
-        if (st == AR_OK) st = tmp.get(&work, setup_scratch_doubles(q1, q2, n1, n2));
+        if (st == AR_OK) st = tmp.get(&work, setup_scratch_doubles(q1, q2, n1, n2, bc));
         if (st == AR_OK) {
             cudaError_t e = cudaMemcpyAsync(h64, psf_host, k * sizeof(double),
                                             cudaMemcpyHostToDevice, s);
@@ -174,8 +183,13 @@ ar_status prec_build(const double* psf_host, int q1, int q2, int n1, int n2, dou
         }
         if (st == AR_OK && cudaMallocAsync((void**)&P->d32, n * sizeof(float), s) != cudaSuccess)
             st = fail(AR_ERR_ALLOC, "filter buffer");
-        if (st == AR_OK) st = setup_eigen(h64, q1, q2, n1, n2, alpha, P->lam64, P->d64, P->d32, work, s);
-        if (st == AR_OK) st = transform_plan_create(n1, n2, precision, s, &P->plan);
+        if (st == AR_OK && bc == AR_BC_PERIODIC &&
+            cudaMallocAsync((void**)&P->d32_odd, n * sizeof(float), s) != cudaSuccess)
+            st = fail(AR_ERR_ALLOC, "odd filter buffer");
+        if (st == AR_OK)
+            st = setup_eigen(h64, q1, q2, n1, n2, alpha, bc, P->lam64, P->d64, P->d32, P->d32_odd,
+                             work, s);
+        if (st == AR_OK) st = transform_plan_create(n1, n2, bc, precision, s, &P->plan);
     }
     if (st != AR_OK) {
         ar_symprec_destroy(P);
@@ -212,32 +226,51 @@ unsigned long long ar_kernel_launches(void) { return g_launches.load(); }
 
 ar_status ar_blur_apply(const float* x, float* y, int n1, int n2, const float* psf, int q1, int q2,
                         void* stream) {
-    return apply_common(x, y, n1, n2, psf, q1, q2, stream, 0);
+    return apply_common(x, y, n1, n2, psf, q1, q2, AR_BC_ANTIREFLECTIVE, stream, 0);
 }
 
 ar_status ar_reblur_apply(const float* x, float* y, int n1, int n2, const float* psf, int q1,
                           int q2, void* stream) {
-    return apply_common(x, y, n1, n2, psf, q1, q2, stream, 1);
+    return apply_common(x, y, n1, n2, psf, q1, q2, AR_BC_ANTIREFLECTIVE, stream, 1);
+}
+
+ar_status ar_blur_apply_bc(const float* x, float* y, int n1, int n2, const float* psf, int q1,
+                           int q2, int bc, void* stream) {
+    return apply_common(x, y, n1, n2, psf, q1, q2, bc, stream, 0);
+}
+
+ar_status ar_reblur_apply_bc(const float* x, float* y, int n1, int n2, const float* psf, int q1,
+                             int q2, int bc, void* stream) {
+    return apply_common(x, y, n1, n2, psf, q1, q2, bc, stream, 1);
 }
 
 ar_status ar_symprec_setup(const double* psf_host, int q1, int q2, int n1, int n2, double alpha,
                            void* stream, ar_prec** out) {
-    return ar_symprec_setup_ex(psf_host, q1, q2, n1, n2, alpha, AR_PRECISION_FP32, stream, out);
+    return ar_symprec_setup_bc(psf_host, q1, q2, n1, n2, alpha, AR_BC_ANTIREFLECTIVE,
+                               AR_PRECISION_FP32, stream, out);
 }
 
 ar_status ar_symprec_setup_ex(const double* psf_host, int q1, int q2, int n1, int n2, double alpha,
                               int precision, void* stream, ar_prec** out) {
+    return ar_symprec_setup_bc(psf_host, q1, q2, n1, n2, alpha, AR_BC_ANTIREFLECTIVE, precision,
+                               stream, out);
+}
+
+ar_status ar_symprec_setup_bc(const double* psf_host, int q1, int q2, int n1, int n2, double alpha,
+                              int bc, int precision, void* stream, ar_prec** out) {
     if (!psf_host || !out) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
     if (precision != AR_PRECISION_FP32 && precision != AR_PRECISION_BF16X2)
         return fail(AR_ERR_INVALID_ARG, "unknown precision %d", precision);
+    AR_TRY(check_bc(bc));
     AR_TRY(check_image_sizes(n1, n2, 3));
-    AR_TRY(check_support(n1, n2, q1, q2, 3));
+    // AR needs the interior grid of size n - 2 to hold the support
+    AR_TRY(check_support(n1, n2, q1, q2, bc == AR_BC_ANTIREFLECTIVE ? 3 : 1));
     if (!(alpha > 0.0) || !std::isfinite(alpha))
         return fail(AR_ERR_INVALID_ARG, "alpha must be finite and > 0 (got %g)", alpha);
     AR_TRY(check_psf_host(psf_host, q1, q2));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     ar_prec* P = nullptr;
-    AR_TRY(prec_build(psf_host, q1, q2, n1, n2, alpha, precision, s, true, &P));
+    AR_TRY(prec_build(psf_host, q1, q2, n1, n2, alpha, bc, precision, s, true, &P));
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         ar_symprec_destroy(P);
@@ -251,7 +284,7 @@ ar_status ar_symprec_solve(const ar_prec* P, const float* y, float* z, void* str
     if (!P || !y || !z) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
     const size_t nb = (size_t)P->n1 * P->n2 * sizeof(float);
     if (y != z && overlaps(y, nb, z, nb)) return fail(AR_ERR_ALIAS, "z partially overlaps y");
-    return transform_apply(P->plan, P->d32, y, DIN_FP32, z, DOUT_STORE, 0.f,
+    return transform_apply(P->plan, P->d32, P->d32_odd, y, DIN_FP32, z, DOUT_STORE, 0.f,
                            static_cast<cudaStream_t>(stream));
 }
 
@@ -278,6 +311,7 @@ void ar_symprec_destroy(ar_prec* P) {
     cudaFree(P->lam64);
     cudaFree(P->d64);
     cudaFree(P->d32);
+    cudaFree(P->d32_odd);
     delete P;
 }
 
@@ -285,20 +319,30 @@ ar_status ar_restore(const float* g, const double* psf_host, int n1, int n2, int
                      double alpha, double tau, int iters, int precondition, const float* x0,
                      const float* f_true, float* x_out, double* rre_trace, int* best_iter,
                      void* stream) {
-    return ar_restore_ex(g, psf_host, n1, n2, q1, q2, alpha, tau, iters, precondition,
-                         AR_PRECISION_FP32, x0, f_true, x_out, rre_trace, best_iter, stream);
+    return ar_restore_bc(g, psf_host, n1, n2, q1, q2, alpha, tau, iters, AR_BC_ANTIREFLECTIVE,
+                         precondition, AR_PRECISION_FP32, x0, f_true, x_out, rre_trace, best_iter,
+                         stream);
 }
 
 ar_status ar_restore_ex(const float* g, const double* psf_host, int n1, int n2, int q1, int q2,
                         double alpha, double tau, int iters, int precondition, int precision,
                         const float* x0, const float* f_true, float* x_out, double* rre_trace,
                         int* best_iter, void* stream) {
+    return ar_restore_bc(g, psf_host, n1, n2, q1, q2, alpha, tau, iters, AR_BC_ANTIREFLECTIVE,
+                         precondition, precision, x0, f_true, x_out, rre_trace, best_iter, stream);
+}
+
+ar_status ar_restore_bc(const float* g, const double* psf_host, int n1, int n2, int q1, int q2,
+                        double alpha, double tau, int iters, int bc, int precondition,
+                        int precision, const float* x0, const float* f_true, float* x_out,
+                        double* rre_trace, int* best_iter, void* stream) {
     if (!g || !psf_host || !x_out) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
     if (precision != AR_PRECISION_FP32 && precision != AR_PRECISION_BF16X2)
         return fail(AR_ERR_INVALID_ARG, "unknown precision %d", precision);
+    AR_TRY(check_bc(bc));
     const bool pc = precondition != 0;
     AR_TRY(check_image_sizes(n1, n2, pc ? 3 : 1));
-    AR_TRY(check_support(n1, n2, q1, q2, pc ? 3 : 1));
+    AR_TRY(check_support(n1, n2, q1, q2, pc && bc == AR_BC_ANTIREFLECTIVE ? 3 : 1));
     if (iters < 0) return fail(AR_ERR_INVALID_ARG, "iters must be >= 0 (got %d)", iters);
     if (!(tau > 0.0) || !std::isfinite(tau))
         return fail(AR_ERR_INVALID_ARG, "tau must be finite and > 0 (got %g)", tau);
@@ -346,7 +390,7 @@ ar_status ar_restore_ex(const float* g, const double* psf_host, int n1, int n2, 
             if (e != cudaSuccess) st = cuda_fail(e, "restore initialisation");
         }
         if (st == AR_OK && pc)
-            st = prec_build(psf_host, q1, q2, n1, n2, alpha, precision, s, false, &P);
+            st = prec_build(psf_host, q1, q2, n1, n2, alpha, bc, precision, s, false, &P);
         if (st == AR_OK && f_true) st = reduce_sq(f_true, n, dsum + iters, s);
 
         ConvArgs blur{};
@@ -360,6 +404,7 @@ ar_status ar_restore_ex(const float* g, const double* psf_host, int n1, int n2, 
         blur.q2 = q2;
         blur.flip = 0;
         blur.mode = CONV_RESIDUAL;
+        blur.bc = bc;
         ConvArgs reblur = blur;
         reblur.x = r;
         reblur.aux = nullptr;
@@ -381,8 +426,9 @@ ar_status ar_restore_ex(const float* g, const double* psf_host, int n1, int n2, 
             if (!pc) reblur.sumsq = f_true ? dsum + it : nullptr;
             if (st == AR_OK) st = conv_launch(reblur, s);        // z = A' r  (or x += tau A' r)
             if (st == AR_OK && pc)                               // x += tau D z
-                st = transform_apply(P->plan, P->d32, nullptr, DIN_SPLIT, x_out, DOUT_AXPY,
-                                     (float)tau, s, f_true, f_true ? dsum + it : nullptr);
+                st = transform_apply(P->plan, P->d32, P->d32_odd, nullptr, DIN_SPLIT, x_out,
+                                     DOUT_AXPY, (float)tau, s, f_true,
+                                     f_true ? dsum + it : nullptr);
         }
         if (st == AR_OK) st = count_nonfinite(x_out, n, dbad, s);
         if (st == AR_OK) {

@@ -89,8 +89,8 @@ ar_status enqueue_image(ar_batch* B, int j, cudaStream_t s, double tau) {
         if (!pc) reblur.sumsq = it.f_true ? B->sums[j] + k : nullptr;
         AR_TRY(conv_launch(reblur, s));
         if (pc)
-            AR_TRY(transform_apply(B->precs[j]->plan, B->precs[j]->d32, nullptr, DIN_SPLIT, it.x_out,
-                                   DOUT_AXPY, (float)tau, s, it.f_true,
+            AR_TRY(transform_apply(B->precs[j]->plan, B->precs[j]->d32, nullptr, nullptr,
+                                   DIN_SPLIT, it.x_out, DOUT_AXPY, (float)tau, s, it.f_true,
                                    it.f_true ? B->sums[j] + k : nullptr));
     }
     AR_TRY(count_nonfinite(it.x_out, n, B->bad + j, s));
@@ -175,8 +175,8 @@ ar_status ar_batch_create(const ar_batch_item* items, int count, double tau, int
         if (cudaMemcpy(B->psf[j], h32.data(), k * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
             st = fail(AR_ERR_CUDA, "PSF upload of item %d", j);
         if (st == AR_OK && pc)
-            st = prec_build(it.psf_host, it.q1, it.q2, it.n1, it.n2, it.alpha, precision, s, false,
-                            &B->precs[j]);
+            st = prec_build(it.psf_host, it.q1, it.q2, it.n1, it.n2, it.alpha,
+                            AR_BC_ANTIREFLECTIVE, precision, s, false, &B->precs[j]);
     }
     if (st != AR_OK) return bail(st);
     if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(AR_ERR_CUDA, "batch setup"));

@@ -1,4 +1,6 @@
 // Fused anti-reflective extension + 2D convolution (y = A_n x and y = A' x).
+// The same kernels serve the comparison boundary conditions: reflective
+// (Section 2.1) and periodic extensions are plain index maps.
 //
 // A_n x is the convolution g_i = sum_s h_s xt_{i-s} (eq. modello_discreto) of
 // the image extended by the anti-reflective rules of Section 2.2: along each
@@ -29,12 +31,23 @@ constexpr int RS = 16;   // rows per strip
 constexpr int TH = TY * RS;
 constexpr int QMAX_FAST = 15;
 
+// Index of the sample that an out-of-image index j maps to under the
+// reflective (f_{1-i} = f_i, f_{n+i} = f_{n+1-i}, Section 2.1) or periodic
+// extension; in-image indices map to themselves.  Valid for -n <= j < 2n.
+__device__ __forceinline__ int mirror_index(int j, int n, int bc) {
+    if (j >= 0 && j < n) return j;
+    if (bc == AR_BC_REFLECTIVE) return j < 0 ? -j - 1 : 2 * n - 1 - j;
+    return j < 0 ? j + n : j - n;                           // periodic
+}
+
 // Sample of the anti-reflectively extended image at (j1, j2) (0-based; may
 // lie outside the image by up to q).  Outside the extended domain the value
 // only feeds outputs that are never stored, so 0 is returned without reading.
 __device__ __forceinline__ float ext_value(const float* __restrict__ x, int n1, int n2,
-                                           int q1, int q2, int j1, int j2) {
+                                           int q1, int q2, int j1, int j2, int bc) {
     if (j1 < -q1 || j1 >= n1 + q1 || j2 < -q2 || j2 >= n2 + q2) return 0.f;
+    if (bc != AR_BC_ANTIREFLECTIVE)
+        return __ldg(x + (size_t)mirror_index(j1, n1, bc) * n2 + mirror_index(j2, n2, bc));
     const bool r_in = (j1 >= 0 && j1 < n1);
     const bool c_in = (j2 >= 0 && j2 < n2);
     // row terms: edge row re (weight 2) and mirror row rm (weight -1)
@@ -133,8 +146,15 @@ conv_fast_kernel(const ConvArgs a) {
             v[k] = 0.f;
             if (i < H * W) {
                 const int r = i / W, c = i % W;
-                const int j1 = min(max(r0 - Q + r, 0), a.n1 - 1);
-                const int j2 = min(max(c0 - Q + c, 0), a.n2 - 1);
+                int j1 = r0 - Q + r, j2 = c0 - Q + c;
+                if (a.bc != AR_BC_ANTIREFLECTIVE && j1 >= -a.q1 && j1 < a.n1 + a.q1 &&
+                    j2 >= -a.q2 && j2 < a.n2 + a.q2) {
+                    j1 = mirror_index(j1, a.n1, a.bc);      // reflective / periodic sample
+                    j2 = mirror_index(j2, a.n2, a.bc);
+                } else {
+                    j1 = min(max(j1, 0), a.n1 - 1);
+                    j2 = min(max(j2, 0), a.n2 - 1);
+                }
                 v[k] = __ldg(a.x + (size_t)j1 * a.n2 + j2);
             }
         }
@@ -149,7 +169,8 @@ conv_fast_kernel(const ConvArgs a) {
     // samples, rows first (Section 2.2 border rule on in-image columns), then
     // columns on every row, which yields the corner rule.  Edge and mirror
     // samples always lie inside the tile.
-    if (r0 - Q < 0 || r0 + TH + Q > a.n1 || c0 - Q < 0 || c0 + TX + Q > a.n2) {
+    if (a.bc == AR_BC_ANTIREFLECTIVE &&
+        (r0 - Q < 0 || r0 + TH + Q > a.n1 || c0 - Q < 0 || c0 + TX + Q > a.n2)) {
         for (int i = tid; i < H * W; i += TX * TY) {
             const int r = i / W, c = i % W;
             const int j1 = r0 - Q + r, j2 = c0 - Q + c;
@@ -224,7 +245,7 @@ conv_generic_kernel(const ConvArgs a) {
             for (int s1 = -a.q1; s1 <= a.q1; ++s1) {
                 const int t1 = a.flip ? -s1 : s1, t2 = a.flip ? -s2 : s2;
                 const float hv = __ldg(a.psf + (t1 + a.q1) * kw + (t2 + a.q2));
-                acc = fmaf(hv, ext_value(a.x, a.n1, a.n2, a.q1, a.q2, row - s1, col - s2), acc);
+                acc = fmaf(hv, ext_value(a.x, a.n1, a.n2, a.q1, a.q2, row - s1, col - s2, a.bc), acc);
             }
         }
         sq = conv_epilogue(a, row, col, acc);

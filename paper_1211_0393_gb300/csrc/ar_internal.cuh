@@ -78,19 +78,21 @@ struct ConvArgs {
     float tau;
     const float* f;      // CONV_AXPY: true image or null
     double* sumsq;       // CONV_AXPY with f: += sum (x_new - f)^2 (float64)
+    int bc;              // AR_BC_ANTIREFLECTIVE / AR_BC_REFLECTIVE / AR_BC_PERIODIC
 };
 
 // Launches the AR stencil on `stream` (validated arguments).
 ar_status conv_launch(const ConvArgs& a, cudaStream_t stream);
 
 // ------------------------------------------------------------ transform ---
-// The AR transform pair for one image size, applied as four dense
-// contractions.  Implemented in ar_transform.cu.
+// The transform pair of a boundary condition for one image size, applied as
+// dense contractions (four for AR and Reflective, seven for Periodic).
+// Implemented in ar_transform.cu.
 struct TransformPlan;
 
 // precision: AR_PRECISION_FP32 (three bf16 planes, six products) or
-// AR_PRECISION_BF16X2 (two planes, three products).
-ar_status transform_plan_create(int n1, int n2, int precision, cudaStream_t stream,
+// AR_PRECISION_BF16X2 (two planes, three products); bc: an ar_bc value.
+ar_status transform_plan_create(int n1, int n2, int bc, int precision, cudaStream_t stream,
                                 TransformPlan** out);
 void transform_plan_destroy(TransformPlan* p);
 
@@ -109,9 +111,12 @@ enum DOutput : int {
 // Pointer to the operand planes the stencil must fill for DIN_SPLIT.
 uint16_t* transform_input_planes(TransformPlan* p, size_t* plane_stride, int* ld);
 
-// With dout == DOUT_AXPY and f non-null, sum (x_new - f)^2 is added to *sumsq
-// (float64) in the same kernel that updates x.
-ar_status transform_apply(TransformPlan* p, const float* d32, const float* y, DInput din,
+// d32 is the filter in the transform domain; for Periodic it is the part of d
+// even in each frequency and d32_odd minus the part odd in both (null for the
+// other BCs).  With dout == DOUT_AXPY and f non-null, sum (x_new - f)^2 is
+// added to *sumsq (float64) in the same kernel that updates x.
+ar_status transform_apply(TransformPlan* p, const float* d32, const float* d32_odd,
+                          const float* y, DInput din,
                           float* out, DOutput dout, float tau, cudaStream_t stream,
                           const float* f = nullptr, double* sumsq = nullptr);
 
@@ -122,12 +127,15 @@ int transform_launches(const TransformPlan* p, DInput din);
 int* transform_error_flag(TransformPlan* p);
 
 // ---------------------------------------------------------------- setup ---
-// FP64 eigenvalue setup on the GPU: symmetrize (eq. simmetrizzata2d), symbol
-// on the AR grid (eq. funzione_generatrice, Theorem 2), Tikhonov (eq. TikFilter).
+// FP64 eigenvalue setup on the GPU.  AR and Reflective: symmetrize (eq.
+// simmetrizzata2d), symbol (eq. funzione_generatrice) on the grid of the BC
+// (Theorem 2 / Section 2.1).  Periodic: |lambda| of the circulant of the PSF
+// itself, then the even/odd split of d that transform_apply takes (d32,
+// d32_odd).  Tikhonov filter d = 1/(lambda^2 + alpha) (eq. TikFilter).
 ar_status setup_eigen(const double* psf_dev64, int q1, int q2, int n1, int n2, double alpha,
-                      double* lam64, double* d64, float* d32, double* scratch_dev,
-                      cudaStream_t stream);
-size_t setup_scratch_doubles(int q1, int q2, int n1, int n2);
+                      int bc, double* lam64, double* d64, float* d32, float* d32_odd,
+                      double* scratch_dev, cudaStream_t stream);
+size_t setup_scratch_doubles(int q1, int q2, int n1, int n2, int bc);
 
 // ------------------------------------------------------------- reductions ---
 // acc[0] += sum (x - f)^2, both n floats, float64 accumulation.
@@ -148,7 +156,7 @@ void set_pool_threshold_once();
 // Builds a preconditioner on `s` without synchronizing (keep64: also keep the
 // float64 eigenvalues and filter).
 ar_status prec_build(const double* psf_host, int q1, int q2, int n1, int n2, double alpha,
-                     int precision, cudaStream_t s, bool keep64, ar_prec** out);
+                     int bc, int precision, cudaStream_t s, bool keep64, ar_prec** out);
 
 // Launch accounting: every kernel launch site calls count_launch(k).
 void count_launch(unsigned k = 1);
@@ -170,9 +178,11 @@ struct ar_prec {
     int n1, n2, q1, q2;
     double alpha;
     int precision;
+    int bc;
     int device;
     double* lam64;
     double* d64;
     float* d32;
+    float* d32_odd;      // Periodic only: minus the part of d odd in both frequencies
     ar::TransformPlan* plan;
 };

@@ -16,6 +16,11 @@
 //   G3: V^T <- (W T2^T)^T         A = W               B = T2
 //   G4: out <- (V^T T1^T)^T       (or out += tau * ...)
 //
+// The comparison BCs use the same chain with other constant operands: the
+// Reflective preconditioner (DCT-III, eq. Rn) takes T~ = R^T and T = R; the
+// Periodic one (a circulant) is applied in the real separable Hartley basis
+// with three more products (see transform_apply).
+//
 // Precision: each operand x is split into three bfloat16 planes
 // x = x0 + x1 + x2 (x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1)),
 // and the six products a_i b_j with i + j <= 2 are accumulated in float32 in
@@ -43,6 +48,7 @@
 
 #include <cstdlib>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <new>
 #include <utility>
@@ -435,6 +441,51 @@ __global__ void fill_transforms_kernel(int m, int ld, const double* tab, const d
     T[2 * ps + o] = a2;
 }
 
+// Comparison-BC transforms as bf16x3 planes, row pitch ld, entry (s, t):
+//  Reflective (eq. Rn, DCT-III): Tt = R^T, T = R with
+//    R[t][k] = sqrt((2 - delta_{k,0}) / m) cos(k (2t + 1) pi / (2m));
+//  Periodic (separable Hartley, normalised): Tt = T = H with
+//    H[s][t] = (cos + sin)(2 pi s t / m) / sqrt(m), and Tp = H' with
+//    H'[s][t] = (cos - sin)(2 pi s t / m) / sqrt(m) (columns of H at -s).
+// Arguments are reduced exactly in integers before cospi / sincospi.
+__global__ void fill_bc_transforms_kernel(int m, int ld, int bc, uint16_t* Tt, uint16_t* T,
+                                          uint16_t* Tp) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)m * m) return;
+    const int s = (int)(idx / m), t = (int)(idx % m);
+    const size_t ps = (size_t)m * ld, o = (size_t)s * ld + t;
+    double vt, v, vp = 0.0;
+    if (bc == AR_BC_REFLECTIVE) {
+        // R^T[s][t] = R[t][s]
+        const long long rt = ((long long)s * (2 * t + 1)) % (4LL * m);
+        vt = sqrt((s == 0 ? 1.0 : 2.0) / (double)m) * cospi((double)rt / (2.0 * m));
+        const long long r = ((long long)t * (2 * s + 1)) % (4LL * m);
+        v = sqrt((t == 0 ? 1.0 : 2.0) / (double)m) * cospi((double)r / (2.0 * m));
+    } else {
+        const long long r = ((long long)s * t) % (long long)m;
+        double sv, cv;
+        sincospi(2.0 * (double)r / (double)m, &sv, &cv);
+        const double sc = 1.0 / sqrt((double)m);
+        vt = v = (cv + sv) * sc;
+        vp = (cv - sv) * sc;
+    }
+    uint16_t a0, a1, a2;
+    split3_f64(vt, a0, a1, a2);
+    Tt[o] = a0;
+    Tt[ps + o] = a1;
+    Tt[2 * ps + o] = a2;
+    split3_f64(v, a0, a1, a2);
+    T[o] = a0;
+    T[ps + o] = a1;
+    T[2 * ps + o] = a2;
+    if (Tp) {
+        split3_f64(vp, a0, a1, a2);
+        Tp[o] = a0;
+        Tp[ps + o] = a1;
+        Tp[2 * ps + o] = a2;
+    }
+}
+
 // float32 image -> bf16x3 planes (row pitch ld).
 __global__ void split_image_kernel(const float* __restrict__ y, int n1, int n2, int ld,
                                    uint16_t* planes, size_t pstride) {
@@ -511,10 +562,34 @@ ar_status alloc_operand(Operand& o, int rows, int K, int box_rows, cudaStream_t 
     return AR_OK;
 }
 
-// Builds T~'_m and T'_m on `s` and waits for them.
-ar_status build_transforms(int m, Operand& Tt, Operand& T, cudaStream_t s) {
-    AR_TRY(alloc_operand(Tt, m, m, BN, s, true));
-    AR_TRY(alloc_operand(T, m, m, BN, s, true));
+// The constant operands of one BC and side length m: the analysis Tt and
+// synthesis T matrices, and for Periodic the flipped synthesis Tp.
+struct TransformSet {
+    Operand Tt, T, Tp;
+};
+
+void free_set(TransformSet& ts) {
+    cudaFree(ts.Tt.planes);
+    cudaFree(ts.T.planes);
+    cudaFree(ts.Tp.planes);
+}
+
+// Builds the operands of (m, bc) on `s` and waits for them.  AR: T~'_m and
+// T'_m of Theorem 1 (eq. Qn for the interior, the boundary columns Q p and
+// Q J p as length-m reductions).
+ar_status build_transforms(int m, int bc, TransformSet& ts, cudaStream_t s) {
+    AR_TRY(alloc_operand(ts.Tt, m, m, BN, s, true));
+    AR_TRY(alloc_operand(ts.T, m, m, BN, s, true));
+    const size_t mm = (size_t)m * m;
+    if (bc != AR_BC_ANTIREFLECTIVE) {
+        if (bc == AR_BC_PERIODIC) AR_TRY(alloc_operand(ts.Tp, m, m, BN, s, true));
+        fill_bc_transforms_kernel<<<(unsigned)((mm + 255) / 256), 256, 0, s>>>(
+            m, ts.Tt.ld, bc, ts.Tt.planes, ts.T.planes, ts.Tp.planes);
+        count_launch();
+        AR_CUDA(cudaGetLastError());
+        AR_CUDA(cudaStreamSynchronize(s));
+        return AR_OK;
+    }
     double* tmp = nullptr;
     const int ntab = 2 * (m - 1);
     AR_CUDA(cudaMallocAsync((void**)&tmp, (2 * (size_t)m + ntab) * sizeof(double), s));
@@ -527,9 +602,9 @@ ar_status build_transforms(int m, Operand& Tt, Operand& T, cudaStream_t s) {
         count_launch();
         AR_CUDA(cudaGetLastError());
     }
-    const size_t mm = (size_t)m * m;
-    fill_transforms_kernel<<<(unsigned)((mm + 255) / 256), 256, 0, s>>>(m, Tt.ld, tab, tmp, tmp + m,
-                                                                       Tt.planes, T.planes);
+    fill_transforms_kernel<<<(unsigned)((mm + 255) / 256), 256, 0, s>>>(m, ts.Tt.ld, tab, tmp,
+                                                                       tmp + m, ts.Tt.planes,
+                                                                       ts.T.planes);
     count_launch();
     AR_CUDA(cudaGetLastError());
     AR_CUDA(cudaFreeAsync(tmp, s));
@@ -537,28 +612,24 @@ ar_status build_transforms(int m, Operand& Tt, Operand& T, cudaStream_t s) {
     return AR_OK;
 }
 
-// The transform operands depend only on the side length: they are built once
-// per (device, m) and kept for the life of the process.
-struct TransformPair {
-    Operand Tt, T;
-};
-
-ar_status cached_transforms(int m, cudaStream_t s, TransformPair* out) {
+// The transform operands depend only on the side length and the BC: they are
+// built once per (device, m, bc) and kept for the life of the process.
+ar_status cached_transforms(int m, int bc, cudaStream_t s, TransformSet* out) {
     static std::mutex mu;
-    static std::map<std::pair<int, int>, TransformPair> cache;
+    static std::map<std::tuple<int, int, int>, TransformSet> cache;
     int dev = 0;
     AR_CUDA(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lock(mu);
-    auto it = cache.find({dev, m});
+    const auto key = std::make_tuple(dev, m, bc);
+    auto it = cache.find(key);
     if (it == cache.end()) {
-        TransformPair tp;
-        ar_status st = build_transforms(m, tp.Tt, tp.T, s);
+        TransformSet ts;
+        ar_status st = build_transforms(m, bc, ts, s);
         if (st != AR_OK) {
-            cudaFree(tp.Tt.planes);
-            cudaFree(tp.T.planes);
+            free_set(ts);
             return st;
         }
-        it = cache.emplace(std::make_pair(dev, m), tp).first;
+        it = cache.emplace(key, ts).first;
     }
     *out = it->second;
     return AR_OK;
@@ -595,29 +666,37 @@ ar_status contract(int np, const Operand& A, const Operand& B, const Operand* O,
 
 struct TransformPlan {
     int n1, n2;
+    int bc;
     int np;                    // bf16 planes per operand: 3 (float32-grade) or 2 (fast)
     Operand Tt1, T1, Tt2, T2;  // constant operands (B side), owned by the process-wide cache
+    Operand Tp1, Tp2;          // Periodic: flipped synthesis operands (cache-owned)
     Operand P;                 // n1 x n2 images: Y, then W          (A side)
+    Operand P2;                // Periodic: n1 x n2, the odd-part filtered spectrum
     Operand Qo;                // n2 x n1 images: U^T, then V^T      (A side)
     int* err = nullptr;
 };
 
-ar_status transform_plan_create(int n1, int n2, int precision, cudaStream_t s, TransformPlan** out) {
+ar_status transform_plan_create(int n1, int n2, int bc, int precision, cudaStream_t s,
+                                TransformPlan** out) {
     TransformPlan* p = new (std::nothrow) TransformPlan();
     if (!p) return fail(AR_ERR_ALLOC, "host allocation of the transform plan");
     p->n1 = n1;
     p->n2 = n2;
+    p->bc = bc;
     p->np = precision == AR_PRECISION_BF16X2 ? 2 : 3;
-    TransformPair t1, t2;
-    ar_status st = cached_transforms(n1, s, &t1);
-    if (st == AR_OK) st = cached_transforms(n2, s, &t2);
+    TransformSet t1, t2;
+    ar_status st = cached_transforms(n1, bc, s, &t1);
+    if (st == AR_OK) st = cached_transforms(n2, bc, s, &t2);
     if (st == AR_OK) {
         p->Tt1 = t1.Tt;
         p->T1 = t1.T;
+        p->Tp1 = t1.Tp;
         p->Tt2 = t2.Tt;
         p->T2 = t2.T;
+        p->Tp2 = t2.Tp;
     }
     if (st == AR_OK) st = alloc_operand(p->P, n1, n2, BM, s);
+    if (st == AR_OK && bc == AR_BC_PERIODIC) st = alloc_operand(p->P2, n1, n2, BM, s);
     if (st == AR_OK) st = alloc_operand(p->Qo, n2, n1, BM, s);
     if (st == AR_OK && cudaMallocAsync((void**)&p->err, sizeof(int), s) != cudaSuccess)
         st = fail(AR_ERR_ALLOC, "transform error flag");
@@ -634,6 +713,7 @@ ar_status transform_plan_create(int n1, int n2, int precision, cudaStream_t s, T
 void transform_plan_destroy(TransformPlan* p) {
     if (!p) return;
     cudaFree(p->P.planes);
+    cudaFree(p->P2.planes);
     cudaFree(p->Qo.planes);
     cudaFree(p->err);
     delete p;
@@ -647,12 +727,25 @@ uint16_t* transform_input_planes(TransformPlan* p, size_t* plane_stride, int* ld
 
 int* transform_error_flag(TransformPlan* p) { return p->err; }
 
-int transform_launches(const TransformPlan*, DInput din) { return din == DIN_FP32 ? 5 : 4; }
+int transform_launches(const TransformPlan* p, DInput din) {
+    return (din == DIN_FP32 ? 1 : 0) + (p->bc == AR_BC_PERIODIC ? 7 : 4);
+}
 
-ar_status transform_apply(TransformPlan* p, const float* d32, const float* y, DInput din,
-                          float* out, DOutput dout, float tau, cudaStream_t s,
-                          const float* f, double* sumsq) {
+// AR / Reflective: D y = T1 (d o (Tt1 Y Tt2^T)) T2^T in four contractions
+// G1..G4.  Periodic (circulant with the even filter d(-k) = d(k)): with the
+// normalised separable Hartley matrix H (symmetric, H H = I) and Y^ = H Y H^T,
+//   D y = H (d_e o Y^) H^T - H' (d_o o Y^) H'^T,
+// where d_e is the part of d even in each frequency (diagonal in the
+// separable Hartley basis) and d_o the part odd in both (which maps the
+// Hartley basis vector of (k1, k2) to minus that of (-k1, -k2), whose matrix
+// is H' = H with its columns at -k).  Seven contractions: G1, G2 (d_e) and
+// G2' (-d_o, into P2) share Y^; G3, G4 and G3', G4' (added) synthesise.
+ar_status transform_apply(TransformPlan* p, const float* d32, const float* d32_odd,
+                          const float* y, DInput din, float* out, DOutput dout, float tau,
+                          cudaStream_t s, const float* f, double* sumsq) {
     const int n1 = p->n1, n2 = p->n2;
+    const bool periodic = p->bc == AR_BC_PERIODIC;
+    if (periodic && !d32_odd) return fail(AR_ERR_INVALID_ARG, "periodic filter without odd part");
     if (din == DIN_FP32) {
         const size_t n = (size_t)n1 * n2;
         ProfScope prof(AR_PROF_OTHER, s);
@@ -676,6 +769,11 @@ ar_status transform_apply(TransformPlan* p, const float* d32, const float* y, DI
     e.d = d32;
     e.ldd = n2;
     AR_TRY(contract(p->np, p->Qo, p->Tt1, &p->P, e, p->err, s));
+    if (periodic) {    // G2': W' = (-d_o) o (U^T T~1^T)^T -> P2 planes
+        e.planes = p->P2.planes;
+        e.d = d32_odd;
+        AR_TRY(contract(p->np, p->Qo, p->Tt1, &p->P2, e, p->err, s));
+    }
     // G3: V^T = (W T2^T)^T -> Q planes
     e.mode = TE_SPLIT_T;
     e.planes = p->Qo.planes;
@@ -683,16 +781,28 @@ ar_status transform_apply(TransformPlan* p, const float* d32, const float* y, DI
     e.ld = p->Qo.ld;
     e.d = nullptr;
     AR_TRY(contract(p->np, p->P, p->T2, &p->Qo, e, p->err, s));
-    // G4: out (=|+= tau) (V^T T1^T)^T
-    e.mode = dout == DOUT_STORE ? TE_STORE_T : TE_AXPY_T;
-    e.out = out;
-    e.ldo = n2;
-    e.tau = tau;
-    if (dout == DOUT_AXPY) {
-        e.f = f;
-        e.sumsq = f ? sumsq : nullptr;
+    // G4: out (=|+= tau) (V^T T1^T)^T; the RRE sum rides on the last update of x
+    TcEpiArgs e4{};
+    e4.mode = dout == DOUT_STORE ? TE_STORE_T : TE_AXPY_T;
+    e4.out = out;
+    e4.ldo = n2;
+    e4.tau = tau;
+    if (dout == DOUT_AXPY && !periodic) {
+        e4.f = f;
+        e4.sumsq = f ? sumsq : nullptr;
     }
-    AR_TRY(contract(p->np, p->Qo, p->T1, nullptr, e, p->err, s));
+    AR_TRY(contract(p->np, p->Qo, p->T1, nullptr, e4, p->err, s));
+    if (periodic) {
+        // G3': V'^T = (W' H'2^T)^T -> Q planes;  G4': out += tau (V'^T H'1^T)^T
+        AR_TRY(contract(p->np, p->P2, p->Tp2, &p->Qo, e, p->err, s));
+        e4.mode = TE_AXPY_T;
+        e4.tau = dout == DOUT_STORE ? 1.f : tau;
+        if (dout == DOUT_AXPY) {
+            e4.f = f;
+            e4.sumsq = f ? sumsq : nullptr;
+        }
+        AR_TRY(contract(p->np, p->Qo, p->Tp1, nullptr, e4, p->err, s));
+    }
     return AR_OK;
 }
 

@@ -124,3 +124,28 @@ def test_binding_refuses_cpu_tensors():
     x = torch.zeros(8, 8)
     with pytest.raises(TypeError):
         ar.ar_blur_apply(x, torch.ones(3, 3))
+
+
+def test_bc_validation(L):
+    args = (FAKE, FAKE * 4, 8, 8, FAKE * 16, 1, 1)
+    for bc in (-1, 3):
+        assert L.ar_blur_apply_bc(*args, bc, None) == 1
+        assert L.ar_reblur_apply_bc(*args, bc, None) == 1
+    for bc in (1, 2):
+        assert L.ar_blur_apply_bc(FAKE, FAKE + 4, 8, 8, FAKE * 16, 1, 1, bc, None) == 2
+        assert L.ar_blur_apply_bc(FAKE, FAKE * 4, 8, 8, FAKE * 16, 8, 1, bc, None) == 1
+    out = ctypes.c_void_p()
+    h = _psf(1, 1)
+    assert L.ar_symprec_setup_bc(h.ctypes.data, 1, 1, 8, 8, 0.1, 3, 0, None,
+                                 ctypes.byref(out)) == 1
+    assert L.ar_symprec_setup_bc(h.ctypes.data, 1, 1, 8, 8, 0.1, 1, 7, None,
+                                 ctypes.byref(out)) == 1          # unknown precision
+    h6 = _psf(6, 6)
+    assert L.ar_symprec_setup_bc(h6.ctypes.data, 6, 6, 6, 6, 0.1, 1, 0, None,
+                                 ctypes.byref(out)) == 1          # q > n - 1
+    assert out.value is None
+    hp = _psf(2, 2).ctypes.data
+    assert L.ar_restore_bc(FAKE, hp, 16, 16, 2, 2, 0.1, 1.0, 3, 5, 1, 0, None, None,
+                           FAKE * 64, None, None, None) == 1      # unknown bc
+    assert L.ar_restore_bc(FAKE, hp, 16, 16, 2, 2, 0.1, 1.0, 3, 1, 1, 0, None, None,
+                           FAKE + 64, None, None, None) == 2      # x_out overlaps g
