@@ -216,6 +216,21 @@ __device__ __forceinline__ uint64_t desc_k_sw128(uint32_t saddr) {
     return d;
 }
 
+// Shared-memory matrix descriptor of a K-major operand tile written by TMA with
+// 64-byte swizzling: rows of 64 bytes (32 bf16), 8-row swizzle atoms of 512
+// bytes stacked along M/N (stride byte offset 512).  The tile base must be
+// 512-byte aligned; the K offset of a 16-element MMA slice (32 bytes) is added
+// to the start address.
+__device__ __forceinline__ uint64_t desc_k_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);          // start address
+    d |= (uint64_t)1u << 16;                          // leading byte offset (unused)
+    d |= (uint64_t)(512u >> 4) << 32;                 // stride byte offset
+    d |= (uint64_t)1u << 46;                          // descriptor version
+    d |= (uint64_t)4u << 61;                          // 64-byte swizzle
+    return d;
+}
+
 // Instruction descriptor, kind::f16: D f32, A and B bf16, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4)                       // D format f32

@@ -28,16 +28,18 @@
 // contraction is as accurate as a float32 one.
 //
 // Kernel: one 128 x 128 output tile per pair of CTAs (a cluster of two that
-// splits K in halves; tcgen05.mma M = 128, N = 128, K = 16; four TMEM
-// accumulators taking the k-blocks in turn), operands staged by TMA (one 3D
-// box loads the three planes of a 128-byte-swizzled K-major tile), a 2-stage
-// mbarrier pipeline between a TMA producer thread and an MMA issuer thread,
-// and an epilogue in which each CTA sends the peer's half of its partial tile
-// through distributed shared memory, adds the half it receives, and writes its
-// half transposed (coalesced along the tile's M index) with the next step
-// fused: the bf16x3 split of the next operand, the filter d, or
-// x += tau * result.  Full-rate MMA at M = 128 needs N >= 128: with smaller N
-// the six products' operand reads exceed the shared-memory bandwidth.
+// splits K in halves; tcgen05.mma M = 128, K = 16, with N = 256 over the
+// back-to-back B planes b0 b1 where a product pair shares its A plane; four
+// TMEM accumulators in two pairs taking the k-blocks in turn), operands staged
+// by TMA (one 3D box loads the planes of a 64-byte-swizzled K-major tile of 32
+// columns), a 4-stage (6 in the two-plane mode) mbarrier pipeline between a
+// TMA producer thread and an MMA issuer thread, and an epilogue in which each
+// CTA sends the peer's half of its partial tile through distributed shared
+// memory, adds the half it receives, and writes its half transposed
+// (coalesced along the tile's M index) with the next step fused: the bf16x3
+// split of the next operand, the filter d, or x += tau * result.  Full-rate
+// MMA at M = 128 needs N >= 128: with smaller N the six products' operand
+// reads exceed the shared-memory bandwidth.
 
 #include "ar_internal.cuh"
 #include "ar_tc.cuh"
@@ -56,45 +58,40 @@
 namespace ar {
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64;
+// K-blocks of 32 (64-byte rows, 64-byte swizzle): small stages let more of the
+// shared memory be in flight while the tensor core reads one stage.
+constexpr int BM = 128, BN = 128, BK = 32;
 constexpr int MAX_PLANES = 3;                             // operand buffers hold three bf16 planes
-constexpr uint32_t A_PLANE = BM * BK * 2;                 // 16 KiB
-constexpr uint32_t B_PLANE = BN * BK * 2;                 // 16 KiB
+constexpr uint32_t A_PLANE = BM * BK * 2;                 // 8 KiB
+constexpr uint32_t B_PLANE = BN * BK * 2;                 // 8 KiB
 // Split-K over the two CTAs of a cluster: CTA r accumulates its half of the
 // k-blocks, then finishes columns [r*HALF, (r+1)*HALF) of the tile after
 // receiving the peer's partial sums for them through distributed shared memory.
 constexpr int SPLITK = 2;
 constexpr int HALF = BN / SPLITK;
 constexpr uint32_t RECV_BYTES = HALF * BM * 4;            // 32 KiB, column-major [HALF][BM]
-// k-blocks are spread round-robin over NACC accumulators of BN columns each,
-// summed with round-to-nearest float32 adds in the epilogue: the tensor core's
-// float32 accumulation loses up to an ulp per accumulate step, so fewer steps
-// per accumulator keep a K = 1024 contraction at float32-grade accuracy.
+// The products are spread over NACC accumulators of BN columns each (two
+// pairs, alternating by k-block; within a pair the b0 and b1 products go to
+// different halves), summed with round-to-nearest float32 adds in the
+// epilogue: the tensor core's float32 accumulation loses up to an ulp per
+// accumulate step, so fewer steps per accumulator keep a K = 1024 contraction
+// at float32-grade accuracy.
 constexpr int NACC = 4;
 constexpr uint32_t TMEM_COLS = NACC * BN;                 // 512: the whole TMEM of the SM
 
 // Precision modes.  NP = 3: three bf16 planes per operand, the six products
-// a_i b_j with i + j <= 2 (float32-grade).  NP = 2: two planes, the three
-// products with i + j <= 1 (about 2^-16 relative; the smaller stages leave
-// room for a third pipeline stage).
+// a_i b_j with i + j <= 2 (float32-grade), four 48 KiB stages.  NP = 2: two
+// planes, the three products with i + j <= 1 (about 2^-16 relative), six
+// 32 KiB stages.
 template <int NP>
 struct TcMode {
     static constexpr int PLANES = NP;
-    static constexpr int NPROD = NP == 3 ? 6 : 3;
-    static constexpr int STAGES = NP == 3 ? 2 : 3;
+    static constexpr int STAGES = NP == 3 ? 4 : 6;
     static constexpr uint32_t A_STAGE = PLANES * A_PLANE;
     static constexpr uint32_t B_STAGE = PLANES * B_PLANE;
-    static constexpr uint32_t STAGE_BYTES = A_STAGE + B_STAGE;   // 96 KiB / 64 KiB
+    static constexpr uint32_t STAGE_BYTES = A_STAGE + B_STAGE;   // 48 KiB / 32 KiB
     static constexpr uint32_t CTRL_BYTES = 8 * (2 * STAGES + 1) + 16;
     static constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + RECV_BYTES + CTRL_BYTES + 1024;
-    // product t uses plane pa(t) of A and pb(t) of B, smallest terms first
-    __host__ __device__ static constexpr int pa(int t) {
-        return NP == 3 ? (t == 0 ? 2 : t == 1 ? 1 : t == 2 ? 0 : t == 3 ? 1 : 0) : (t == 0 ? 1 : 0);
-    }
-    __host__ __device__ static constexpr int pb(int t) {
-        return NP == 3 ? (t == 0 ? 0 : t == 1 ? 1 : t == 2 ? 2 : t == 3 ? 0 : t == 4 ? 1 : 0)
-                       : (t == 1 ? 1 : 0);
-    }
 };
 static_assert(TcMode<3>::SMEM_BYTES <= 232448 && TcMode<2>::SMEM_BYTES <= 232448, "smem budget");
 
@@ -155,7 +152,7 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     constexpr uint32_t STAGE_BYTES = Mode::STAGE_BYTES;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
-    const uint32_t base = (raw + 1023u) & ~1023u;         // 128B-swizzled tiles need 1 KiB alignment
+    const uint32_t base = (raw + 1023u) & ~1023u;         // swizzled tiles need 512 B alignment
     uint8_t* gbase = smem_raw + (base - raw);
     const uint32_t recv = base + STAGES * STAGE_BYTES;
     const float* recv_ptr = reinterpret_cast<const float*>(gbase + STAGES * STAGE_BYTES);
@@ -226,8 +223,15 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
             if (!mbar_wait(bars + 8u * (kb % STAGES), (kb / STAGES) & 1)) *sflag = 1;
     } else if (warp == 1 && lane == 0) {
-        // ---- MMA issuer
-        const uint32_t idesc = idesc_bf16_f32(BM, BN);
+        // ---- MMA issuer.  The B planes b0 and b1 lie back to back in shared
+        // memory, so one N = 256 MMA forms a_i b0 and a_i b1 into the two
+        // halves of an accumulator pair; k-blocks alternate between two pairs
+        // (the four accumulators of the epilogue).  Per 16-wide k slice:
+        //   NP = 3: a1 [b0 b1], a2 b0 (first half), a0 b2 (second half), a0 [b0 b1]
+        //   NP = 2: a0 [b0 b1], a1 b0 (first half)
+        // The first MMA into a pair covers both halves and initialises them.
+        const uint32_t idesc128 = idesc_bf16_f32(BM, BN);
+        const uint32_t idesc256 = idesc_bf16_f32(BM, 2 * BN);
         for (int kb = 0; kb < nk; ++kb) {
             const int s = kb % STAGES;
             if (!mbar_wait(bars + 8u * s, (kb / STAGES) & 1)) {
@@ -237,14 +241,21 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             fence_after_sync();
             const uint32_t a = base + s * STAGE_BYTES;
             const uint32_t b = a + A_STAGE;
-            const uint32_t d = tmem + (uint32_t)(kb % NACC) * BN;
+            const uint32_t d0 = tmem + (uint32_t)(kb & 1) * (2 * BN);
+            const uint32_t d1 = d0 + BN;
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
-#pragma unroll
-                for (int t = 0; t < Mode::NPROD; ++t) {
-                    const uint64_t ad = desc_k_sw128(a + Mode::pa(t) * A_PLANE + kk * 32);
-                    const uint64_t bd = desc_k_sw128(b + Mode::pb(t) * B_PLANE + kk * 32);
-                    mma_bf16(d, ad, bd, idesc, (kb >= NACC || kk != 0 || t != 0) ? 1u : 0u);
+                const uint32_t acc = (kb >= 2 || kk != 0) ? 1u : 0u;
+                const uint64_t b0 = desc_k_sw64(b + kk * 32);
+                if (NP == 3) {
+                    mma_bf16(d0, desc_k_sw64(a + A_PLANE + kk * 32), b0, idesc256, acc);
+                    mma_bf16(d0, desc_k_sw64(a + 2 * A_PLANE + kk * 32), b0, idesc128, 1u);
+                    mma_bf16(d1, desc_k_sw64(a + kk * 32), desc_k_sw64(b + 2 * B_PLANE + kk * 32),
+                             idesc128, 1u);
+                    mma_bf16(d0, desc_k_sw64(a + kk * 32), b0, idesc256, 1u);
+                } else {
+                    mma_bf16(d0, desc_k_sw64(a + kk * 32), b0, idesc256, acc);
+                    mma_bf16(d0, desc_k_sw64(a + A_PLANE + kk * 32), b0, idesc128, 1u);
                 }
             }
             mma_commit(bars + 8u * (STAGES + s));        // frees the stage when its MMAs finish
@@ -287,7 +298,7 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     fence_after_sync();
     pdl_trigger();
     const bool ok = ready && *sflag == 0;
-    const int nacc = ok ? (nk < NACC ? nk : NACC) : 0;
+    const int nacc = ok ? (2 * nk < NACC ? 2 * nk : NACC) : 0;
     const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
 
     // 1) the peer's columns -> the peer's receive buffer [HALF][BM]
@@ -518,7 +529,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 int round_up8(int v) { return (v + 7) & ~7; }
 
 // 3D map over bf16x3 planes {K (inner), rows, 3 planes} with box
-// {box_k, box_rows, 3}: 128-byte swizzle for operand loads, none for stores.
+// {box_k, box_rows, 3}: 64-byte swizzle for operand loads, none for stores.
 ar_status make_map(CUtensorMap* map, const uint16_t* planes, int K, int rows, int ld, int box_k,
                    int box_rows, int nplanes, bool swizzle) {
     auto enc = encode_fn();
@@ -529,7 +540,7 @@ ar_status make_map(CUtensorMap* map, const uint16_t* planes, int K, int rows, in
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(planes), dims,
                      strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                     swizzle ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(AR_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return AR_OK;
@@ -539,7 +550,7 @@ struct Operand {               // bf16 planes of a rows x K matrix and its TMA m
     uint16_t* planes = nullptr;
     int rows = 0, K = 0, ld = 0;
     size_t pstride = 0;
-    CUtensorMap map[2];        // operand loads, [0]: 3 planes, [1]: 2 planes; box {BK, box_rows, np}, 128B swizzle
+    CUtensorMap map[2];        // operand loads, [0]: 3 planes, [1]: 2 planes; box {BK, box_rows, np}, 64B swizzle
     CUtensorMap omap[2];       // epilogue stores (image operands): box {BM, HALF, np}
 };
 
