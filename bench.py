@@ -246,6 +246,7 @@ def run_own(args):
             if not args.no_batch:
                 out["forms"]["batched"] = batched_form(ar, torch, dev, stream, flush, 3)
             out["bcs"] = bcs_form(ar, torch, stream, g_d, f_d, h, flush, max(args.steps // 2, 3))
+            out["matvec_hbm"] = matvec_hbm_form(ar, torch, dev, stream)
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(h, g, f)
     if world > 1:
@@ -255,6 +256,16 @@ def run_own(args):
         print(json.dumps(out), flush=True)
 
 
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+PEAKS = load_peaks()
+
+
 def kernel_rooflines(ar, torch, dev, step):
     """Device time per kernel class over one profiled step of the same workload.
 
@@ -262,11 +273,7 @@ def kernel_rooflines(ar, torch, dev, step):
     stream (profiled kernels run serialized, without dependent-launch overlap).
     The dominant class is the one with the largest share of the step.
     """
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
+    peaks = PEAKS
     bf16 = peaks.get("bf16_tflops")
     smax = peaks.get("sm_max_mhz", 2070.0)
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -417,6 +424,44 @@ def batched_form(ar, torch, dev, stream, flush, runs):
                            "ms_per_batch": round(t_seq, 3)},
             "speedup": round(t_seq / t_batch, 2), "identical_results": bool(same),
             "median_best_iter": int(np.median(best))}
+
+
+MATVEC_SIDE = 8192      # 256 MiB per image: input and output are both far larger than L2
+
+
+def matvec_hbm_form(ar, torch, dev, stream, reps=10):
+    """The AR matvec y = A_n x alone where it is byte-bound: small PSFs on an
+    8192^2 image (in + out = 512 MiB per call, no L2 reuse across calls).
+    Achieved bytes = 8 B per pixel (one read of x, one write of y) over the
+    CUDA-event time of one call, against the measured copy bandwidth."""
+    n = MATVEC_SIDE
+    x = torch.rand(n, n, device=dev)
+    y = torch.empty_like(x)
+    peak = PEAKS.get("hbm_gbs")
+    out = {}
+    for q in (1, 2, 3):
+        a = np.arange(-q, q + 1)
+        h = np.exp(-0.5 * (a[:, None] ** 2 + a[None, :] ** 2) / max(q, 1) ** 2)
+        hd = torch.from_numpy((h / h.sum()).astype(np.float32)).to(dev)
+        for _ in range(3):
+            ar.ar_blur_apply(x, hd, y)
+        tot = 0.0
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ar.ar_blur_apply(x, hd, y)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        ms = tot / reps
+        gbs = 8.0 * n * n / (ms / 1e3) / 1e9
+        out[f"{2 * q + 1}x{2 * q + 1}"] = {
+            "us_per_call": round(ms * 1e3, 2), "achieved_gbs": round(gbs, 1),
+            "hbm_frac": round(gbs / peak, 4) if peak else None,
+            "fp32_tflops": round(2 * (2 * q + 1) ** 2 * n * n / (ms / 1e3) / 1e12, 2)}
+    out["workload"] = f"ar_blur_apply on {n}x{n} float32, Gaussian PSFs, 8 B/px algorithmic"
+    out["peak"] = f"{peak} GB/s of measured" if peak else None
+    return out
 
 
 BC_PLAIN_ITERS = 3000

@@ -366,7 +366,9 @@ ar_status ar_restore_bc(const float* g, const double* psf_host, int n1, int n2, 
 
     ar_prec* P = nullptr;
     unsigned long long bad = 0;
-    int timeout = 0;
+    int timeout = 0, conv_timeout = 0;
+    int* conv_err = conv_error_flag();
+    if (!conv_err) return fail(AR_ERR_CUDA, "stencil error flag unavailable");
     std::vector<double> sums((size_t)iters + 1, 0.0);
     ar_status st = AR_OK;
     {
@@ -383,6 +385,7 @@ ar_status ar_restore_bc(const float* g, const double* psf_host, int n1, int n2, 
                                             cudaMemcpyHostToDevice, s);
             if (e == cudaSuccess) e = cudaMemsetAsync(dsum, 0, ((size_t)iters + 1) * sizeof(double), s);
             if (e == cudaSuccess) e = cudaMemsetAsync(dbad, 0, sizeof(unsigned long long), s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(conv_err, 0, sizeof(int), s);
             if (e == cudaSuccess) {
                 if (!x0) e = cudaMemsetAsync(x_out, 0, nb, s);
                 else if (x0 != x_out) e = cudaMemcpyAsync(x_out, x0, nb, cudaMemcpyDeviceToDevice, s);
@@ -438,6 +441,8 @@ ar_status ar_restore_bc(const float* g, const double* psf_host, int n1, int n2, 
             if (e == cudaSuccess && P)
                 e = cudaMemcpyAsync(&timeout, transform_error_flag(P->plan), sizeof(int),
                                     cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(&conv_timeout, conv_err, sizeof(int), cudaMemcpyDeviceToHost, s);
             if (e != cudaSuccess) st = cuda_fail(e, "restore readback");
         }
     }
@@ -460,6 +465,7 @@ ar_status ar_restore_bc(const float* g, const double* psf_host, int n1, int n2, 
         if (best_iter) *best_iter = best;
     }
     if (timeout) return fail(AR_ERR_TIMEOUT, "a tensor-core contraction gave up waiting");
+    if (conv_timeout) return fail(AR_ERR_TIMEOUT, "a stencil gave up waiting for its halo tile");
     if (bad) return fail(AR_ERR_NONFINITE, "%llu non-finite entries in the final iterate", bad);
     return AR_OK;
 }

@@ -9,18 +9,26 @@
 // 4 x_c - 2 x - 2 x + x at the corners.  A' (Section 4, reblurring) is the same
 // operator with the PSF rotated by 180 degrees.
 //
-// The extension is never materialised: every CTA loads its halo tile into
-// shared memory (all loads of a thread in flight at once) and, on tiles that
-// reach past the image, overwrites the out-of-image samples with their
-// anti-reflections computed from in-tile samples.  Each thread then computes a vertical strip of R outputs of one
+// The extension is never materialised: every CTA brings its halo tile into
+// shared memory (by TMA, double- or triple-buffered in a persistent loop over
+// tiles, when the image rows are 16-byte aligned; otherwise by the threads,
+// all loads of a thread in flight at once) and, on tiles that reach past the
+// image, overwrites the out-of-image samples with their anti-reflections
+// computed from in-tile samples.  Each thread then computes a vertical strip of R outputs of one
 // column, sliding a register window down the tile: per PSF column it loads
 // R + 2Q values from shared memory (consecutive lanes read consecutive
 // columns: conflict-free) and issues R (2Q+1) FMAs against broadcast PSF
 // coefficients.  The kernel is FP32-FMA bound for Q >= 2.
 
 #include "ar_internal.cuh"
+#include "ar_tc.cuh"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+
+#include <cstdint>
+#include <mutex>
 
 namespace ar {
 namespace {
@@ -108,8 +116,126 @@ __device__ __forceinline__ void add_sumsq(double* sumsq, double v) {
     if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(sumsq, v);
 }
 
+// Coefficient rows are padded to a multiple of 4 so that a PSF column is
+// read with 16-byte shared-memory loads.
+template <int Q>
+struct Coefs {
+    static constexpr int K = 2 * Q + 1;
+    static constexpr int KP = (K + 3) & ~3;
+    static constexpr int COUNT = K * KP;
+};
+
+// Coefficients of the support padded to Q x Q: coef[b * KP + a] = h_{a-Q, b-Q}
+// (h_{Q-a, Q-b} for A'), zero outside the true support and in the row padding.
+template <int Q>
+__device__ __forceinline__ void load_coefs(const ConvArgs& a, float* coef, int tid, int nthreads) {
+    constexpr int KP = Coefs<Q>::KP;
+    const int kw = 2 * a.q2 + 1;
+    for (int i = tid; i < Coefs<Q>::COUNT; i += nthreads) {
+        const int b = i / KP, aa = i % KP;
+        const int s1 = aa - Q, s2 = b - Q;      // tap offsets in the padded support
+        float v = 0.f;
+        if (aa < 2 * Q + 1 && s1 >= -a.q1 && s1 <= a.q1 && s2 >= -a.q2 && s2 <= a.q2) {
+            const int t1 = a.flip ? -s1 : s1, t2 = a.flip ? -s2 : s2;
+            v = __ldg(a.psf + (t1 + a.q1) * kw + (t2 + a.q2));
+        }
+        coef[i] = v;
+    }
+}
+
+// Out-of-image samples of a halo tile that reaches past the image, from the
+// in-image samples of the same tile: tile(r, c) = tile[r * WP + c] holds the
+// image sample (r0 - Q + r, c0 - Q + c).  Rows first (on in-image columns),
+// then columns on every row of the extended domain, which gives the corner
+// rules.  AR (Section 2.2): 2 x_edge - x_mirror; Reflective (Section 2.1):
+// x_{-1-i} = x_i, x_{n+i} = x_{n-1-i}.  Edge and mirror samples lie in the tile.
+template <int Q>
+__device__ void fixup_tile(const ConvArgs& a, float* tile, int WP, int r0, int c0, int tid,
+                           int nthreads) {
+    constexpr int W = TX + 2 * Q, H = TH + 2 * Q;
+    const bool ar = a.bc == AR_BC_ANTIREFLECTIVE;
+    for (int i = tid; i < H * W; i += nthreads) {
+        const int r = i / W, c = i % W;
+        const int j1 = r0 - Q + r, j2 = c0 - Q + c;
+        if (j2 < 0 || j2 >= a.n2) continue;
+        int re, rm;
+        if (j1 < 0 && j1 >= -a.q1) { re = 0; rm = ar ? -j1 : -j1 - 1; }
+        else if (j1 >= a.n1 && j1 < a.n1 + a.q1) {
+            re = a.n1 - 1;
+            rm = ar ? 2 * (a.n1 - 1) - j1 : 2 * a.n1 - 1 - j1;
+        } else continue;
+        const float vm = tile[(rm - (r0 - Q)) * WP + c];
+        tile[r * WP + c] = ar ? 2.f * tile[(re - (r0 - Q)) * WP + c] - vm : vm;
+    }
+    __syncthreads();
+    for (int i = tid; i < H * W; i += nthreads) {
+        const int r = i / W, c = i % W;
+        const int j1 = r0 - Q + r, j2 = c0 - Q + c;
+        if (j1 < -a.q1 || j1 >= a.n1 + a.q1) continue;
+        int ce, cm;
+        if (j2 < 0 && j2 >= -a.q2) { ce = 0; cm = ar ? -j2 : -j2 - 1; }
+        else if (j2 >= a.n2 && j2 < a.n2 + a.q2) {
+            ce = a.n2 - 1;
+            cm = ar ? 2 * (a.n2 - 1) - j2 : 2 * a.n2 - 1 - j2;
+        } else continue;
+        const float vm = tile[r * WP + (cm - (c0 - Q))];
+        tile[r * WP + c] = ar ? 2.f * tile[r * WP + (ce - (c0 - Q))] - vm : vm;
+    }
+    __syncthreads();
+}
+
+// Each thread computes a vertical strip of RS outputs of one column from the
+// halo tile (row pitch WP) and applies the epilogue.
+template <int Q>
+__device__ __forceinline__ void compute_tile(const ConvArgs& a, const float* tile, int WP,
+                                             const float* coef, int r0, int c0) {
+    constexpr int K = 2 * Q + 1;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    float acc[RS];
+#pragma unroll
+    for (int r = 0; r < RS; ++r) acc[r] = 0.f;
+
+#pragma unroll 1
+    for (int b = 0; b < K; ++b) {
+        // output column tx reads tile column tx - s2 + Q = tx + 2Q - b
+        const float* col = tile + (ty * RS) * WP + tx + 2 * Q - b;
+        float win[RS + 2 * Q];
+#pragma unroll
+        for (int t = 0; t < RS + 2 * Q; ++t) win[t] = col[t * WP];
+        float hc[Coefs<Q>::KP];
+        const float4* cb = reinterpret_cast<const float4*>(coef + b * Coefs<Q>::KP);
+#pragma unroll
+        for (int j = 0; j < Coefs<Q>::KP / 4; ++j) {
+            const float4 v = cb[j];
+            hc[4 * j] = v.x;
+            hc[4 * j + 1] = v.y;
+            hc[4 * j + 2] = v.z;
+            hc[4 * j + 3] = v.w;
+        }
+#pragma unroll
+        for (int aa = 0; aa < K; ++aa) {
+            const float hv = hc[aa];
+            // output row r reads tile row r - s1 + Q = r + 2Q - aa (strip-relative)
+#pragma unroll
+            for (int r = 0; r < RS; ++r) acc[r] = fmaf(hv, win[r + 2 * Q - aa], acc[r]);
+        }
+    }
+
+    const int col = c0 + tx;
+    double sq = 0.0;
+    if (col < a.n2) {
+#pragma unroll
+        for (int r = 0; r < RS; ++r) {
+            const int row = r0 + ty * RS + r;
+            if (row < a.n1) sq += conv_epilogue(a, row, col, acc[r]);
+        }
+    }
+    if (a.sumsq) add_sumsq(a.sumsq, sq);
+}
+
 // Fast path: support padded to Q x Q (Q = max(q1, q2) <= 15, zero taps outside
-// the true support), tile TH x TX, R = RS rows per thread.
+// the true support), tile TH x TX, R = RS rows per thread; the halo tile is
+// loaded by the threads (any row pitch and alignment, every BC).
 template <int Q>
 __global__ void __launch_bounds__(TX * TY)
 conv_fast_kernel(const ConvArgs a) {
@@ -117,26 +243,17 @@ conv_fast_kernel(const ConvArgs a) {
     constexpr int H = TH + 2 * Q;        // tile rows
     constexpr int K = 2 * Q + 1;
     __shared__ float tile[H * W];
-    __shared__ float coef[K * K];        // coef[b * K + a] = h_{a-Q, b-Q} (flipped for A')
+    __shared__ __align__(16) float coef[Coefs<Q>::COUNT];   // see load_coefs
 
     const int tid = threadIdx.y * TX + threadIdx.x;
     const int r0 = blockIdx.y * TH;
     const int c0 = blockIdx.x * TX;
-    const int kw = 2 * a.q2 + 1;
 
     pdl_wait();                          // the input image comes from the previous kernel
-    for (int i = tid; i < K * K; i += TX * TY) {
-        const int b = i / K, aa = i % K;
-        const int s1 = aa - Q, s2 = b - Q;      // tap offsets in the padded support
-        float v = 0.f;
-        if (s1 >= -a.q1 && s1 <= a.q1 && s2 >= -a.q2 && s2 <= a.q2) {
-            const int t1 = a.flip ? -s1 : s1, t2 = a.flip ? -s2 : s2;
-            v = __ldg(a.psf + (t1 + a.q1) * kw + (t2 + a.q2));
-        }
-        coef[i] = v;
-    }
-    // Phase 1: every tile sample at its coordinate clamped into the image.
-    // All loads of a thread are issued before the first shared-memory store.
+    load_coefs<Q>(a, coef, tid, TX * TY);
+    // Phase 1: every tile sample at its coordinate clamped into the image
+    // (reflective / periodic samples at their mapped coordinate).  All loads
+    // of a thread are issued before the first shared-memory store.
     constexpr int NLD = (H * W + TX * TY - 1) / (TX * TY);
     {
         float v[NLD];
@@ -165,69 +282,97 @@ conv_fast_kernel(const ConvArgs a) {
         }
     }
     __syncthreads();
-    // Phase 2 (tiles that reach past the image only): the anti-reflected
-    // samples, rows first (Section 2.2 border rule on in-image columns), then
-    // columns on every row, which yields the corner rule.  Edge and mirror
-    // samples always lie inside the tile.
+    // Phase 2 (AR tiles that reach past the image only): the anti-reflected samples.
     if (a.bc == AR_BC_ANTIREFLECTIVE &&
-        (r0 - Q < 0 || r0 + TH + Q > a.n1 || c0 - Q < 0 || c0 + TX + Q > a.n2)) {
-        for (int i = tid; i < H * W; i += TX * TY) {
-            const int r = i / W, c = i % W;
-            const int j1 = r0 - Q + r, j2 = c0 - Q + c;
-            if (j2 < 0 || j2 >= a.n2) continue;
-            int re, rm;
-            if (j1 < 0 && j1 >= -a.q1) { re = 0; rm = -j1; }
-            else if (j1 >= a.n1 && j1 < a.n1 + a.q1) { re = a.n1 - 1; rm = 2 * (a.n1 - 1) - j1; }
-            else continue;
-            tile[i] = 2.f * tile[(re - (r0 - Q)) * W + c] - tile[(rm - (r0 - Q)) * W + c];
-        }
-        __syncthreads();
-        for (int i = tid; i < H * W; i += TX * TY) {
-            const int r = i / W, c = i % W;
-            const int j1 = r0 - Q + r, j2 = c0 - Q + c;
-            if (j1 < -a.q1 || j1 >= a.n1 + a.q1) continue;
-            int ce, cm;
-            if (j2 < 0 && j2 >= -a.q2) { ce = 0; cm = -j2; }
-            else if (j2 >= a.n2 && j2 < a.n2 + a.q2) { ce = a.n2 - 1; cm = 2 * (a.n2 - 1) - j2; }
-            else continue;
-            tile[i] = 2.f * tile[r * W + (ce - (c0 - Q))] - tile[r * W + (cm - (c0 - Q))];
-        }
-        __syncthreads();
-    }
-
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    float acc[RS];
-#pragma unroll
-    for (int r = 0; r < RS; ++r) acc[r] = 0.f;
-
-#pragma unroll 1
-    for (int b = 0; b < K; ++b) {
-        // output column tx reads tile column tx - s2 + Q = tx + 2Q - b
-        const float* col = tile + (ty * RS) * W + tx + 2 * Q - b;
-        float win[RS + 2 * Q];
-#pragma unroll
-        for (int t = 0; t < RS + 2 * Q; ++t) win[t] = col[t * W];
-        const float* cb = coef + b * K;
-#pragma unroll
-        for (int aa = 0; aa < K; ++aa) {
-            const float hv = cb[aa];
-            // output row r reads tile row r - s1 + Q = r + 2Q - aa (strip-relative)
-#pragma unroll
-            for (int r = 0; r < RS; ++r) acc[r] = fmaf(hv, win[r + 2 * Q - aa], acc[r]);
-        }
-    }
+        (r0 - Q < 0 || r0 + TH + Q > a.n1 || c0 - Q < 0 || c0 + TX + Q > a.n2))
+        fixup_tile<Q>(a, tile, W, r0, c0, tid, TX * TY);
 
     pdl_trigger();
-    const int col = c0 + tx;
-    double sq = 0.0;
-    if (col < a.n2) {
-#pragma unroll
-        for (int r = 0; r < RS; ++r) {
-            const int row = r0 + ty * RS + r;
-            if (row < a.n1) sq += conv_epilogue(a, row, col, acc[r]);
-        }
+    compute_tile<Q>(a, tile, W, coef, r0, c0);
+}
+
+__device__ int g_conv_timeout;
+
+// Halo tile of the TMA path: the box starts PADL >= Q columns left of the
+// tile (a multiple of 4, so the box's x coordinate is 16-byte aligned) and
+// is WB = TX + 2 PADL wide, HB = TH + 2Q high.  NBUF boxes are in flight or
+// in use per CTA (three for 4 <= Q <= 7, measured faster on 4096^2 images;
+// two otherwise, where more buffers cost resident CTAs).
+template <int Q>
+struct TmaTile {
+    static constexpr int PADL = (Q + 3) & ~3;
+    static constexpr int WB = TX + 2 * PADL;
+    static constexpr int HB = TH + 2 * Q;
+    static constexpr uint32_t BYTES = (uint32_t)WB * HB * 4;
+    static constexpr uint32_t BUF = (BYTES + 127u) & ~127u;   // buffers start 128-byte aligned
+    static constexpr int NBUF = (Q >= 4 && Q <= 7) ? 3 : 2;
+    static constexpr size_t SMEM = NBUF * (size_t)BUF + (size_t)Coefs<Q>::COUNT * 4 + 8 * NBUF + 128;
+};
+
+// Persistent TMA path (AR and Reflective, 16-byte aligned rows): each CTA
+// walks the tiles t = blockIdx.x + i gridDim.x; thread 0 keeps the halo boxes
+// of the next NBUF - 1 tiles requested by TMA (zeros outside the image) while
+// the CTA works on the current one.  Out-of-image samples of the extended
+// domain are then filled in shared memory.
+template <int Q>
+__global__ void __launch_bounds__(TX * TY)
+conv_tma_kernel(const __grid_constant__ CUtensorMap tmx, const ConvArgs a, int ntx, int ntiles) {
+    using namespace tc;
+    using T = TmaTile<Q>;
+    constexpr int WB = T::WB, NBUF = T::NBUF;
+    extern __shared__ __align__(128) uint8_t smem_raw_c[];
+    // TMA destinations: 128-byte aligned (the allocation has 128 bytes of slack)
+    uint8_t* sbase = smem_raw_c + ((128u - (smem_u32(smem_raw_c) & 127u)) & 127u);
+    float* coef = reinterpret_cast<float*>(sbase + NBUF * T::BUF);
+    const uint32_t bar0 = smem_u32(coef + Coefs<Q>::COUNT);   // NBUF mbarriers, 8 bytes apart
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    auto buffer = [&](int i) { return reinterpret_cast<float*>(sbase + i * T::BUF); };
+
+    if (tid == 0) {
+        for (int i = 0; i < NBUF; ++i) mbar_init(bar0 + 8u * i, 1);
+        fence_mbar_init();
+        prefetch_tmap(&tmx);
     }
-    if (a.sumsq) add_sumsq(a.sumsq, sq);
+    load_coefs<Q>(a, coef, tid, TX * TY);
+    __syncthreads();
+    pdl_wait();                          // the input image comes from the previous kernel
+
+    // local tile i of this CTA is t = blockIdx.x + i gridDim.x, in buffer i % NBUF
+    auto request = [&](int i) {
+        const int t = blockIdx.x + i * gridDim.x;
+        const int r0 = (t / ntx) * TH, c0 = (t % ntx) * TX;
+        const uint32_t bar = bar0 + 8u * (i % NBUF);
+        fence_proxy_async_smem();        // generic writes to the buffer (fix-up) before the async copy
+        mbar_arrive_expect_tx(bar, T::BYTES);
+        tma_load_2d(smem_u32(buffer(i % NBUF)), &tmx, c0 - T::PADL, r0 - Q, bar);
+    };
+    const int nmine = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    if (tid == 0)
+        for (int i = 0; i < NBUF - 1 && i < nmine; ++i) request(i);
+    int li = 0;
+    bool failed = false;
+    for (; li < nmine; ++li) {
+        if (tid == 0 && li + NBUF - 1 < nmine) request(li + NBUF - 1);   // buffer of tile li-1
+        const bool ok = mbar_wait(bar0 + 8u * (li % NBUF), (li / NBUF) & 1);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        const int t = blockIdx.x + li * gridDim.x;
+        const int r0 = (t / ntx) * TH, c0 = (t % ntx) * TX;
+        float* tile = buffer(li % NBUF) + (T::PADL - Q);
+        if (r0 - Q < 0 || r0 + TH + Q > a.n1 || c0 - Q < 0 || c0 + TX + Q > a.n2)
+            fixup_tile<Q>(a, tile, WB, r0, c0, tid, TX * TY);
+        if (li == nmine - 1) pdl_trigger();
+        compute_tile<Q>(a, tile, WB, coef, r0, c0);
+        __syncthreads();                 // the buffer is refilled for tile li + NBUF
+    }
+    if (failed && tid == 0) {
+        atomicExch(&g_conv_timeout, 1);
+        // copies still in flight (tiles li + 1 .. li + NBUF - 1): wait for them (bounded)
+        for (int i = li + 1; i < li + NBUF && i < nmine; ++i)
+            mbar_wait(bar0 + 8u * (i % NBUF), (i / NBUF) & 1);
+    }
 }
 
 // Generic path for large supports: one output per thread, taps read straight
@@ -253,14 +398,66 @@ conv_generic_kernel(const ConvArgs a) {
     if (a.sumsq) add_sumsq(a.sumsq, sq);
 }
 
+// TMA map of the float32 image x (n1 rows of n2) with the halo box of Q.
+template <int Q>
+bool make_image_map(const ConvArgs& a, CUtensorMap* map) {
+    auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder());
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)a.n2, (cuuint64_t)a.n1};
+    cuuint64_t strides[1] = {(cuuint64_t)a.n2 * 4};
+    cuuint32_t box[2] = {(cuuint32_t)TmaTile<Q>::WB, (cuuint32_t)TmaTile<Q>::HB};
+    cuuint32_t es[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(a.x), dims, strides, box,
+               es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int Q>
 cudaError_t launch_fast(const ConvArgs& a, cudaStream_t s) {
+    // TMA path: AR / Reflective, 16-byte aligned image and row pitch
+    if (a.bc != AR_BC_PERIODIC && (reinterpret_cast<uintptr_t>(a.x) & 15) == 0 &&
+        (a.n2 & 3) == 0) {
+        using T = TmaTile<Q>;
+        static std::once_flag once;
+        static cudaError_t attr = cudaSuccess;
+        static int per_sm = 1;
+        std::call_once(once, [] {
+            attr = cudaFuncSetAttribute(conv_tma_kernel<Q>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
+            if (attr == cudaSuccess)
+                attr = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_tma_kernel<Q>,
+                                                                     TX * TY, T::SMEM);
+            if (per_sm < 1) per_sm = 1;
+        });
+        CUtensorMap map;
+        if (attr == cudaSuccess && make_image_map<Q>(a, &map)) {
+            const int ntx = (a.n2 + TX - 1) / TX, nty = (a.n1 + TH - 1) / TH;
+            const int ntiles = ntx * nty;
+            const int cap = sm_count() * per_sm;
+            const int grid = ntiles < cap ? ntiles : cap;
+            count_launch();
+            return launch_pdl(conv_tma_kernel<Q>, dim3(grid), dim3(TX, TY), T::SMEM, s, map, a,
+                              ntx, ntiles);
+        }
+    }
     dim3 grid((a.n2 + TX - 1) / TX, (a.n1 + TH - 1) / TH);
     count_launch();
     return launch_pdl(conv_fast_kernel<Q>, grid, dim3(TX, TY), 0, s, a);
 }
 
 }  // namespace
+
+int* conv_error_flag() {
+    static int* p[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!p[dev]) {
+        void* q = nullptr;
+        if (cudaGetSymbolAddress(&q, g_conv_timeout) == cudaSuccess) p[dev] = static_cast<int*>(q);
+    }
+    return p[dev];
+}
 
 ar_status conv_launch(const ConvArgs& a, cudaStream_t s) {
     if (a.n1 <= 0 || a.n2 <= 0) return AR_OK;

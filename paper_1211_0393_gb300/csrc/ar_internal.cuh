@@ -84,6 +84,13 @@ struct ConvArgs {
 // Launches the AR stencil on `stream` (validated arguments).
 ar_status conv_launch(const ConvArgs& a, cudaStream_t stream);
 
+// Device int set to 1 by a stencil kernel whose bounded TMA wait gave up
+// (cleared by the caller that reads it).
+int* conv_error_flag();
+
+// cuTensorMapEncodeTiled from the driver (null if unavailable), as void*.
+void* tensor_map_encoder();
+
 // ------------------------------------------------------------ transform ---
 // The transform pair of a boundary condition for one image size, applied as
 // dense contractions (four for AR and Reflective, seven for Periodic).

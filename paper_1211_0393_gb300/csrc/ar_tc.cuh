@@ -1,6 +1,7 @@
 // Thin inline-PTX wrappers for the sm_103a tensor-core path: mbarriers with
 // bounded waits, TMA tensor loads, tcgen05 MMA / commit / TMEM management and
-// the shared-memory matrix descriptor.  Only used by ar_transform.cu.
+// the shared-memory matrix descriptor.  Used by ar_transform.cu (contractions)
+// and ar_conv.cu (TMA halo tiles of the stencil).
 #pragma once
 
 #include <cstdint>
@@ -53,6 +54,17 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* tmap, int 
         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
         " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
         "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+
+// 2D tiled TMA load global -> shared, completion on an mbarrier (out-of-range
+// elements of the box are filled with zeros).
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int c0, int c1,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(bar)
         : "memory");
 }
 

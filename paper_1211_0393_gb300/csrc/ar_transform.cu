@@ -512,7 +512,9 @@ __global__ void split_image_kernel(const float* __restrict__ y, int n1, int n2, 
 }
 
 // ------------------------------------------------------------ host side --
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+}  // namespace
+
+void* tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static std::once_flag once;
     std::call_once(once, [] {
@@ -523,7 +525,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
             q == cudaDriverEntryPointSuccess)
             fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
     });
-    return fn;
+    return reinterpret_cast<void*>(fn);
+}
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder());
 }
 
 int round_up8(int v) { return (v + 7) & ~7; }
