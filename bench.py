@@ -247,6 +247,8 @@ def run_own(args):
                 out["forms"]["batched"] = batched_form(ar, torch, dev, stream, flush, 3)
             out["bcs"] = bcs_form(ar, torch, stream, g_d, f_d, h, flush, max(args.steps // 2, 3))
             out["matvec_hbm"] = matvec_hbm_form(ar, torch, dev, stream)
+            out["forms"]["precision_2048"] = precision_2048_form(ar, torch, dev, stream, flush,
+                                                                 max(args.steps // 4, 2))
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(h, g, f)
     if world > 1:
@@ -424,6 +426,57 @@ def batched_form(ar, torch, dev, stream, flush, runs):
                            "ms_per_batch": round(t_seq, 3)},
             "speedup": round(t_seq / t_batch, 2), "identical_results": bool(same),
             "median_best_iter": int(np.median(best))}
+
+
+PREC4_ALPHA = 0.1      # smallest half-decade alpha for which tau = 1 is stable with the 21x21 PSF
+
+
+def precision_2048_form(ar, torch, dev, stream, flush, steps):
+    """The 2048^2 precision workload (ellipses, 21x21 asymmetric Gaussian PSF,
+    1% noise, 50 D-Landweber iterations): throughput and restoration error of
+    the float32-grade (bf16x3) and fast (bf16x2) contractions, and how far the
+    fast iterates drift from the float32-grade ones step by step.  (The error
+    of both against the FP64 oracle per step is checked by the GPU tests.)"""
+    wl = W.WORKLOADS["ellipses2048_gauss21"]
+    n1, n2 = wl["n"]
+    h = W.psf_config4()
+    q1, q2 = (h.shape[0] - 1) // 2, (h.shape[1] - 1) // 2
+    ext, f, e = W.make_inputs(n1, n2, h, "ellipses", wl["config_idx"])
+    blurred = ar.ar_blur_apply(torch.from_numpy(ext.astype(np.float32)).to(dev),
+                               torch.from_numpy(h.astype(np.float32)).to(dev))
+    g = W.add_noise(W.crop(blurred.cpu().numpy().astype(np.float64), q1, q2), e, wl["nu"])
+    g_d = torch.from_numpy(g.astype(np.float32)).to(dev)
+    f_d = torch.from_numpy(f.astype(np.float32)).to(dev)
+    out = {"workload": f"ellipses{n1}_gauss21: {n1}x{n2}, 21x21 asymmetric Gaussian, 1% noise, "
+                       f"alpha {PREC4_ALPHA}, {ITERS} iterations"}
+    for prec in ("fp32", "bf16x2"):
+        x = torch.empty_like(g_d)
+
+        def step():
+            return ar.ar_restore(g_d, h, PREC4_ALPHA, TAU, ITERS, True, f_true=f_d, x_out=x,
+                                 precision=prec)
+
+        for _ in range(2):
+            step()
+        tot = 0.0
+        for i in range(steps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            _, tr, best = step()
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        out[prec] = {"value": round(n1 * n2 * ITERS * steps / 1e6 / (tot / 1e3), 2), "unit": UNIT,
+                     "ms_per_step": round(tot / steps, 3), "rre_best": round(float(np.min(tr)), 6),
+                     "best_iter": best, "rre_final": round(float(tr[-1]), 6)}
+    drift = []
+    for k in (1, 2, 5, 10, 50):
+        xa, _, _ = ar.ar_restore(g_d, h, PREC4_ALPHA, TAU, k, True)
+        xb, _, _ = ar.ar_restore(g_d, h, PREC4_ALPHA, TAU, k, True, precision="bf16x2")
+        drift.append([k, float(torch.linalg.vector_norm(xb - xa) / torch.linalg.vector_norm(xa))])
+    out["bf16x2_vs_fp32_rel_l2_at_step"] = drift
+    return out
 
 
 MATVEC_SIDE = 8192      # 256 MiB per image: input and output are both far larger than L2
