@@ -6,3 +6,4 @@ library never calls it, shares no code with it, and imports nothing from it.
 """
 
 from .ar_oracle import *  # noqa: F401,F403
+from .spectral_correction import *  # noqa: F401,F403

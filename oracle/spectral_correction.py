@@ -1,0 +1,209 @@
+"""FP64 oracle of the spectral correction of the symmetrized preconditioner
+and of the small MLP that predicts it.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+The paper's optimal preconditioner (Theorem 4) replaces the PSF h by its
+symmetrized part s (eq. simmetrizzata2d); with a = h - s the antisymmetric
+part, the AR eigenvalue of frequency x is the symbol of s (eq.
+funzione_generatrice), lambda_s(x) = s^(x).  Iterating with A' A (Section 4),
+the quantity a preconditioner should invert per frequency is the response of
+A' A there.  For large images its value at an AR grid point is the average of
+|h^|^2 over the four sign flips of the frequency, and since the flip average
+of a^ is zero,
+
+    avg_flips |h^(+-x1, +-x2)|^2 = lambda_s(x)^2 + delta(x),
+    delta(x1, x2) = (|a^(x1, x2)|^2 + |a^(-x1, x2)|^2) / 2,
+
+where a^(w) = sum_s a_s exp(-i s.w).  delta >= 0 depends only on the
+antisymmetric part, and vanishes for strongly symmetric PSFs.  The corrected
+filter is d = 1/(lambda_s^2 + delta + alpha) (eq. TikFilter with the refined
+eigenvalue).  The paper has no such correction: it is the learned form's
+target, the per-frequency refinement of the symmetrized eigenvalues.
+
+The learned form predicts delta on a G x G grid of [0, pi]^2 (G = 33) from the
+antisymmetric part of a 15 x 15 PSF with a three-layer perceptron (ReLU,
+width 256), trained by mean squared error with Adam; the image's AR grid
+reads the prediction by bilinear interpolation.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+from .ar_oracle import (ar_analysis, ar_blur, ar_grid, ar_reblur, ar_synthesis, eigenvalues,
+                        psf_support, rre, symmetrize)
+
+CORR_GRID = 33                 # points per axis of the predicted table on [0, pi]
+CORR_Q = 7                     # the model takes 15 x 15 PSFs
+CORR_IN = (2 * CORR_Q + 1) ** 2
+CORR_HIDDEN = 256
+CORR_OUT = CORR_GRID * CORR_GRID
+CORR_IN_SCALE = 16.0           # inputs are 16 (h - s): O(1) entries for typical PSFs
+
+
+def antisymmetric_part(h: np.ndarray) -> np.ndarray:
+    """``a = h - s`` with ``s`` the symmetrized PSF of eq. simmetrizzata2d."""
+    h = np.asarray(h, dtype=np.float64)
+    return h - symmetrize(h)
+
+
+def spectral_energy(a: np.ndarray, x1: np.ndarray, x2: np.ndarray) -> np.ndarray:
+    """``delta(x1, x2) = (|a^(x1, x2)|^2 + |a^(-x1, x2)|^2) / 2`` on the grid ``x1 x x2``,
+    ``a^(w) = sum_s a_s exp(-i (s1 w1 + s2 w2))``, summed term by term."""
+    a = np.asarray(a, dtype=np.float64)
+    q1, q2 = psf_support(a)
+    x1 = np.asarray(x1, dtype=np.float64)[:, None]
+    x2 = np.asarray(x2, dtype=np.float64)[None, :]
+    ap = np.zeros((x1.shape[0], x2.shape[1]), dtype=complex)
+    am = np.zeros_like(ap)
+    for s1 in range(-q1, q1 + 1):
+        for s2 in range(-q2, q2 + 1):
+            v = a[s1 + q1, s2 + q2]
+            ap += v * np.exp(-1j * (s1 * x1 + s2 * x2))
+            am += v * np.exp(-1j * (-s1 * x1 + s2 * x2))
+    return 0.5 * (np.abs(ap) ** 2 + np.abs(am) ** 2)
+
+
+def corr_grid() -> np.ndarray:
+    """The model's frequency grid ``j pi / (G - 1)``, ``j = 0..G-1``."""
+    return np.arange(CORR_GRID) * np.pi / (CORR_GRID - 1)
+
+
+def corr_target(h: np.ndarray) -> np.ndarray:
+    """Training target: ``delta`` of the PSF's antisymmetric part on the model grid."""
+    g = corr_grid()
+    return spectral_energy(antisymmetric_part(h), g, g)
+
+
+def corr_input(h: np.ndarray) -> np.ndarray:
+    """Model input: ``16 (h - s)`` of a 15 x 15 PSF, row-major, length 225."""
+    h = np.asarray(h, dtype=np.float64)
+    if h.shape != (2 * CORR_Q + 1, 2 * CORR_Q + 1):
+        raise ValueError("the correction model takes 15 x 15 PSFs")
+    return CORR_IN_SCALE * antisymmetric_part(h).reshape(-1)
+
+
+def bilinear(table: np.ndarray, x1: np.ndarray, x2: np.ndarray) -> np.ndarray:
+    """Bilinear interpolation of a ``G x G`` table on ``[0, pi]^2`` at ``x1 x x2``."""
+    G = table.shape[0]
+
+    def cell(x):
+        u = np.asarray(x, dtype=np.float64) / np.pi * (G - 1)
+        i = np.minimum(np.floor(u).astype(int), G - 2)
+        return i, u - i
+
+    i, t = cell(x1)
+    j, w = cell(x2)
+    out = np.zeros((len(i), len(j)))
+    for r in range(len(i)):
+        for c in range(len(j)):
+            a, b = i[r], j[c]
+            out[r, c] = ((1 - t[r]) * (1 - w[c]) * table[a, b] + (1 - t[r]) * w[c] * table[a, b + 1]
+                         + t[r] * (1 - w[c]) * table[a + 1, b] + t[r] * w[c] * table[a + 1, b + 1])
+    return out
+
+
+# ------------------------------------------------------------------ model --
+
+def mlp_init(rng: np.random.Generator) -> dict:
+    """He-uniform weights (row-major ``in x out``) and zero biases."""
+    def layer(i, o):
+        lim = np.sqrt(6.0 / i)
+        return rng.uniform(-lim, lim, size=(i, o)), np.zeros(o)
+
+    W1, b1 = layer(CORR_IN, CORR_HIDDEN)
+    W2, b2 = layer(CORR_HIDDEN, CORR_HIDDEN)
+    W3, b3 = layer(CORR_HIDDEN, CORR_OUT)
+    return {"W1": W1, "b1": b1, "W2": W2, "b2": b2, "W3": W3, "b3": b3}
+
+
+PARAM_ORDER = ("W1", "b1", "W2", "b2", "W3", "b3")
+
+
+def mlp_forward(P: dict, X: np.ndarray):
+    """``Y = relu(relu(X W1 + b1) W2 + b2) W3 + b3``; returns ``(Y, cache)``."""
+    X = np.asarray(X, dtype=np.float64)
+    Z1 = X @ P["W1"] + P["b1"]
+    H1 = np.maximum(Z1, 0.0)
+    Z2 = H1 @ P["W2"] + P["b2"]
+    H2 = np.maximum(Z2, 0.0)
+    Y = H2 @ P["W3"] + P["b3"]
+    return Y, (X, Z1, H1, Z2, H2)
+
+
+def mse_loss(Y: np.ndarray, T: np.ndarray):
+    """``L = mean (Y - T)^2`` over the batch and the outputs, and ``dL/dY``."""
+    D = Y - T
+    return float(np.mean(D * D)), 2.0 * D / D.size
+
+
+def mlp_backward(P: dict, cache, dY: np.ndarray) -> dict:
+    """Gradients of the loss with respect to every parameter (chain rule)."""
+    X, Z1, H1, Z2, H2 = cache
+    g = {"W3": H2.T @ dY, "b3": dY.sum(axis=0)}
+    dH2 = dY @ P["W3"].T
+    dZ2 = dH2 * (Z2 > 0)
+    g["W2"] = H1.T @ dZ2
+    g["b2"] = dZ2.sum(axis=0)
+    dH1 = dZ2 @ P["W2"].T
+    dZ1 = dH1 * (Z1 > 0)
+    g["W1"] = X.T @ dZ1
+    g["b1"] = dZ1.sum(axis=0)
+    return g
+
+
+def adam_step(P: dict, G: dict, state: dict, lr: float, beta1=0.9, beta2=0.999, eps=1e-8) -> None:
+    """One Adam update (Kingma and Ba) of every parameter, in place.
+    ``state`` holds ``t`` and the first / second moment estimates."""
+    state["t"] = state.get("t", 0) + 1
+    t = state["t"]
+    for k in PARAM_ORDER:
+        m = state.setdefault("m_" + k, np.zeros_like(P[k]))
+        v = state.setdefault("v_" + k, np.zeros_like(P[k]))
+        m[:] = beta1 * m + (1 - beta1) * G[k]
+        v[:] = beta2 * v + (1 - beta2) * G[k] ** 2
+        mh = m / (1 - beta1 ** t)
+        vh = v / (1 - beta2 ** t)
+        P[k] = P[k] - lr * mh / (np.sqrt(vh) + eps)
+
+
+def mlp_predict_table(P: dict, h: np.ndarray) -> np.ndarray:
+    """The model's ``delta`` table for one PSF (negative predictions clipped to 0)."""
+    Y, _ = mlp_forward(P, corr_input(h)[None, :])
+    return np.maximum(Y[0].reshape(CORR_GRID, CORR_GRID), 0.0)
+
+
+# ------------------------------------------------------ corrected filter --
+
+def symprec_setup_corrected(h: np.ndarray, n1: int, n2: int, alpha: float,
+                            table: np.ndarray | None = None) -> dict:
+    """AR preconditioner with the refined eigenvalues: ``d = 1/(lambda_s^2 + delta + alpha)``.
+
+    ``delta`` is the exact spectral energy of ``h - s`` on the AR grid when
+    ``table`` is None, else the bilinear reading of a ``G x G`` table."""
+    s = symmetrize(h)
+    lam = eigenvalues(s, n1, n2)
+    x1, x2 = ar_grid(n1), ar_grid(n2)
+    if table is None:
+        delta = spectral_energy(antisymmetric_part(h), x1, x2)
+    else:
+        delta = bilinear(np.asarray(table, dtype=np.float64), x1, x2)
+    return {"s": s, "lam": lam, "delta": delta, "d": 1.0 / (lam ** 2 + delta + alpha),
+            "n1": n1, "n2": n2}
+
+
+def restore_corrected(g, h, alpha, tau=1.0, iters=20, table=None, f_true=None):
+    """D-Landweber (eq. DLandweberMeth) with the corrected filter."""
+    g = np.asarray(g, dtype=np.float64)
+    n1, n2 = g.shape
+    prec = symprec_setup_corrected(h, n1, n2, alpha, table)
+    x = np.zeros((n1, n2))
+    trace = [] if f_true is not None else None
+    for _ in range(iters):
+        z = ar_synthesis(prec["d"] * ar_analysis(ar_reblur(g - ar_blur(x, h), h)))
+        x = x + tau * z
+        if trace is not None:
+            trace.append(rre(x, f_true))
+    best = int(np.argmin(trace)) + 1 if trace else None
+    return x, (np.asarray(trace) if trace is not None else None), best

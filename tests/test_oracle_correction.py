@@ -1,0 +1,144 @@
+"""Pins of the spectral-correction oracle (the learned form's target, model
+and corrected filter) against things other than itself: numpy's FFT, a dense
+assembly of A' A in the AR basis, finite differences, Adam's closed-form
+first step, exact interpolation identities and dense brute force."""
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+
+def rand_psf(rng, q1, q2):
+    h = rng.random((2 * q1 + 1, 2 * q2 + 1))
+    return h / h.sum()
+
+
+@pytest.mark.parametrize("q1,q2", [(2, 2), (3, 1), (7, 7)])
+def test_lambda2_plus_delta_is_flip_averaged_fft_energy(q1, q2):
+    """lambda_s^2 + delta = (|h^(w1, w2)|^2 + |h^(-w1, w2)|^2) / 2 with h^ from numpy's FFT."""
+    rng = np.random.default_rng(q1 * 10 + q2)
+    h = rand_psf(rng, q1, q2)
+    N = 64
+    F = np.fft.fft2(h, s=(N, N))          # |F[k]| = |h^(2 pi k / N)| (the offset is a phase)
+    k = np.arange(N // 2 + 1)
+    x = 2 * np.pi * k / N
+    E = np.abs(F) ** 2
+    want = 0.5 * (E[np.ix_(k, k)] + E[np.ix_((-k) % N, k)])
+    lam = O.symbol(O.symmetrize(h), x, x)
+    got = lam ** 2 + O.spectral_energy(O.antisymmetric_part(h), x, x)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-13)
+
+
+def test_delta_vanishes_exactly_for_strongly_symmetric_psfs_only():
+    rng = np.random.default_rng(3)
+    h = rand_psf(rng, 3, 2)
+    s = O.symmetrize(h)
+    x = O.corr_grid()
+    assert np.max(np.abs(O.antisymmetric_part(s))) < 1e-17
+    assert np.max(O.spectral_energy(O.antisymmetric_part(s), x, x)) < 1e-30
+    d = O.spectral_energy(O.antisymmetric_part(h), x, x)
+    assert d.min() >= 0 and d.max() > 1e-4
+
+
+def test_corrected_eigenvalue_tracks_the_diagonal_of_AtA_in_the_AR_basis():
+    """diag(T~ A'A T) at interior frequencies is matched by lambda_s^2 + delta far
+    better than by lambda_s^2 alone (boundary terms are O(q/n))."""
+    rng = np.random.default_rng(1)
+    n = 40
+    h = rand_psf(rng, 2, 2)
+    A = O.ar_matrix_dense(h, n, n)
+    Ap = O.ar_matrix_dense(h[::-1, ::-1], n, n)
+    T = np.kron(O.ar_T(n), O.ar_T(n))
+    Tt = np.kron(O.ar_Ttilde(n), O.ar_Ttilde(n))
+    diag = np.diag(Tt @ Ap @ A @ T).reshape(n, n)[1:-1, 1:-1]
+    lam = O.eigenvalues(O.symmetrize(h), n, n)[1:-1, 1:-1]
+    x = O.ar_grid(n)[1:-1]
+    corr = lam ** 2 + O.spectral_energy(O.antisymmetric_part(h), x, x)
+    err_corr = np.max(np.abs(diag - corr))
+    err_sym = np.max(np.abs(diag - lam ** 2))
+    assert err_corr < 1e-2
+    assert err_corr < 0.25 * err_sym
+
+
+def test_bilinear_is_exact_on_nodes_and_for_bilinear_functions():
+    G = O.CORR_GRID
+    x = O.corr_grid()
+    rng = np.random.default_rng(0)
+    T = rng.random((G, G))
+    np.testing.assert_allclose(O.bilinear(T, x, x), T, rtol=0, atol=1e-12)
+    f = lambda u, v: 0.3 + 1.7 * u - 0.4 * v + 0.25 * u * v  # noqa: E731
+    tab = f(x[:, None], x[None, :])
+    y = rng.uniform(0, np.pi, 17)
+    np.testing.assert_allclose(O.bilinear(tab, y, y[::-1]), f(y[:, None], y[::-1][None, :]),
+                               atol=1e-12)
+
+
+def test_mlp_gradients_match_finite_differences():
+    rng = np.random.default_rng(5)
+    P = O.mlp_init(rng)
+    for k in O.PARAM_ORDER:
+        if k.startswith("b"):
+            P[k] = rng.normal(0, 0.1, P[k].shape)
+    X = rng.normal(0, 1, (4, O.CORR_IN))
+    T = rng.normal(0, 1, (4, O.CORR_OUT))
+    Y, cache = O.mlp_forward(P, X)
+    _, dY = O.mse_loss(Y, T)
+    G = O.mlp_backward(P, cache, dY)
+    eps = 1e-6
+    for k in O.PARAM_ORDER:
+        flat = P[k].reshape(-1)
+        for idx in rng.choice(flat.size, 4, replace=False):
+            old = flat[idx]
+            flat[idx] = old + eps
+            lp, _ = O.mse_loss(O.mlp_forward(P, X)[0], T)
+            flat[idx] = old - eps
+            lm, _ = O.mse_loss(O.mlp_forward(P, X)[0], T)
+            flat[idx] = old
+            num = (lp - lm) / (2 * eps)
+            assert abs(G[k].reshape(-1)[idx] - num) <= 1e-6 * max(1.0, abs(num)), (k, idx)
+
+
+def test_adam_first_step_closed_form():
+    """After one step m^ = g and v^ = g^2, so the update is -lr g / (|g| + eps)."""
+    rng = np.random.default_rng(2)
+    P = O.mlp_init(rng)
+    G = {k: rng.normal(0, 1e-3, P[k].shape) for k in O.PARAM_ORDER}
+    before = {k: P[k].copy() for k in O.PARAM_ORDER}
+    st = {}
+    O.adam_step(P, G, st, lr=1e-3)
+    for k in O.PARAM_ORDER:
+        want = before[k] - 1e-3 * G[k] / (np.abs(G[k]) + 1e-8)
+        np.testing.assert_allclose(P[k], want, rtol=1e-12, atol=1e-15)
+
+
+def test_corrected_setup_reads_exact_delta_on_grid_nodes():
+    """For n = 33 every AR grid point is a table node, so the table reading is exact."""
+    rng = np.random.default_rng(9)
+    h = rand_psf(rng, 7, 7)
+    exact = O.symprec_setup_corrected(h, 33, 33, 0.1)
+    tab = O.symprec_setup_corrected(h, 33, 33, 0.1, table=O.corr_target(h))
+    np.testing.assert_allclose(tab["d"], exact["d"], rtol=1e-11)
+    assert np.all(exact["d"] <= 1.0 / (exact["lam"] ** 2 + 0.1) + 1e-15)
+
+
+def test_restore_corrected_reduces_to_restore_for_symmetric_psf_and_matches_dense():
+    rng = np.random.default_rng(4)
+    n = 12
+    hs = O.symmetrize(rand_psf(rng, 2, 2))
+    g = rng.random((n, n))
+    x1, _, _ = O.restore(g, hs, 0.05, 1.0, 5, True)
+    x2, _, _ = O.restore_corrected(g, hs, 0.05, 1.0, 5)
+    np.testing.assert_allclose(x2, x1, rtol=0, atol=1e-14)
+    # asymmetric PSF against a dense iteration with D = T diag(d) inv(T)
+    h = rand_psf(rng, 2, 1)
+    prec = O.symprec_setup_corrected(h, n, n, 0.05)
+    A = O.ar_matrix_dense(h, n, n)
+    Ap = O.ar_matrix_dense(h[::-1, ::-1], n, n)
+    T = np.kron(O.ar_T(n), O.ar_T(n))
+    D = T @ np.diag(prec["d"].reshape(-1)) @ np.linalg.inv(T)
+    x = np.zeros(n * n)
+    for _ in range(5):
+        x = x + D @ (Ap @ (g.reshape(-1) - A @ x))
+    x3, _, _ = O.restore_corrected(g, h, 0.05, 1.0, 5)
+    np.testing.assert_allclose(x3.reshape(-1), x, rtol=0, atol=1e-11)
