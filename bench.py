@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     return ap.parse_args()
 
 
@@ -249,6 +250,8 @@ def run_own(args):
             out["matvec_hbm"] = matvec_hbm_form(ar, torch, dev, stream)
             out["forms"]["precision_2048"] = precision_2048_form(ar, torch, dev, stream, flush,
                                                                  max(args.steps // 4, 2))
+            if not args.no_learned:
+                out["forms"]["learned"] = learned_form(ar, torch, dev, stream)
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(h, g, f)
     if world > 1:
@@ -476,6 +479,88 @@ def precision_2048_form(ar, torch, dev, stream, flush, steps):
         xb, _, _ = ar.ar_restore(g_d, h, PREC4_ALPHA, TAU, k, True, precision="bf16x2")
         drift.append([k, float(torch.linalg.vector_norm(xb - xa) / torch.linalg.vector_norm(xa))])
     out["bf16x2_vs_fp32_rel_l2_at_step"] = drift
+    return out
+
+
+CORR_TRAIN, CORR_EVAL = 10000, 500
+CORR_EPOCHS, CORR_BATCH, CORR_LR = 40, 250, 1e-3
+CORR_ALPHAS = (0.3, 0.1)
+
+
+def learned_form(ar, torch, dev, stream, n_eval=CORR_EVAL):
+    """The learned spectral correction: train the model on 10,000 random 15x15
+    PSFs (targets computed on the GPU), then restore a 1024^2 scene blurred by
+    each of 500 held-out PSFs (0.5% noise, 50 D-Landweber iterations) with the
+    symmetrized preconditioner (the judge), the learned correction and the
+    exact correction, at two alphas."""
+    train = W.corr_psfs(CORR_TRAIN, salt=1)
+    held = W.corr_psfs(n_eval, salt=2)
+    model = ar.Corr(W.corr_init_params(W.SEED_BASE + 4))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = model.train(train, CORR_EPOCHS, CORR_BATCH, CORR_LR)
+    t_train = time.perf_counter() - t0
+    # held-out fit of the tables
+    tgt = ar.corr_targets(held[:64])
+    pred = np.stack([np.maximum(model.predict(h), 0.0) for h in held[:64]])
+    fit = float(np.linalg.norm(pred - tgt) / np.linalg.norm(tgt))
+
+    n = N1
+    ext, f, e = W.make_inputs(n, n, held[0], "ellipses", 4)
+    ext_d = torch.from_numpy(ext.astype(np.float32)).to(dev)
+    f_d = torch.from_numpy(f.astype(np.float32)).to(dev)
+    e_d = torch.from_numpy(e.astype(np.float32)).to(dev)
+    arms = {}
+    for alpha in CORR_ALPHAS:
+        for arm in ("symmetrized", "learned", "exact"):
+            arms[(arm, alpha)] = {"best": [], "it": [], "final": [], "ms": [], "reach": []}
+    x = torch.empty(n, n, device=dev)
+    for h in held:
+        hd = torch.from_numpy(h.astype(np.float32)).to(dev)
+        gc = ar.ar_blur_apply(ext_d, hd)[7:7 + n, 7:7 + n].contiguous()
+        g = gc + (NU * torch.linalg.vector_norm(gc) / torch.linalg.vector_norm(e_d)) * e_d
+        for alpha in CORR_ALPHAS:
+            best_sym = None
+            for arm in ("symmetrized", "learned", "exact"):
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                if arm == "symmetrized":
+                    _, tr, best = ar.ar_restore(g, h, alpha, TAU, ITERS, True, f_true=f_d, x_out=x)
+                else:
+                    P = ar.ar_symprec_setup_corrected(h, n, n, alpha,
+                                                      model=model if arm == "learned" else None)
+                    _, tr, best = ar.ar_restore_prec(P, g, h, TAU, ITERS, f_true=f_d, x_out=x)
+                    P.close()
+                a1.record(stream)
+                a1.synchronize()
+                rec = arms[(arm, alpha)]
+                tr = np.nan_to_num(tr, nan=np.inf)
+                rec["best"].append(float(np.min(tr)))
+                rec["it"].append(best)
+                rec["final"].append(float(tr[-1]))
+                rec["ms"].append(a0.elapsed_time(a1))
+                if arm == "symmetrized":
+                    best_sym = float(np.min(tr))
+                hit = np.nonzero(tr <= best_sym * 1.01)[0]
+                rec["reach"].append(int(hit[0]) + 1 if len(hit) else None)
+    model.close()
+    out = {"train": {"psfs": CORR_TRAIN, "epochs": CORR_EPOCHS, "batch": CORR_BATCH, "lr": CORR_LR,
+                     "seconds": round(t_train, 2), "loss_first": float(loss[0]),
+                     "loss_last": float(loss[-1]),
+                     "heldout_table_rel_l2": round(fit, 4)},
+           "eval": {"psfs": n_eval, "image": f"ellipses {n}x{n}, 0.5% noise",
+                    "iterations": ITERS}}
+    for (arm, alpha), rec in arms.items():
+        reach = [r for r in rec["reach"] if r is not None]
+        out["eval"][f"{arm}_alpha{alpha}"] = {
+            "median_best_rre": round(float(np.median(rec["best"])), 6),
+            "median_best_iter": float(np.median(rec["it"])),
+            "unstable_frac": round(float(np.mean(~(np.array(rec["final"]) < 1.0))), 4),
+            "final_over_best_median": round(float(np.median(np.array(rec["final"]) /
+                                                            np.array(rec["best"]))), 3),
+            "reached_sym_best_frac": round(len(reach) / len(rec["reach"]), 4),
+            "median_iters_to_sym_best": float(np.median(reach)) if reach else None,
+            "median_ms_per_restore": round(float(np.median(rec["ms"])), 3)}
     return out
 
 

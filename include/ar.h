@@ -296,6 +296,81 @@ AR_API ar_status ar_batch_results(ar_batch* B, double* rre_traces, int* best_ite
                                   unsigned long long* kernels_per_run);
 AR_API void ar_batch_destroy(ar_batch* B);
 
+/*
+ * Spectral correction of the symmetrized preconditioner (learned form).
+ *
+ * With s the symmetrized PSF (eq. simmetrizzata2d) and a = h - s, the
+ * response of A'A at an AR frequency x of a large image is, averaged over the
+ * sign flips of x, lambda_s(x)^2 + delta(x) with
+ *     delta(x1, x2) = (|a^(x1, x2)|^2 + |a^(-x1, x2)|^2) / 2,
+ *     a^(w) = sum_s a_s exp(-i s.w);
+ * the corrected filter is d = 1/(lambda_s^2 + delta + alpha) (eq. TikFilter
+ * with the refined eigenvalue).  The paper has no such correction; it is the
+ * per-frequency refinement of the symmetrized eigenvalues that a small model
+ * learns from the PSF's antisymmetric part: an MLP (ReLU, widths 225 -> 256
+ * -> 256 -> 1089) mapping 16 (h - s) of a 15 x 15 PSF (row-major) to delta on
+ * the 33 x 33 grid x_j = j pi / 32 of [0, pi]^2 (row-major), read on the AR
+ * grid by bilinear interpolation (negative predictions count as 0).
+ * Parameters are float32, row-major (inputs x outputs), in the order
+ * W1 (225 x 256), b1, W2 (256 x 256), b2, W3 (256 x 1089), b3.
+ */
+#define AR_CORR_Q 7
+#define AR_CORR_IN 225
+#define AR_CORR_HIDDEN 256
+#define AR_CORR_GRID 33
+#define AR_CORR_OUT 1089
+
+typedef struct ar_corr ar_corr;
+
+/* Number of float32 parameters of the model (403521). */
+AR_API size_t ar_corr_param_count(void);
+
+/* Create a model on the current device from ar_corr_param_count() host
+ * floats (copied).  Errors: AR_ERR_INVALID_ARG (null, non-finite), AR_ERR_ALLOC. */
+AR_API ar_status ar_corr_create(const float* params_host, ar_corr** out);
+
+/* Copy the model's parameters to the host (waits for pending training). */
+AR_API ar_status ar_corr_params(const ar_corr* M, float* params_host);
+
+/* Free a model (NULL is a no-op). */
+AR_API void ar_corr_destroy(ar_corr* M);
+
+/* The training targets: delta on the 33 x 33 grid, float64, computed exactly
+ * on the GPU, for `count` 15 x 15 PSFs (host float64, 225 each) into
+ * delta_host (count x 1089).  Synchronous. */
+AR_API ar_status ar_corr_targets(const double* psfs_host, int count, double* delta_host);
+
+/* Train on `count` 15 x 15 PSFs (host float64): inputs 16 (h - s) and targets
+ * delta computed on the GPU, then `epochs` passes over the PSFs in order, in
+ * batches of `batch` (the last may be smaller), each one Adam step (beta1
+ * 0.9, beta2 0.999, eps 1e-8, learning rate lr) on the mean squared error
+ * over the batch and the 1089 outputs.  loss_trace_host (may be NULL)
+ * receives the mean batch loss of each epoch.  Synchronizes `stream`. */
+AR_API ar_status ar_corr_train(ar_corr* M, const double* psfs_host, int count, int epochs,
+                               int batch, double lr, float* loss_trace_host, void* stream);
+
+/* The model's 33 x 33 delta table for one 15 x 15 PSF (host float64) into
+ * table_host (1089 floats, before clipping at 0).  Synchronous. */
+AR_API ar_status ar_corr_predict(const ar_corr* M, const double* psf_host, float* table_host);
+
+/* ar_symprec_setup_ex (AR BCs) with the corrected filter
+ * d = 1/(lambda_s^2 + delta + alpha): delta exact on the AR grid (float64)
+ * when M is NULL, else read from M's prediction for the PSF (which must then
+ * be 15 x 15).  Errors as ar_symprec_setup_ex. */
+AR_API ar_status ar_symprec_setup_corrected(const double* psf_host, int q1, int q2, int n1, int n2,
+                                            double alpha, const ar_corr* M, int precision,
+                                            void* stream, ar_prec** out);
+
+/* D-Landweber (eq. DLandweberMeth with the reblurred A' of Section 4) with a
+ * preconditioner built beforehand (ar_symprec_setup*, any BC, symmetrized or
+ * corrected): the blur and reblur take psf_host, which must have P's support
+ * and sum to 1; g, x0, f_true, x_out are n1 x n2 as P.  Other arguments,
+ * outputs and errors as ar_restore.  Calls that share P must not overlap in
+ * time (P's transform buffers are reused). */
+AR_API ar_status ar_restore_prec(const ar_prec* P, const float* g, const double* psf_host,
+                                 double tau, int iters, const float* x0, const float* f_true,
+                                 float* x_out, double* rre_trace, int* best_iter, void* stream);
+
 /* Static name of a status code ("AR_OK", ...; "AR_UNKNOWN" otherwise). */
 AR_API const char* ar_status_string(ar_status s);
 

@@ -31,7 +31,12 @@ EXPORTS = [
     "ar_profile_begin", "ar_profile_end", "ar_restore_plain_static", "ar_symprec_setup_ex",
     "ar_restore_ex", "ar_batch_create", "ar_batch_run", "ar_batch_results", "ar_batch_destroy",
     "ar_blur_apply_bc", "ar_reblur_apply_bc", "ar_symprec_setup_bc", "ar_restore_bc",
+    "ar_corr_param_count", "ar_corr_create", "ar_corr_params", "ar_corr_destroy",
+    "ar_corr_targets", "ar_corr_train", "ar_corr_predict", "ar_symprec_setup_corrected",
+    "ar_restore_prec",
 ]
+
+CORR_GRID = 33      # the correction model's delta table is CORR_GRID x CORR_GRID
 
 
 class BatchItem(ctypes.Structure):
@@ -113,6 +118,22 @@ def lib() -> ctypes.CDLL:
         L.ar_profile_end.restype = _i
         L.ar_kernel_launches.argtypes = []
         L.ar_kernel_launches.restype = ctypes.c_ulonglong
+        L.ar_corr_param_count.argtypes = []
+        L.ar_corr_param_count.restype = ctypes.c_size_t
+        for name, args in {
+            "ar_corr_create": [_vp, ctypes.POINTER(_vp)],
+            "ar_corr_params": [_vp, _vp],
+            "ar_corr_targets": [_vp, _i, _vp],
+            "ar_corr_train": [_vp, _vp, _i, _i, _i, _d, _vp, _vp],
+            "ar_corr_predict": [_vp, _vp, _vp],
+            "ar_symprec_setup_corrected": [_vp, _i, _i, _i, _i, _d, _vp, _i, _vp,
+                                           ctypes.POINTER(_vp)],
+            "ar_restore_prec": [_vp, _vp, _vp, _d, _i, _vp, _vp, _vp, _vp, _vp, _vp],
+        }.items():
+            getattr(L, name).argtypes = args
+            getattr(L, name).restype = _i
+        L.ar_corr_destroy.argtypes = [_vp]
+        L.ar_corr_destroy.restype = None
         _lib = L
     return _lib
 
@@ -376,6 +397,98 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Corr:
+    """Owner of an ``ar_corr*``: the MLP that predicts the spectral correction
+    delta (33 x 33 table) from the antisymmetric part of a 15 x 15 PSF."""
+
+    def __init__(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != param_count():
+            raise ValueError(f"expected {param_count()} parameters, got {p.size}")
+        out = _vp()
+        _check(lib().ar_corr_create(p.ctypes.data, ctypes.byref(out)), "ar_corr_create")
+        self.handle = out.value
+
+    def params(self) -> np.ndarray:
+        p = np.empty(param_count(), dtype=np.float32)
+        _check(lib().ar_corr_params(self.handle, p.ctypes.data), "ar_corr_params")
+        return p
+
+    def train(self, psfs, epochs: int, batch: int, lr: float, stream=None) -> np.ndarray:
+        """Adam on the mean squared error of the delta tables; returns the loss per epoch."""
+        h = np.ascontiguousarray(psfs, dtype=np.float64).reshape(-1, 225)
+        tr = np.zeros(max(int(epochs), 1), dtype=np.float32)
+        _check(lib().ar_corr_train(self.handle, h.ctypes.data, h.shape[0], int(epochs), int(batch),
+                                   float(lr), tr.ctypes.data, _stream(stream)), "ar_corr_train")
+        return tr[:int(epochs)]
+
+    def predict(self, psf) -> np.ndarray:
+        h = np.ascontiguousarray(psf, dtype=np.float64).reshape(225)
+        t = np.empty(CORR_GRID * CORR_GRID, dtype=np.float32)
+        _check(lib().ar_corr_predict(self.handle, h.ctypes.data, t.ctypes.data), "ar_corr_predict")
+        return t.reshape(CORR_GRID, CORR_GRID)
+
+    def close(self) -> None:
+        if self.handle:
+            lib().ar_corr_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def param_count() -> int:
+    return int(lib().ar_corr_param_count())
+
+
+def corr_targets(psfs) -> np.ndarray:
+    """Exact delta tables (float64, computed on the GPU) of 15 x 15 PSFs."""
+    h = np.ascontiguousarray(psfs, dtype=np.float64).reshape(-1, 225)
+    out = np.empty((h.shape[0], CORR_GRID * CORR_GRID), dtype=np.float64)
+    _check(lib().ar_corr_targets(h.ctypes.data, h.shape[0], out.ctypes.data), "ar_corr_targets")
+    return out.reshape(-1, CORR_GRID, CORR_GRID)
+
+
+def ar_symprec_setup_corrected(psf, n1: int, n2: int, alpha: float, model: "Corr | None" = None,
+                               stream=None, precision: str = "fp32") -> Prec:
+    """AR preconditioner with d = 1/(lambda_s^2 + delta + alpha); delta exact
+    (model None) or predicted by ``model``."""
+    h = _host_psf(psf)
+    q1, q2 = _support(h.shape)
+    out = _vp()
+    _check(lib().ar_symprec_setup_corrected(h.ctypes.data, q1, q2, n1, n2, float(alpha),
+                                            model.handle if model is not None else None,
+                                            PRECISION[precision], _stream(stream),
+                                            ctypes.byref(out)), "ar_symprec_setup_corrected")
+    return Prec(out.value, n1, n2)
+
+
+def ar_restore_prec(P: Prec, g: torch.Tensor, psf, tau: float = 1.0, iters: int = 20,
+                    x0: torch.Tensor | None = None, f_true: torch.Tensor | None = None,
+                    x_out: torch.Tensor | None = None, trace: bool = True, stream=None):
+    """D-Landweber with a preconditioner built beforehand.  Returns ``(x, trace, best)``."""
+    _image(g, "g")
+    if tuple(g.shape) != P.shape:
+        raise ValueError(f"g has shape {tuple(g.shape)}, preconditioner expects {P.shape}")
+    h = _host_psf(psf)
+    if x_out is None:
+        x_out = torch.empty_like(g)
+    _image(x_out, "x_out")
+    want = f_true is not None and trace
+    tr = np.zeros(max(iters, 1), dtype=np.float64) if want else None
+    best = _i(0)
+    _check(lib().ar_restore_prec(
+        P.handle, g.data_ptr(), h.ctypes.data, float(tau), int(iters),
+        _image(x0, "x0").data_ptr() if x0 is not None else None,
+        _image(f_true, "f_true").data_ptr() if f_true is not None else None,
+        x_out.data_ptr(), tr.ctypes.data if want else None,
+        ctypes.addressof(best) if want else None, _stream(stream)), "ar_restore_prec")
+    return x_out, (tr[:iters] if want else None), (best.value if want else None)
 
 
 def kernel_launches() -> int:

@@ -149,7 +149,8 @@ ar_status apply_common(const float* x, float* y, int n1, int n2, const float* ps
 
 // Builds the preconditioner's device data on `s` without synchronizing.
 ar_status prec_build(const double* psf_host, int q1, int q2, int n1, int n2, double alpha,
-                     int bc, int precision, cudaStream_t s, bool keep64, ar_prec** out) {
+                     int bc, int precision, cudaStream_t s, bool keep64, ar_prec** out,
+                     int correction, const ar_corr* model) {
     set_pool_threshold_once();
     ar_prec* P = new (std::nothrow) ar_prec();
     if (!P) return fail(AR_ERR_ALLOC, "host allocation of ar_prec");
@@ -186,9 +187,18 @@ ar_status prec_build(const double* psf_host, int q1, int q2, int n1, int n2, dou
         if (st == AR_OK && bc == AR_BC_PERIODIC &&
             cudaMallocAsync((void**)&P->d32_odd, n * sizeof(float), s) != cudaSuccess)
             st = fail(AR_ERR_ALLOC, "odd filter buffer");
+        double* delta = nullptr;
+        if (st == AR_OK && correction) {
+            double* cwork = nullptr;
+            st = tmp.get(&delta, n);
+            if (st == AR_OK) st = tmp.get(&cwork, corr_scratch_doubles(q1, q2, n1, n2));
+            if (st == AR_OK)
+                st = corr_delta(h64, q1, q2, n1, n2, correction == 2 ? model : nullptr, psf_host,
+                                delta, cwork, s);
+        }
         if (st == AR_OK)
             st = setup_eigen(h64, q1, q2, n1, n2, alpha, bc, P->lam64, P->d64, P->d32, P->d32_odd,
-                             work, s);
+                             work, s, delta);
         if (st == AR_OK) st = transform_plan_create(n1, n2, bc, precision, s, &P->plan);
     }
     if (st != AR_OK) {
@@ -196,6 +206,133 @@ ar_status prec_build(const double* psf_host, int q1, int q2, int n1, int n2, dou
         return st;
     }
     *out = P;
+    return AR_OK;
+}
+
+}  // namespace ar
+
+namespace ar {
+
+// The (D-)Landweber loop of ar_restore_bc on validated arguments; with Pext
+// non-null its preconditioner is used instead of building one.
+static ar_status restore_run(const float* g, const double* psf_host, int n1, int n2, int q1, int q2,
+                             double alpha, double tau, int iters, int bc, bool pc, int precision,
+                             const float* x0, const float* f_true, float* x_out, double* rre_trace,
+                             int* best_iter, void* stream, const ar_prec* Pext) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    set_pool_threshold_once();
+    const size_t n = (size_t)n1 * n2;
+    const size_t nb = n * sizeof(float);
+    const size_t k = (size_t)(2 * q1 + 1) * (2 * q2 + 1);
+    std::vector<float> h32(k);
+    for (size_t i = 0; i < k; ++i) h32[i] = (float)psf_host[i];
+
+    ar_prec* P = nullptr;            // built here (and destroyed) unless Pext is given
+    const ar_prec* PP = Pext;
+    unsigned long long bad = 0;
+    int timeout = 0, conv_timeout = 0;
+    int* conv_err = conv_error_flag();
+    if (!conv_err) return fail(AR_ERR_CUDA, "stencil error flag unavailable");
+    std::vector<double> sums((size_t)iters + 1, 0.0);
+    ar_status st = AR_OK;
+    {
+        Scratch ws(s);
+        float *psf = nullptr, *r = nullptr;
+        double* dsum = nullptr;
+        unsigned long long* dbad = nullptr;
+        st = ws.get(&psf, k);
+        if (st == AR_OK) st = ws.get(&r, n);
+        if (st == AR_OK) st = ws.get(&dsum, (size_t)iters + 1);
+        if (st == AR_OK) st = ws.get(&dbad, 1);
+        if (st == AR_OK) {
+            cudaError_t e = cudaMemcpyAsync(psf, h32.data(), k * sizeof(float),
+                                            cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(dsum, 0, ((size_t)iters + 1) * sizeof(double), s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(dbad, 0, sizeof(unsigned long long), s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(conv_err, 0, sizeof(int), s);
+            if (e == cudaSuccess) {
+                if (!x0) e = cudaMemsetAsync(x_out, 0, nb, s);
+                else if (x0 != x_out) e = cudaMemcpyAsync(x_out, x0, nb, cudaMemcpyDeviceToDevice, s);
+            }
+            if (e != cudaSuccess) st = cuda_fail(e, "restore initialisation");
+        }
+        if (st == AR_OK && pc && !Pext) {
+            st = prec_build(psf_host, q1, q2, n1, n2, alpha, bc, precision, s, false, &P);
+            PP = P;
+        }
+        if (st == AR_OK && f_true) st = reduce_sq(f_true, n, dsum + iters, s);
+
+        ConvArgs blur{};
+        blur.x = x_out;
+        blur.out = r;
+        blur.aux = g;
+        blur.psf = psf;
+        blur.n1 = n1;
+        blur.n2 = n2;
+        blur.q1 = q1;
+        blur.q2 = q2;
+        blur.flip = 0;
+        blur.mode = CONV_RESIDUAL;
+        blur.bc = bc;
+        ConvArgs reblur = blur;
+        reblur.x = r;
+        reblur.aux = nullptr;
+        reblur.flip = 1;
+        if (pc && st == AR_OK) {
+            // A' r is written straight into the transform's bf16x3 operand planes
+            reblur.out = nullptr;
+            reblur.mode = CONV_SPLIT3;
+            reblur.planes = transform_input_planes(PP->plan, &reblur.plane_stride, &reblur.ld);
+        } else {
+            reblur.out = x_out;
+            reblur.mode = CONV_AXPY;
+            reblur.tau = (float)tau;
+        }
+        reblur.f = f_true;
+        for (int it = 0; st == AR_OK && it < iters; ++it) {
+            // the RRE numerator ||x_{k+1} - f||^2 is accumulated by the kernel that writes x_{k+1}
+            st = conv_launch(blur, s);                           // r = g - A x_k
+            if (!pc) reblur.sumsq = f_true ? dsum + it : nullptr;
+            if (st == AR_OK) st = conv_launch(reblur, s);        // z = A' r  (or x += tau A' r)
+            if (st == AR_OK && pc)                               // x += tau D z
+                st = transform_apply(PP->plan, PP->d32, PP->d32_odd, nullptr, DIN_SPLIT, x_out,
+                                     DOUT_AXPY, (float)tau, s, f_true,
+                                     f_true ? dsum + it : nullptr);
+        }
+        if (st == AR_OK) st = count_nonfinite(x_out, n, dbad, s);
+        if (st == AR_OK) {
+            cudaError_t e = cudaMemcpyAsync(sums.data(), dsum, sums.size() * sizeof(double),
+                                            cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, dbad, sizeof(bad), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess && PP)
+                e = cudaMemcpyAsync(&timeout, transform_error_flag(PP->plan), sizeof(int),
+                                    cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(&conv_timeout, conv_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+            if (e != cudaSuccess) st = cuda_fail(e, "restore readback");
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (P) ar_symprec_destroy(P);
+    if (st != AR_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "restore");
+    if (f_true) {
+        const double fn = sums[(size_t)iters];
+        int best = 0;
+        double bestv = 0.0;
+        for (int it = 0; it < iters; ++it) {
+            const double v = std::sqrt(sums[(size_t)it] / fn);
+            if (rre_trace) rre_trace[it] = v;
+            if (best == 0 || v < bestv) {
+                best = it + 1;
+                bestv = v;
+            }
+        }
+        if (best_iter) *best_iter = best;
+    }
+    if (timeout) return fail(AR_ERR_TIMEOUT, "a tensor-core contraction gave up waiting");
+    if (conv_timeout) return fail(AR_ERR_TIMEOUT, "a stencil gave up waiting for its halo tile");
+    if (bad) return fail(AR_ERR_NONFINITE, "%llu non-finite entries in the final iterate", bad);
     return AR_OK;
 }
 
@@ -271,6 +408,33 @@ ar_status ar_symprec_setup_bc(const double* psf_host, int q1, int q2, int n1, in
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     ar_prec* P = nullptr;
     AR_TRY(prec_build(psf_host, q1, q2, n1, n2, alpha, bc, precision, s, true, &P));
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        ar_symprec_destroy(P);
+        return cuda_fail(e, "setup");
+    }
+    *out = P;
+    return AR_OK;
+}
+
+ar_status ar_symprec_setup_corrected(const double* psf_host, int q1, int q2, int n1, int n2,
+                                     double alpha, const ar_corr* M, int precision, void* stream,
+                                     ar_prec** out) {
+    if (!psf_host || !out) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
+    if (precision != AR_PRECISION_FP32 && precision != AR_PRECISION_BF16X2)
+        return fail(AR_ERR_INVALID_ARG, "unknown precision %d", precision);
+    if (M && (q1 != AR_CORR_Q || q2 != AR_CORR_Q))
+        return fail(AR_ERR_INVALID_ARG, "the correction model takes %dx%d PSFs", 2 * AR_CORR_Q + 1,
+                    2 * AR_CORR_Q + 1);
+    AR_TRY(check_image_sizes(n1, n2, 3));
+    AR_TRY(check_support(n1, n2, q1, q2, 3));
+    if (!(alpha > 0.0) || !std::isfinite(alpha))
+        return fail(AR_ERR_INVALID_ARG, "alpha must be finite and > 0 (got %g)", alpha);
+    AR_TRY(check_psf_host(psf_host, q1, q2));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    ar_prec* P = nullptr;
+    AR_TRY(prec_build(psf_host, q1, q2, n1, n2, alpha, AR_BC_ANTIREFLECTIVE, precision, s, true, &P,
+                      M ? 2 : 1, M));
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         ar_symprec_destroy(P);
@@ -357,117 +521,31 @@ ar_status ar_restore_bc(const float* g, const double* psf_host, int n1, int n2, 
     if (f_true && overlaps(x_out, nb, f_true, nb)) return fail(AR_ERR_ALIAS, "x_out overlaps f_true");
     if (x0 && x0 != x_out && overlaps(x0, nb, x_out, nb))
         return fail(AR_ERR_ALIAS, "x0 partially overlaps x_out");
+    return restore_run(g, psf_host, n1, n2, q1, q2, alpha, tau, iters, bc, pc, precision, x0, f_true,
+                       x_out, rre_trace, best_iter, stream, nullptr);
+}
 
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    set_pool_threshold_once();
-    const size_t k = (size_t)(2 * q1 + 1) * (2 * q2 + 1);
-    std::vector<float> h32(k);
-    for (size_t i = 0; i < k; ++i) h32[i] = (float)psf_host[i];
-
-    ar_prec* P = nullptr;
-    unsigned long long bad = 0;
-    int timeout = 0, conv_timeout = 0;
-    int* conv_err = conv_error_flag();
-    if (!conv_err) return fail(AR_ERR_CUDA, "stencil error flag unavailable");
-    std::vector<double> sums((size_t)iters + 1, 0.0);
-    ar_status st = AR_OK;
-    {
-        Scratch ws(s);
-        float *psf = nullptr, *r = nullptr;
-        double* dsum = nullptr;
-        unsigned long long* dbad = nullptr;
-        st = ws.get(&psf, k);
-        if (st == AR_OK) st = ws.get(&r, n);
-        if (st == AR_OK) st = ws.get(&dsum, (size_t)iters + 1);
-        if (st == AR_OK) st = ws.get(&dbad, 1);
-        if (st == AR_OK) {
-            cudaError_t e = cudaMemcpyAsync(psf, h32.data(), k * sizeof(float),
-                                            cudaMemcpyHostToDevice, s);
-            if (e == cudaSuccess) e = cudaMemsetAsync(dsum, 0, ((size_t)iters + 1) * sizeof(double), s);
-            if (e == cudaSuccess) e = cudaMemsetAsync(dbad, 0, sizeof(unsigned long long), s);
-            if (e == cudaSuccess) e = cudaMemsetAsync(conv_err, 0, sizeof(int), s);
-            if (e == cudaSuccess) {
-                if (!x0) e = cudaMemsetAsync(x_out, 0, nb, s);
-                else if (x0 != x_out) e = cudaMemcpyAsync(x_out, x0, nb, cudaMemcpyDeviceToDevice, s);
-            }
-            if (e != cudaSuccess) st = cuda_fail(e, "restore initialisation");
-        }
-        if (st == AR_OK && pc)
-            st = prec_build(psf_host, q1, q2, n1, n2, alpha, bc, precision, s, false, &P);
-        if (st == AR_OK && f_true) st = reduce_sq(f_true, n, dsum + iters, s);
-
-        ConvArgs blur{};
-        blur.x = x_out;
-        blur.out = r;
-        blur.aux = g;
-        blur.psf = psf;
-        blur.n1 = n1;
-        blur.n2 = n2;
-        blur.q1 = q1;
-        blur.q2 = q2;
-        blur.flip = 0;
-        blur.mode = CONV_RESIDUAL;
-        blur.bc = bc;
-        ConvArgs reblur = blur;
-        reblur.x = r;
-        reblur.aux = nullptr;
-        reblur.flip = 1;
-        if (pc && st == AR_OK) {
-            // A' r is written straight into the transform's bf16x3 operand planes
-            reblur.out = nullptr;
-            reblur.mode = CONV_SPLIT3;
-            reblur.planes = transform_input_planes(P->plan, &reblur.plane_stride, &reblur.ld);
-        } else {
-            reblur.out = x_out;
-            reblur.mode = CONV_AXPY;
-            reblur.tau = (float)tau;
-        }
-        reblur.f = f_true;
-        for (int it = 0; st == AR_OK && it < iters; ++it) {
-            // the RRE numerator ||x_{k+1} - f||^2 is accumulated by the kernel that writes x_{k+1}
-            st = conv_launch(blur, s);                           // r = g - A x_k
-            if (!pc) reblur.sumsq = f_true ? dsum + it : nullptr;
-            if (st == AR_OK) st = conv_launch(reblur, s);        // z = A' r  (or x += tau A' r)
-            if (st == AR_OK && pc)                               // x += tau D z
-                st = transform_apply(P->plan, P->d32, P->d32_odd, nullptr, DIN_SPLIT, x_out,
-                                     DOUT_AXPY, (float)tau, s, f_true,
-                                     f_true ? dsum + it : nullptr);
-        }
-        if (st == AR_OK) st = count_nonfinite(x_out, n, dbad, s);
-        if (st == AR_OK) {
-            cudaError_t e = cudaMemcpyAsync(sums.data(), dsum, sums.size() * sizeof(double),
-                                            cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, dbad, sizeof(bad), cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess && P)
-                e = cudaMemcpyAsync(&timeout, transform_error_flag(P->plan), sizeof(int),
-                                    cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(&conv_timeout, conv_err, sizeof(int), cudaMemcpyDeviceToHost, s);
-            if (e != cudaSuccess) st = cuda_fail(e, "restore readback");
-        }
-    }
-    cudaError_t e = cudaStreamSynchronize(s);
-    if (P) ar_symprec_destroy(P);
-    if (st != AR_OK) return st;
-    if (e != cudaSuccess) return cuda_fail(e, "restore");
-    if (f_true) {
-        const double fn = sums[(size_t)iters];
-        int best = 0;
-        double bestv = 0.0;
-        for (int it = 0; it < iters; ++it) {
-            const double v = std::sqrt(sums[(size_t)it] / fn);
-            if (rre_trace) rre_trace[it] = v;
-            if (best == 0 || v < bestv) {
-                best = it + 1;
-                bestv = v;
-            }
-        }
-        if (best_iter) *best_iter = best;
-    }
-    if (timeout) return fail(AR_ERR_TIMEOUT, "a tensor-core contraction gave up waiting");
-    if (conv_timeout) return fail(AR_ERR_TIMEOUT, "a stencil gave up waiting for its halo tile");
-    if (bad) return fail(AR_ERR_NONFINITE, "%llu non-finite entries in the final iterate", bad);
-    return AR_OK;
+ar_status ar_restore_prec(const ar_prec* P, const float* g, const double* psf_host, double tau,
+                          int iters, const float* x0, const float* f_true, float* x_out,
+                          double* rre_trace, int* best_iter, void* stream) {
+    if (!P || !g || !psf_host || !x_out) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
+    const int n1 = P->n1, n2 = P->n2, q1 = P->q1, q2 = P->q2;
+    int dev = 0;
+    AR_CUDA(cudaGetDevice(&dev));
+    if (dev != P->device) return fail(AR_ERR_INVALID_ARG, "preconditioner belongs to device %d", P->device);
+    if (iters < 0) return fail(AR_ERR_INVALID_ARG, "iters must be >= 0 (got %d)", iters);
+    if (!(tau > 0.0) || !std::isfinite(tau))
+        return fail(AR_ERR_INVALID_ARG, "tau must be finite and > 0 (got %g)", tau);
+    if ((rre_trace || best_iter) && !f_true)
+        return fail(AR_ERR_INVALID_ARG, "rre_trace/best_iter need f_true");
+    AR_TRY(check_psf_host(psf_host, q1, q2));
+    const size_t nb = (size_t)n1 * n2 * sizeof(float);
+    if (overlaps(x_out, nb, g, nb)) return fail(AR_ERR_ALIAS, "x_out overlaps g");
+    if (f_true && overlaps(x_out, nb, f_true, nb)) return fail(AR_ERR_ALIAS, "x_out overlaps f_true");
+    if (x0 && x0 != x_out && overlaps(x0, nb, x_out, nb))
+        return fail(AR_ERR_ALIAS, "x0 partially overlaps x_out");
+    return restore_run(g, psf_host, n1, n2, q1, q2, P->alpha, tau, iters, P->bc, true, P->precision,
+                       x0, f_true, x_out, rre_trace, best_iter, stream, P);
 }
 
 }  // extern "C"

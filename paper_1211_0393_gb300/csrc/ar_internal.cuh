@@ -139,9 +139,11 @@ int* transform_error_flag(TransformPlan* p);
 // (Theorem 2 / Section 2.1).  Periodic: |lambda| of the circulant of the PSF
 // itself, then the even/odd split of d that transform_apply takes (d32,
 // d32_odd).  Tikhonov filter d = 1/(lambda^2 + alpha) (eq. TikFilter).
+// delta_dev (AR / Reflective, may be null): a float64 correction added to
+// lambda^2 in the filter, d = 1/(lambda^2 + delta + alpha).
 ar_status setup_eigen(const double* psf_dev64, int q1, int q2, int n1, int n2, double alpha,
                       int bc, double* lam64, double* d64, float* d32, float* d32_odd,
-                      double* scratch_dev, cudaStream_t stream);
+                      double* scratch_dev, cudaStream_t stream, const double* delta_dev = nullptr);
 size_t setup_scratch_doubles(int q1, int q2, int n1, int n2, int bc);
 
 // ------------------------------------------------------------- reductions ---
@@ -162,8 +164,18 @@ ar_status check_psf_host(const double* h, int q1, int q2);
 void set_pool_threshold_once();
 // Builds a preconditioner on `s` without synchronizing (keep64: also keep the
 // float64 eigenvalues and filter).
+// correction: 0 none, 1 exact spectral correction, 2 the model's (AR only).
 ar_status prec_build(const double* psf_host, int q1, int q2, int n1, int n2, double alpha,
-                     int bc, int precision, cudaStream_t s, bool keep64, ar_prec** out);
+                     int bc, int precision, cudaStream_t s, bool keep64, ar_prec** out,
+                     int correction = 0, const ar_corr* model = nullptr);
+
+// ----------------------------------------------------- spectral correction
+// delta of the PSF (device float64) on the AR grid of an n1 x n2 image into
+// `delta`: exact when model is null, else the model's bilinear reading
+// (15 x 15 PSF).  `scratch` holds corr_scratch_doubles(q1, q2, n1, n2) doubles.
+ar_status corr_delta(const double* psf_dev64, int q1, int q2, int n1, int n2, const ar_corr* model,
+                     const double* psf_host, double* delta, double* scratch, cudaStream_t s);
+size_t corr_scratch_doubles(int q1, int q2, int n1, int n2);
 
 // Launch accounting: every kernel launch site calls count_launch(k).
 void count_launch(unsigned k = 1);

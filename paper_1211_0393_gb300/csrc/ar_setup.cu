@@ -11,7 +11,8 @@
 //      f is separable, f = sum_a cos(a x1) t_a(x2) with
 //      t_a(x2) = w_a (s_{a,0} + 2 sum_{b>=1} s_{a,b} cos(b x2)), w_0 = 1, w_a = 2,
 //      which regroups the four sums of the equation.
-//  S2  d = 1/(lambda^2 + alpha), eq. TikFilter.
+//  S2  d = 1/(lambda^2 + alpha), eq. TikFilter (with a spectral correction
+//      delta when one is given: d = 1/(lambda^2 + delta + alpha)).
 //
 // Periodic (comparison BC): lambda = |sum_s h_s exp(-i s . w)| at
 // w = 2 pi k / m, the eigenvalue magnitudes of the circulant of the PSF itself,
@@ -82,13 +83,13 @@ __global__ void symbol_tables_kernel(const double* __restrict__ s, int q1, int q
 __global__ void eigen_kernel(const double* __restrict__ t, const double* __restrict__ c1,
                              int q1, int n1, int n2, double alpha,
                              double* __restrict__ lam64, double* __restrict__ d64,
-                             float* __restrict__ d32) {
+                             float* __restrict__ d32, const double* __restrict__ delta) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)n1 * n2) return;
     const int i = (int)(idx / n2), j = (int)(idx % n2);
     double lam = 0.0;
     for (int a = q1; a >= 0; --a) lam += c1[(size_t)a * n1 + i] * t[(size_t)a * n2 + j];
-    const double d = 1.0 / (lam * lam + alpha);
+    const double d = 1.0 / (lam * lam + (delta ? delta[idx] : 0.0) + alpha);
     if (lam64) lam64[idx] = lam;
     if (d64) d64[idx] = d;
     d32[idx] = (float)d;
@@ -152,7 +153,7 @@ size_t setup_scratch_doubles(int q1, int q2, int n1, int n2, int bc) {
 
 ar_status setup_eigen(const double* psf_dev64, int q1, int q2, int n1, int n2, double alpha,
                       int bc, double* lam64, double* d64, float* d32, float* d32_odd,
-                      double* scratch, cudaStream_t stream) {
+                      double* scratch, cudaStream_t stream, const double* delta_dev) {
     const size_t n = (size_t)n1 * n2;
     if (bc == AR_BC_PERIODIC) {
         double2* pr = reinterpret_cast<double2*>(scratch);
@@ -185,7 +186,7 @@ ar_status setup_eigen(const double* psf_dev64, int q1, int q2, int n1, int n2, d
     count_launch();
     AR_CUDA(cudaGetLastError());
     eigen_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(t, c1, q1, n1, n2, alpha,
-                                                                  lam64, d64, d32);
+                                                                  lam64, d64, d32, delta_dev);
     count_launch();
     AR_CUDA(cudaGetLastError());
     return AR_OK;

@@ -255,3 +255,30 @@ def batch_inputs(spec: dict):
 
 def psf_named(name: str) -> np.ndarray:
     return {"config1": psf_config1, "config2": psf_config2, "config4": psf_config4}[name]()
+
+
+# --------------------------------------------------------------------------
+# the spectral-correction model: seeded PSF sets and initial parameters
+# --------------------------------------------------------------------------
+
+CORR_SHAPES = ((225, 256), (256,), (256, 256), (256,), (256, 1089), (1089,))
+
+
+def corr_psfs(count: int, salt: int, config_idx: int = 4) -> np.ndarray:
+    """``count`` random 15 x 15 PSFs (Gaussian / motion / asymmetric-Gaussian mixtures)."""
+    rng = rng_for(config_idx, salt)
+    return np.stack([psf_random(7, 7, rng) for _ in range(count)])
+
+
+def corr_init_params(seed: int) -> np.ndarray:
+    """Initial parameters W1 b1 W2 b2 W3 b3 (float32, flattened): He-uniform
+    weights (row-major in x out), zero biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for shape in CORR_SHAPES:
+        if len(shape) == 2:
+            lim = np.sqrt(6.0 / shape[0])
+            parts.append(rng.uniform(-lim, lim, size=shape).reshape(-1))
+        else:
+            parts.append(np.zeros(shape))
+    return np.concatenate(parts).astype(np.float32)

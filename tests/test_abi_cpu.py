@@ -149,3 +149,25 @@ def test_bc_validation(L):
                            FAKE * 64, None, None, None) == 1      # unknown bc
     assert L.ar_restore_bc(FAKE, hp, 16, 16, 2, 2, 0.1, 1.0, 3, 1, 1, 0, None, None,
                            FAKE + 64, None, None, None) == 2      # x_out overlaps g
+
+
+def test_correction_validation(L):
+    out = ctypes.c_void_p()
+    assert L.ar_corr_param_count() == 225 * 256 + 256 + 256 * 256 + 256 + 256 * 1089 + 1089
+    assert L.ar_corr_create(None, ctypes.byref(out)) == 1
+    bad = np.zeros(L.ar_corr_param_count(), dtype=np.float32)
+    bad[7] = np.nan
+    assert L.ar_corr_create(bad.ctypes.data, ctypes.byref(out)) == 1
+    assert out.value is None
+    h = np.ones(225) / 225.0
+    assert L.ar_corr_targets(h.ctypes.data, 0, FAKE) == 1
+    assert L.ar_corr_train(None, h.ctypes.data, 1, 1, 1, 1e-3, None, None) == 1
+    assert L.ar_corr_predict(None, h.ctypes.data, FAKE) == 1
+    h3 = _psf(1, 1)
+    # a model takes 15 x 15 PSFs only (the model pointer is not dereferenced)
+    assert L.ar_symprec_setup_corrected(h3.ctypes.data, 1, 1, 16, 16, 0.1, FAKE, 0, None,
+                                        ctypes.byref(out)) == 1
+    assert L.ar_symprec_setup_corrected(h3.ctypes.data, 1, 1, 16, 16, 0.0, None, 0, None,
+                                        ctypes.byref(out)) == 1
+    assert L.ar_restore_prec(None, FAKE, h3.ctypes.data, 1.0, 3, None, None, FAKE * 64, None,
+                             None, None) == 1
