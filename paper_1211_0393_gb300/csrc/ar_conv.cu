@@ -148,38 +148,46 @@ __device__ __forceinline__ void load_coefs(const ConvArgs& a, float* coef, int t
 // image sample (r0 - Q + r, c0 - Q + c).  Rows first (on in-image columns),
 // then columns on every row of the extended domain, which gives the corner
 // rules.  AR (Section 2.2): 2 x_edge - x_mirror; Reflective (Section 2.1):
-// x_{-1-i} = x_i, x_{n+i} = x_{n-1-i}.  Edge and mirror samples lie in the tile.
+// x_{-1-i} = x_i, x_{n+i} = x_{n-1-i}.  Edge and mirror samples lie in the
+// tile.  Only the out-of-image strips (at most q rows or columns per side) are
+// visited.
 template <int Q>
 __device__ void fixup_tile(const ConvArgs& a, float* tile, int WP, int r0, int c0, int tid,
                            int nthreads) {
     constexpr int W = TX + 2 * Q, H = TH + 2 * Q;
     const bool ar = a.bc == AR_BC_ANTIREFLECTIVE;
-    for (int i = tid; i < H * W; i += nthreads) {
-        const int r = i / W, c = i % W;
-        const int j1 = r0 - Q + r, j2 = c0 - Q + c;
-        if (j2 < 0 || j2 >= a.n2) continue;
+    const int rb = r0 - Q, cb = c0 - Q;                 // image coordinates of tile (0, 0)
+    // tile rows with j1 in [-q1, 0) and in [n1, n1 + q1), clipped to the tile
+    const int t0 = max(0, -a.q1 - rb), t1 = min(H, -rb);
+    const int b0 = max(0, a.n1 - rb), b1 = min(H, a.n1 + a.q1 - rb);
+    const int nt = max(0, t1 - t0), nbot = max(0, b1 - b0);
+    // in-image columns of the tile
+    const int ci0 = max(0, -cb), ci1 = min(W, a.n2 - cb), nci = max(0, ci1 - ci0);
+    for (int i = tid; i < (nt + nbot) * nci; i += nthreads) {
+        const int k = i / nci, c = ci0 + i % nci;
+        const int r = k < nt ? t0 + k : b0 + (k - nt);
+        const int j1 = rb + r;
         int re, rm;
-        if (j1 < 0 && j1 >= -a.q1) { re = 0; rm = ar ? -j1 : -j1 - 1; }
-        else if (j1 >= a.n1 && j1 < a.n1 + a.q1) {
-            re = a.n1 - 1;
-            rm = ar ? 2 * (a.n1 - 1) - j1 : 2 * a.n1 - 1 - j1;
-        } else continue;
-        const float vm = tile[(rm - (r0 - Q)) * WP + c];
-        tile[r * WP + c] = ar ? 2.f * tile[(re - (r0 - Q)) * WP + c] - vm : vm;
+        if (j1 < 0) { re = 0; rm = ar ? -j1 : -j1 - 1; }
+        else { re = a.n1 - 1; rm = ar ? 2 * (a.n1 - 1) - j1 : 2 * a.n1 - 1 - j1; }
+        const float vm = tile[(rm - rb) * WP + c];
+        tile[r * WP + c] = ar ? 2.f * tile[(re - rb) * WP + c] - vm : vm;
     }
     __syncthreads();
-    for (int i = tid; i < H * W; i += nthreads) {
-        const int r = i / W, c = i % W;
-        const int j1 = r0 - Q + r, j2 = c0 - Q + c;
-        if (j1 < -a.q1 || j1 >= a.n1 + a.q1) continue;
+    // tile columns with j2 in [-q2, 0) and [n2, n2 + q2), on rows of the extended domain
+    const int l0 = max(0, -a.q2 - cb), l1 = min(W, -cb);
+    const int g0 = max(0, a.n2 - cb), g1 = min(W, a.n2 + a.q2 - cb);
+    const int nl = max(0, l1 - l0), ng = max(0, g1 - g0);
+    const int re0 = max(0, -a.q1 - rb), re1 = min(H, a.n1 + a.q1 - rb), nr = max(0, re1 - re0);
+    for (int i = tid; i < (nl + ng) * nr; i += nthreads) {
+        const int k = i / nr, r = re0 + i % nr;
+        const int c = k < nl ? l0 + k : g0 + (k - nl);
+        const int j2 = cb + c;
         int ce, cm;
-        if (j2 < 0 && j2 >= -a.q2) { ce = 0; cm = ar ? -j2 : -j2 - 1; }
-        else if (j2 >= a.n2 && j2 < a.n2 + a.q2) {
-            ce = a.n2 - 1;
-            cm = ar ? 2 * (a.n2 - 1) - j2 : 2 * a.n2 - 1 - j2;
-        } else continue;
-        const float vm = tile[r * WP + (cm - (c0 - Q))];
-        tile[r * WP + c] = ar ? 2.f * tile[r * WP + (ce - (c0 - Q))] - vm : vm;
+        if (j2 < 0) { ce = 0; cm = ar ? -j2 : -j2 - 1; }
+        else { ce = a.n2 - 1; cm = ar ? 2 * (a.n2 - 1) - j2 : 2 * a.n2 - 1 - j2; }
+        const float vm = tile[r * WP + (cm - cb)];
+        tile[r * WP + c] = ar ? 2.f * tile[r * WP + (ce - cb)] - vm : vm;
     }
     __syncthreads();
 }
