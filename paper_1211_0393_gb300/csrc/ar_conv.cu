@@ -10,8 +10,8 @@
 // operator with the PSF rotated by 180 degrees.
 //
 // The extension is never materialised: every CTA brings its halo tile into
-// shared memory (by TMA, double- or triple-buffered in a persistent loop over
-// tiles, when the image rows are 16-byte aligned; otherwise by the threads,
+// shared memory (by TMA, double-buffered in a persistent loop over tiles,
+// when the image rows are 16-byte aligned; otherwise by the threads,
 // all loads of a thread in flight at once) and, on tiles that reach past the
 // image, overwrites the out-of-image samples with their anti-reflections
 // computed from in-tile samples.  Each thread then computes a vertical strip of R outputs of one
@@ -303,9 +303,9 @@ __device__ int g_conv_timeout;
 
 // Halo tile of the TMA path: the box starts PADL >= Q columns left of the
 // tile (a multiple of 4, so the box's x coordinate is 16-byte aligned) and
-// is WB = TX + 2 PADL wide, HB = TH + 2Q high.  NBUF boxes are in flight or
-// in use per CTA (three for 4 <= Q <= 7, measured faster on 4096^2 images;
-// two otherwise, where more buffers cost resident CTAs).
+// is WB = TX + 2 PADL wide, HB = TH + 2Q high.  Two boxes per CTA: one in
+// use, one in flight (a third was faster on 4096^2 images alone but cost
+// resident CTAs and time inside the restoration loop).
 template <int Q>
 struct TmaTile {
     static constexpr int PADL = (Q + 3) & ~3;
@@ -313,7 +313,7 @@ struct TmaTile {
     static constexpr int HB = TH + 2 * Q;
     static constexpr uint32_t BYTES = (uint32_t)WB * HB * 4;
     static constexpr uint32_t BUF = (BYTES + 127u) & ~127u;   // buffers start 128-byte aligned
-    static constexpr int NBUF = (Q >= 4 && Q <= 7) ? 3 : 2;
+    static constexpr int NBUF = 2;
     static constexpr size_t SMEM = NBUF * (size_t)BUF + (size_t)Coefs<Q>::COUNT * 4 + 8 * NBUF + 128;
 };
 
@@ -444,14 +444,17 @@ cudaError_t launch_fast(const ConvArgs& a, cudaStream_t s) {
             const int ntiles = ntx * nty;
             const int cap = sm_count() * per_sm;
             const int grid = ntiles < cap ? ntiles : cap;
+            // plain stream order: launched early (programmatic serialization) the
+            // stencil's CTAs cost the iteration more than they save (measured)
             count_launch();
-            return launch_pdl(conv_tma_kernel<Q>, dim3(grid), dim3(TX, TY), T::SMEM, s, map, a,
-                              ntx, ntiles);
+            conv_tma_kernel<Q><<<dim3(grid), dim3(TX, TY), T::SMEM, s>>>(map, a, ntx, ntiles);
+            return cudaGetLastError();
         }
     }
     dim3 grid((a.n2 + TX - 1) / TX, (a.n1 + TH - 1) / TH);
     count_launch();
-    return launch_pdl(conv_fast_kernel<Q>, grid, dim3(TX, TY), 0, s, a);
+    conv_fast_kernel<Q><<<grid, dim3(TX, TY), 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace
