@@ -310,7 +310,7 @@ def kernel_rooflines(ar, torch, dev, step):
                 "work_per_launch": "6 x 2 x 1024^3 bf16 flops"}
     else:
         ach = stencil_flops / t_st / 1e12
-        roof = {"kernel": "conv_fast_kernel<7> (AR pad + 15x15 convolution)", "bound": "alu",
+        roof = {"kernel": "conv_tma_kernel<7> (AR pad + 15x15 convolution)", "bound": "alu",
                 "achieved": round(ach, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
                 "frac": round(ach / fp32_peak, 4), "traffic": measured_traffic("stencil"),
                 "peak_source": "derived: SMs x 128 FP32 lanes x 2 x sm_max_mhz of MEASURED_PEAKS.json",
@@ -324,7 +324,7 @@ def ar_psf_shape():
 
 PROFILES = {
     "contraction": ("profiles/tc_contract_kernel_ellipses1024.md", "paper_1211_0393_gb300/csrc/ar_transform.cu"),
-    "stencil": ("profiles/conv_fast_kernel_q7_ellipses1024.md", "paper_1211_0393_gb300/csrc/ar_conv.cu"),
+    "stencil": ("profiles/conv_tma_kernel_q7_ellipses1024.md", "paper_1211_0393_gb300/csrc/ar_conv.cu"),
 }
 
 
