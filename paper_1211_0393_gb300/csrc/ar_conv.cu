@@ -91,7 +91,7 @@ __device__ __forceinline__ void split3_store(uint16_t* planes, size_t pstride, s
 }
 
 // Writes one output; returns (x_new - f)^2 for CONV_AXPY with a true image, else 0.
-__device__ __forceinline__ double conv_epilogue(const ConvArgs& a, int row, int col, float v) {
+__device__ __forceinline__ float conv_epilogue(const ConvArgs& a, int row, int col, float v) {
     const size_t o = (size_t)row * a.n2 + col;
     switch (a.mode) {
         case CONV_STORE: a.out[o] = v; break;
@@ -100,20 +100,34 @@ __device__ __forceinline__ double conv_epilogue(const ConvArgs& a, int row, int 
             const float xn = fmaf(a.tau, v, a.out[o]);
             a.out[o] = xn;
             if (a.f) {
-                const double e = (double)xn - (double)__ldg(a.f + o);
+                const float e = xn - __ldg(a.f + o);
                 return e * e;
             }
             break;
         }
         default: split3_store(a.planes, a.plane_stride, (size_t)row * a.ld + col, v); break;
     }
-    return 0.0;
+    return 0.f;
 }
 
-__device__ __forceinline__ void add_sumsq(double* sumsq, double v) {
+// *sumsq += the block's sum of v (one float64 atomic per block).  Each thread's
+// v is a float32 sum of at most RS squares (relative error ~RS 2^-24); the
+// block reduction is float64.  Called by every thread of the block.
+__device__ __forceinline__ void add_sumsq(double* sumsq, float vf) {
+    __shared__ double part[32];
+    double v = vf;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(sumsq, v);
+    const int nthreads = blockDim.x * blockDim.y;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    if ((tid & 31) == 0) part[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (nthreads + 31) / 32; ++w) t += part[w];
+        if (t != 0.0) atomicAdd(sumsq, t);
+    }
+    __syncthreads();                     // part[] is reused by the next tile
 }
 
 // Coefficient rows are padded to a multiple of 4 so that a PSF column is
@@ -230,7 +244,7 @@ __device__ __forceinline__ void compute_tile(const ConvArgs& a, const float* til
     }
 
     const int col = c0 + tx;
-    double sq = 0.0;
+    float sq = 0.f;
     if (col < a.n2) {
 #pragma unroll
         for (int r = 0; r < RS; ++r) {
@@ -392,7 +406,7 @@ conv_generic_kernel(const ConvArgs a) {
     const bool in = row < a.n1 && col < a.n2;
     const int kw = 2 * a.q2 + 1;
     float acc = 0.f;
-    double sq = 0.0;
+    float sq = 0.f;
     if (in) {
         for (int s2 = -a.q2; s2 <= a.q2; ++s2) {
             for (int s1 = -a.q1; s1 <= a.q1; ++s1) {

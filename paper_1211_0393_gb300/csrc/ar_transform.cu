@@ -315,7 +315,7 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 
     // 2) own columns: own partial sums + the peer's, then the fused next step
     const bool split_out = ep.mode == TE_SPLIT_T || ep.mode == TE_SCALE_SPLIT_T;
-    double sq = 0.0;
+    float sq = 0.f;                       // this thread's (x_new - f)^2, at most WCOLS terms
 #pragma unroll
     for (int c = 0; c < WCOLS / 16; ++c) {
         float v[16];
@@ -340,17 +340,25 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                     const float xn = fmaf(ep.tau, x, pre[jj]);
                     ep.out[o] = xn;
                     if (ep.f) {
-                        const double e = (double)xn - (double)pref[jj];
-                        sq += e * e;
+                        const float e = xn - pref[jj];
+                        sq = fmaf(e, e, sq);
                     }
                 }
             }
         }
     }
-    if (ep.sumsq) {                                      // fused ||x_{k+1} - f||^2 (float64)
+    if (ep.sumsq) {                                      // fused ||x_{k+1} - f||^2, one float64 atomic per CTA
+        __shared__ double part[NTHREADS / 32];
+        double v = sq;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
-        if (lane == 0 && sq != 0.0) atomicAdd(ep.sumsq, sq);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) part[warp] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < NTHREADS / 32; ++w) t += part[w];
+            if (t != 0.0) atomicAdd(ep.sumsq, t);
+        }
     }
     if (split_out) {
         // the staged [NP][HALF][BM] tile leaves in one TMA store (rows past M and
