@@ -63,6 +63,25 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", "1")))
 
 
+def max_over_ranks(value_ms, world, device):
+    """The largest of the ranks' timings (all ranks call this; world 1: identity)."""
+    if world <= 1:
+        return float(value_ms)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(value_ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(pixels, iters, steps, world, total_ms):
+    """Whole-job Mpixel*iter/s of `world` independent replicas, each restoring
+    `steps` images of `pixels` pixels for `iters` iterations, timed at the
+    slowest rank (weak scaling: the work per rank is fixed)."""
+    return pixels * iters * steps * world / 1e6 / (total_ms / 1e3)
+
+
 def config_dict(extra=None):
     c = {"workload": WORKLOAD, "n1": N1, "n2": N2, "psf": "15x15 motion(len 11, 30 deg)+0.2 gauss",
          "iters_per_step": ITERS, "alpha": ALPHA, "tau": TAU, "precondition": True, "noise": NU,
@@ -190,12 +209,8 @@ def run_own(args):
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    units = N1 * N2 * ITERS * args.steps * world / 1e6
-    value = units / (total_ms / 1e3)
+    total_ms = max_over_ranks(total_ms, world, dev)
+    value = replica_throughput(N1 * N2, ITERS, args.steps, world, total_ms)
 
     # ---- end to end through host buffers: H2D of g and f, restore, D2H of x
     g_h = torch.from_numpy(g).pin_memory()
@@ -214,11 +229,8 @@ def run_own(args):
         b.synchronize()
         e2e_ms.append(a.elapsed_time(b))
     e2e_total = sum(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = N1 * N2 * ITERS * len(e2e_ms) * world / 1e6 / (e2e_total / 1e3)
+    e2e_total = max_over_ranks(e2e_total, world, dev)
+    e2e_value = replica_throughput(N1 * N2, ITERS, len(e2e_ms), world, e2e_total)
 
     out = None
     if rank == 0:
