@@ -38,7 +38,7 @@ def _worker(rank, world, port, out):
 
 def test_two_rank_timing_is_the_slowest_rank_and_counts_all_work():
     world = 2
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
     for r in range(world):
