@@ -18,7 +18,7 @@
  *    psf[(i1+q1)*(2q2+1) + (i2+q2)] = h_{i1,i2} (eq. coefficienti_psf).
  *    The blur is a true convolution, g_i = sum_s h_s f_{i-s}.
  *    0 <= q_j <= n_j - 1 for the blur (the anti-reflection must stay inside
- *    the image); the preconditioner additionally needs q_j <= n_j - 3 (the
+ *    the image); the AR preconditioner additionally needs q_j <= n_j - 3 (the
  *    support condition of Section 2.2).  q_j <= 15 runs on the fast
  *    register-blocked kernels, larger supports on a generic kernel.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
@@ -58,8 +58,9 @@ typedef enum ar_status {
  * 2.2, the default of every call without a bc argument); AR_BC_REFLECTIVE
  * (Section 2.1: reflection about the boundary, DCT-III algebra) and
  * AR_BC_PERIODIC (circulant) are the comparison BCs of Section 4's tables.
- * The blur, reblur and plain Landweber support all three; the preconditioner
- * supports AR and Reflective (AR_ERR_UNSUPPORTED for Periodic). */
+ * Every call with a bc argument supports all three: the Reflective
+ * preconditioner works in the DCT-III basis, the Periodic one in the real
+ * separable Hartley basis (see ar_symprec_setup_bc). */
 typedef enum ar_bc { AR_BC_ANTIREFLECTIVE = 0, AR_BC_REFLECTIVE = 1, AR_BC_PERIODIC = 2 } ar_bc;
 
 /* Arithmetic of the AR transform contractions (tensor cores).

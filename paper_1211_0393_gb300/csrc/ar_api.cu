@@ -426,6 +426,8 @@ ar_status ar_symprec_setup_corrected(const double* psf_host, int q1, int q2, int
     if (M && (q1 != AR_CORR_Q || q2 != AR_CORR_Q))
         return fail(AR_ERR_INVALID_ARG, "the correction model takes %dx%d PSFs", 2 * AR_CORR_Q + 1,
                     2 * AR_CORR_Q + 1);
+    if (M && !corr_on_current_device(M))
+        return fail(AR_ERR_INVALID_ARG, "the correction model belongs to another device");
     AR_TRY(check_image_sizes(n1, n2, 3));
     AR_TRY(check_support(n1, n2, q1, q2, 3));
     if (!(alpha > 0.0) || !std::isfinite(alpha))
@@ -446,6 +448,9 @@ ar_status ar_symprec_setup_corrected(const double* psf_host, int q1, int q2, int
 
 ar_status ar_symprec_solve(const ar_prec* P, const float* y, float* z, void* stream) {
     if (!P || !y || !z) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
+    int dev = 0;
+    AR_CUDA(cudaGetDevice(&dev));
+    if (dev != P->device) return fail(AR_ERR_INVALID_ARG, "preconditioner belongs to device %d", P->device);
     const size_t nb = (size_t)P->n1 * P->n2 * sizeof(float);
     if (y != z && overlaps(y, nb, z, nb)) return fail(AR_ERR_ALIAS, "z partially overlaps y");
     return transform_apply(P->plan, P->d32, P->d32_odd, y, DIN_FP32, z, DOUT_STORE, 0.f,

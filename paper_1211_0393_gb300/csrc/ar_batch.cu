@@ -17,6 +17,7 @@
 #include <vector>
 
 struct ar_batch {
+    int device = 0;
     int count = 0, iters = 0, precondition = 0;
     std::vector<ar_batch_item> items;
     std::vector<ar_prec*> precs;
@@ -144,6 +145,7 @@ ar_status ar_batch_create(const ar_batch_item* items, int count, double tau, int
     ar_batch* B = new (std::nothrow) ar_batch();
     if (!B) return fail(AR_ERR_ALLOC, "host allocation of the batch plan");
     B->count = count;
+    cudaGetDevice(&B->device);
     B->iters = iters;
     B->precondition = pc;
     B->items.assign(items, items + count);
@@ -217,6 +219,9 @@ ar_status ar_batch_create(const ar_batch_item* items, int count, double tau, int
 
 ar_status ar_batch_run(ar_batch* B, void* stream) {
     if (!B) return fail(AR_ERR_INVALID_ARG, "null batch");
+    int dev = 0;
+    AR_CUDA(cudaGetDevice(&dev));
+    if (dev != B->device) return fail(AR_ERR_INVALID_ARG, "batch belongs to device %d", B->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     AR_CUDA(cudaMemsetAsync(B->bad, 0, B->count * sizeof(unsigned long long), s));
     AR_CUDA(cudaGraphLaunch(B->exec, s));

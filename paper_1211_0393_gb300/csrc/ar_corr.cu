@@ -357,6 +357,11 @@ ar_status corr_delta(const double* psf_dev64, int q1, int q2, int n1, int n2, co
     return AR_OK;
 }
 
+bool corr_on_current_device(const ar_corr* model) {
+    int dev = 0;
+    return cudaGetDevice(&dev) == cudaSuccess && dev == model->device;
+}
+
 size_t corr_scratch_doubles(int q1, int q2, int n1, int n2) {
     const size_t exact = 2 * ((size_t)(2 * q1 + 1) * n2 + (size_t)n1 * (2 * q1 + 1) +
                               (size_t)n2 * (2 * q2 + 1));
@@ -405,6 +410,7 @@ void ar_corr_destroy(ar_corr* M) {
 
 ar_status ar_corr_params(const ar_corr* M, float* params_host) {
     if (!M || !params_host) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
+    if (!corr_on_current_device(M)) return fail(AR_ERR_INVALID_ARG, "model belongs to another device");
     AR_CUDA(cudaDeviceSynchronize());
     AR_CUDA(cudaMemcpy(params_host, M->P, NPARAM * sizeof(float), cudaMemcpyDeviceToHost));
     return AR_OK;
@@ -440,6 +446,7 @@ ar_status ar_corr_targets(const double* psfs_host, int count, double* delta_host
 
 ar_status ar_corr_predict(const ar_corr* M, const double* psf_host, float* table_host) {
     if (!M || !psf_host || !table_host) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
+    if (!corr_on_current_device(M)) return fail(AR_ERR_INVALID_ARG, "model belongs to another device");
     AR_TRY(check_psfs15(psf_host, 1));
     double* h = nullptr;
     float* buf = nullptr;
@@ -469,6 +476,7 @@ ar_status ar_corr_predict(const ar_corr* M, const double* psf_host, float* table
 ar_status ar_corr_train(ar_corr* M, const double* psfs_host, int count, int epochs, int batch,
                         double lr, float* loss_trace_host, void* stream) {
     if (!M || !psfs_host) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
+    if (!corr_on_current_device(M)) return fail(AR_ERR_INVALID_ARG, "model belongs to another device");
     if (count < 1 || epochs < 0 || batch < 1)
         return fail(AR_ERR_INVALID_ARG, "count %d, epochs %d, batch %d", count, epochs, batch);
     if (!(lr > 0.0) || !std::isfinite(lr))

@@ -176,6 +176,7 @@ ar_status prec_build(const double* psf_host, int q1, int q2, int n1, int n2, dou
 ar_status corr_delta(const double* psf_dev64, int q1, int q2, int n1, int n2, const ar_corr* model,
                      const double* psf_host, double* delta, double* scratch, cudaStream_t s);
 size_t corr_scratch_doubles(int q1, int q2, int n1, int n2);
+bool corr_on_current_device(const ar_corr* model);
 
 // Launch accounting: every kernel launch site calls count_launch(k).
 void count_launch(unsigned k = 1);
