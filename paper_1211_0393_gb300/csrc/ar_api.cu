@@ -148,6 +148,14 @@ ar_status apply_common(const float* x, float* y, int n1, int n2, const float* ps
 }
 
 // Builds the preconditioner's device data on `s` without synchronizing.
+void prec_release(ar_prec* P, cudaStream_t s) {
+    if (!P) return;
+    transform_plan_release(P->plan, s);
+    for (void* q : {(void*)P->lam64, (void*)P->d64, (void*)P->d32, (void*)P->d32_odd})
+        if (q) cudaFreeAsync(q, s);
+    delete P;
+}
+
 ar_status prec_build(const double* psf_host, int q1, int q2, int n1, int n2, double alpha,
                      int bc, int precision, cudaStream_t s, bool keep64, ar_prec** out,
                      int correction, const ar_corr* model) {
@@ -313,7 +321,7 @@ static ar_status restore_run(const float* g, const double* psf_host, int n1, int
         }
     }
     cudaError_t e = cudaStreamSynchronize(s);
-    if (P) ar_symprec_destroy(P);
+    if (P) prec_release(P, s);       // after the synchronize above: no work pending
     if (st != AR_OK) return st;
     if (e != cudaSuccess) return cuda_fail(e, "restore");
     if (f_true) {

@@ -102,6 +102,8 @@ struct TransformPlan;
 ar_status transform_plan_create(int n1, int n2, int bc, int precision, cudaStream_t stream,
                                 TransformPlan** out);
 void transform_plan_destroy(TransformPlan* p);
+// Frees the plan's buffers in the order of stream s (after its pending work).
+void transform_plan_release(TransformPlan* p, cudaStream_t s);
 
 // Where the input of D comes from.
 enum DInput : int {
@@ -164,6 +166,10 @@ ar_status check_psf_host(const double* h, int q1, int q2);
 void set_pool_threshold_once();
 // Builds a preconditioner on `s` without synchronizing (keep64: also keep the
 // float64 eigenvalues and filter).
+// Frees a preconditioner whose buffers came from the stream-ordered pool, in
+// the order of stream s (no device-wide synchronization).
+void prec_release(ar_prec* P, cudaStream_t s);
+
 // correction: 0 none, 1 exact spectral correction, 2 the model's (AR only).
 ar_status prec_build(const double* psf_host, int q1, int q2, int n1, int n2, double alpha,
                      int bc, int precision, cudaStream_t s, bool keep64, ar_prec** out,

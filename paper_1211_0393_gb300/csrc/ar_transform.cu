@@ -572,8 +572,10 @@ struct Operand {               // bf16 planes of a rows x K matrix and its TMA m
 
 inline int mode_index(int np) { return np == 3 ? 0 : 1; }
 
+// only_np (0: both) restricts the maps of a per-plan image operand to the
+// plan's precision mode.
 ar_status alloc_operand(Operand& o, int rows, int K, int box_rows, cudaStream_t s,
-                        bool permanent = false) {
+                        bool permanent = false, int only_np = 0) {
     o.rows = rows;
     o.K = K;
     o.ld = round_up8(K);
@@ -582,6 +584,7 @@ ar_status alloc_operand(Operand& o, int rows, int K, int box_rows, cudaStream_t 
     if (permanent) AR_CUDA(cudaMalloc((void**)&o.planes, bytes));
     else AR_CUDA(cudaMallocAsync((void**)&o.planes, bytes, s));
     for (int np = 3; np >= 2; --np) {
+        if (only_np && np != only_np) continue;
         AR_TRY(make_map(&o.map[mode_index(np)], o.planes, K, rows, o.ld, BK, box_rows, np, true));
         if (!permanent)
             AR_TRY(make_map(&o.omap[mode_index(np)], o.planes, K, rows, o.ld, BM, HALF, np, false));
@@ -722,9 +725,9 @@ ar_status transform_plan_create(int n1, int n2, int bc, int precision, cudaStrea
         p->T2 = t2.T;
         p->Tp2 = t2.Tp;
     }
-    if (st == AR_OK) st = alloc_operand(p->P, n1, n2, BM, s);
-    if (st == AR_OK && bc == AR_BC_PERIODIC) st = alloc_operand(p->P2, n1, n2, BM, s);
-    if (st == AR_OK) st = alloc_operand(p->Qo, n2, n1, BM, s);
+    if (st == AR_OK) st = alloc_operand(p->P, n1, n2, BM, s, false, p->np);
+    if (st == AR_OK && bc == AR_BC_PERIODIC) st = alloc_operand(p->P2, n1, n2, BM, s, false, p->np);
+    if (st == AR_OK) st = alloc_operand(p->Qo, n2, n1, BM, s, false, p->np);
     if (st == AR_OK && cudaMallocAsync((void**)&p->err, sizeof(int), s) != cudaSuccess)
         st = fail(AR_ERR_ALLOC, "transform error flag");
     if (st == AR_OK && cudaMemsetAsync(p->err, 0, sizeof(int), s) != cudaSuccess)
@@ -743,6 +746,13 @@ void transform_plan_destroy(TransformPlan* p) {
     cudaFree(p->P2.planes);
     cudaFree(p->Qo.planes);
     cudaFree(p->err);
+    delete p;
+}
+
+void transform_plan_release(TransformPlan* p, cudaStream_t s) {
+    if (!p) return;
+    for (void* q : {(void*)p->P.planes, (void*)p->P2.planes, (void*)p->Qo.planes, (void*)p->err})
+        if (q) cudaFreeAsync(q, s);
     delete p;
 }
 
