@@ -208,6 +208,7 @@ ar_status prec_build(const double* psf_host, int q1, int q2, int n1, int n2, dou
             st = setup_eigen(h64, q1, q2, n1, n2, alpha, bc, P->lam64, P->d64, P->d32, P->d32_odd,
                              work, s, delta);
         if (st == AR_OK) st = transform_plan_create(n1, n2, bc, precision, s, &P->plan);
+        if (st == AR_OK) st = transform_set_filter(P->plan, P->d32, s);
     }
     if (st != AR_OK) {
         ar_symprec_destroy(P);

@@ -117,6 +117,11 @@ enum DOutput : int {
     DOUT_AXPY = 1        // x += tau * D y
 };
 
+// Hands the plan the filter d (float32, n1 x n2) the next transform_apply
+// calls use: AR plans keep it in their folded spectral order (call after
+// every change of d); other plans read d32 as given to transform_apply.
+ar_status transform_set_filter(TransformPlan* p, const float* d32, cudaStream_t stream);
+
 // Pointer to the operand planes the stencil must fill for DIN_SPLIT.
 uint16_t* transform_input_planes(TransformPlan* p, size_t* plane_stride, int* ld);
 

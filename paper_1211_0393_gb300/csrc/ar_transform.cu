@@ -109,7 +109,22 @@ struct TcEpiArgs {
     float tau;
     const float* f;        // TE_AXPY_T: true image (same layout as out) or null
     double* sumsq;         // TE_AXPY_T with f: += sum (x_new - f)^2
+    // Folded (even/odd) transforms.  kdiag: A and B are block diagonal in K, so
+    // the output columns of the first half of N use the first half of K and
+    // the others the second half.  pair: the 128 rows of an A tile are two
+    // 64-row boxes, row r paired with row 64 + r of the tile:
+    //   PAIR_MIRROR: boxes at rows m0 and mrows - m0 - 64 (row i with row
+    //     mrows - 1 - i); the output is the even/odd fold of the M index, the
+    //     sums (i < npair) and differences (i < nminus, at column kout + i);
+    //   PAIR_HALVES: boxes at rows m0 and mhalf + m0 (row j of the first half
+    //     with row j of the second); the output is the unfold, row j gets
+    //     first + second (j < npair), row nout - 1 - j first - second (j < nminus).
+    int kdiag;
+    int pair;
+    int mrows, mhalf, npair, nminus, kout, nout;
 };
+
+enum TcPair : int { PAIR_NONE = 0, PAIR_MIRROR = 1, PAIR_HALVES = 2 };
 
 __device__ __forceinline__ void split3(float v, uint16_t& h0, uint16_t& h1, uint16_t& h2) {
     const __nv_bfloat16 p0 = __float2bfloat16_rn(v);
@@ -142,9 +157,9 @@ constexpr int WCOLS = HALF / 2;         // columns of the CTA's half handled by 
 
 template <int NP>
 __global__ void __cluster_dims__(1, 1, SPLITK) __launch_bounds__(NTHREADS, 1)
-tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const __grid_constant__ CUtensorMap tmO, int M, int N, int K, const TcEpiArgs ep,
-                   int* err) {
+tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA64,
+                   const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmO,
+                   int M, int N, int K, const TcEpiArgs ep, int* err) {
     using namespace tc;
     using Mode = TcMode<NP>;
     constexpr int STAGES = Mode::STAGES;
@@ -166,12 +181,29 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int quarter = warp & 3, sub = warp >> 2;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int m0 = blockIdx.x * (ep.pair ? BM / 2 : BM), n0 = blockIdx.y * BN;
     const uint32_t rank = cluster_ctarank();
-    const int nk_all = (K + BK - 1) / BK;
+    int nk_all = (K + BK - 1) / BK, kb0 = 0;
+    if (ep.kdiag) {                      // block-diagonal operands: this tile's half of K
+        nk_all /= 2;
+        if (n0 >= N / 2) kb0 = nk_all;
+    }
     const int nk_first = (nk_all + 1) / 2;
-    const int kb_begin = rank == 0 ? 0 : nk_first;
+    const int kb_begin = kb0 + (rank == 0 ? 0 : nk_first);
     const int nk = rank == 0 ? nk_first : nk_all - nk_first;
+    // A tile of k-block kb into dst: one 3D box, or two 64-row boxes per plane
+    auto load_a = [&](uint32_t dst, int kb, uint32_t bar) {
+        if (!ep.pair) {
+            tma_load_3d(dst, &tmA, kb * BK, m0, 0, bar);
+            return;
+        }
+        const int r2 = ep.pair == PAIR_MIRROR ? ep.mrows - m0 - BM / 2 : ep.mhalf + m0;
+#pragma unroll
+        for (int pl = 0; pl < NP; ++pl) {
+            tma_load_3d(dst + pl * A_PLANE, &tmA64, kb * BK, m0, pl, bar);
+            tma_load_3d(dst + pl * A_PLANE + (BM / 2) * BK * 2, &tmA64, kb * BK, r2, pl, bar);
+        }
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -204,7 +236,7 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         }
         pdl_wait();
         for (int kb = 0; kb < npre; ++kb)
-            tma_load_3d(base + kb * STAGE_BYTES, &tmA, (kb_begin + kb) * BK, m0, 0, bars + 8u * kb);
+            load_a(base + kb * STAGE_BYTES, kb_begin + kb, bars + 8u * kb);
         int issued = npre;
         for (int kb = npre; kb < nk; ++kb) {
             const int s = kb % STAGES;
@@ -215,7 +247,7 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             if (*sflag) break;
             const uint32_t a = base + s * STAGE_BYTES;
             mbar_arrive_expect_tx(bars + 8u * s, STAGE_BYTES);
-            tma_load_3d(a, &tmA, (kb_begin + kb) * BK, m0, 0, bars + 8u * s);
+            load_a(a, kb_begin + kb, bars + 8u * s);
             tma_load_3d(a + A_STAGE, &tmB, (kb_begin + kb) * BK, n0, 0, bars + 8u * s);
             ++issued;
         }
@@ -270,7 +302,15 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     // ---- epilogue.  Warp w reads TMEM lanes 32(w%4).. (tile rows m0 + 32(w%4) + lane) and
     // handles WCOLS of the CTA's HALF columns; its inputs are fetched while the MMAs run.
     const int lrow = quarter * 32 + lane;
-    const int row = m0 + lrow;
+    // output row of this thread's values: the tile row, or for the unfold the
+    // row j = m0 + lrow (first half of the tile) or nout - 1 - j (second half)
+    int row = m0 + lrow;
+    bool row_ok = row < M;
+    if (ep.pair == PAIR_HALVES) {
+        const int j = m0 + (lrow & (BM / 2 - 1));
+        row = lrow < BM / 2 ? j : ep.nout - 1 - j;
+        row_ok = lrow < BM / 2 ? j < ep.npair : j < ep.nminus;
+    }
     const uint32_t peer = rank ^ 1u;
     const int ocol0 = (int)rank * HALF + sub * WCOLS;    // tile-relative own columns
     const int pcol0 = (int)peer * HALF + sub * WCOLS;    // tile-relative peer columns
@@ -279,7 +319,7 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 #pragma unroll
     for (int j = 0; j < WCOLS; ++j) {
         const int col = n0 + ocol0 + j;
-        const bool in = row < M && col < N;
+        const bool in = row_ok && col < N;
         pre[j] = 0.f;
         pref[j] = 0.f;
         if (ep.mode == TE_SCALE_SPLIT_T) {
@@ -315,24 +355,63 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 
     // 2) own columns: own partial sums + the peer's, then the fused next step
     const bool split_out = ep.mode == TE_SPLIT_T || ep.mode == TE_SCALE_SPLIT_T;
-    float sq = 0.f;                       // this thread's (x_new - f)^2, at most WCOLS terms
+    float xv[WCOLS];
 #pragma unroll
     for (int c = 0; c < WCOLS / 16; ++c) {
         float v[16];
         acc_sum16(trow, ocol0 + c * 16, nacc, v);
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            const int jj = c * 16 + j;                  // 0..WCOLS-1
-            const int hc = sub * WCOLS + jj;            // column within the CTA's half
-            float x = v[j] + recv_ptr[hc * BM + lrow];
+            const int hc = sub * WCOLS + c * 16 + j;    // column within the CTA's half
+            xv[c * 16 + j] = v[j] + recv_ptr[hc * BM + lrow];
+        }
+    }
+    // paired rows: exchange through shared memory ([HALF][BM] float32 in the
+    // stage area, the split output staged after it)
+    float* xbuf = reinterpret_cast<float*>(gbase);
+    uint16_t* stage = ep.pair ? stage_out + 2 * HALF * BM : stage_out;
+    if (ep.pair) {
+#pragma unroll
+        for (int jj = 0; jj < WCOLS; ++jj) xbuf[(sub * WCOLS + jj) * BM + lrow] = xv[jj];
+        __syncthreads();
+        const int partner = ep.pair == PAIR_MIRROR ? BM - 1 - lrow : lrow ^ (BM / 2);
+        const bool first = lrow < BM / 2;
+#pragma unroll
+        for (int jj = 0; jj < WCOLS; ++jj) {
+            const float xp = xbuf[(sub * WCOLS + jj) * BM + partner];
+            xv[jj] = first ? xv[jj] + xp : xp - xv[jj];
+        }
+    }
+    float sq = 0.f;                       // this thread's (x_new - f)^2, at most WCOLS terms
+    if (ep.pair == PAIR_MIRROR) {
+        // fold: lanes < 64 hold the sums of rows i = m0 + lrow, the others the
+        // differences of rows i = m0 + 127 - lrow; beyond npair / nminus: 0
+        const int box = lrow < BM / 2 ? 0 : 1;
+        const int ir = box == 0 ? lrow : BM - 1 - lrow;
+        const bool valid = m0 + ir < (box == 0 ? ep.npair : ep.nminus);
+#pragma unroll
+        for (int jj = 0; jj < WCOLS; ++jj) {
+            const int hc = sub * WCOLS + jj;
+            uint16_t h0, h1, h2;
+            split3(valid ? xv[jj] : 0.f, h0, h1, h2);
+            uint16_t* st = stage + (size_t)box * NP * HALF * (BM / 2);
+            st[(0 * HALF + hc) * (BM / 2) + ir] = h0;
+            st[(1 * HALF + hc) * (BM / 2) + ir] = h1;
+            if (NP == 3) st[(2 * HALF + hc) * (BM / 2) + ir] = h2;
+        }
+    } else {
+#pragma unroll
+        for (int jj = 0; jj < WCOLS; ++jj) {
+            const int hc = sub * WCOLS + jj;
+            float x = xv[jj];
             if (split_out) {
                 if (ep.mode == TE_SCALE_SPLIT_T) x *= pre[jj];
                 uint16_t h0, h1, h2;
                 split3(x, h0, h1, h2);
-                stage_out[(0 * HALF + hc) * BM + lrow] = h0;
-                stage_out[(1 * HALF + hc) * BM + lrow] = h1;
-                if (NP == 3) stage_out[(2 * HALF + hc) * BM + lrow] = h2;
-            } else if (ok && row < M && n0 + ocol0 + jj < N) {
+                stage[(0 * HALF + hc) * BM + lrow] = h0;
+                stage[(1 * HALF + hc) * BM + lrow] = h1;
+                if (NP == 3) stage[(2 * HALF + hc) * BM + lrow] = h2;
+            } else if (ok && row_ok && n0 + ocol0 + jj < N) {
                 const size_t o = (size_t)(n0 + ocol0 + jj) * ep.ldo + row;
                 if (ep.mode == TE_STORE_T) {
                     ep.out[o] = x;
@@ -362,11 +441,19 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     }
     if (split_out) {
         // the staged [NP][HALF][BM] tile leaves in one TMA store (rows past M and
-        // columns past N are clipped by the tensor map)
+        // columns past N are clipped by the tensor map); the fold's two
+        // [NP][HALF][64] boxes go to columns m0 and kout + m0 of the output
         fence_proxy_async_smem();
         __syncthreads();
         if (threadIdx.x == 0 && ok) {
-            tma_store_3d(&tmO, m0, n0 + (int)rank * HALF, 0, base);
+            const uint32_t sb = base + (ep.pair ? 2u * HALF * BM * 2u : 0u);
+            if (ep.pair == PAIR_MIRROR) {
+                tma_store_3d(&tmO, m0, n0 + (int)rank * HALF, 0, sb);
+                tma_store_3d(&tmO, ep.kout + m0, n0 + (int)rank * HALF, 0,
+                             sb + (uint32_t)(NP * HALF * (BM / 2) * 2));
+            } else {
+                tma_store_3d(&tmO, m0, n0 + (int)rank * HALF, 0, sb);
+            }
             bulk_commit();
             bulk_wait_read();
         }
@@ -505,6 +592,124 @@ __global__ void fill_bc_transforms_kernel(int m, int ld, int bc, uint16_t* Tt, u
     }
 }
 
+// ----------------------------------------------------- folded AR transforms --
+// The AR pair has the reflection symmetry of the sine transform: row s of
+// T~'_m (s interior) satisfies T~'[s][m-1-t] = (-1)^(s+1) T~'[s][t], including
+// the boundary columns (Q J p = (-1)^(s+1) Q p), and column k of T'_m
+// satisfies T'[m-1-s][k] = (-1)^(k+1) T'[s][k].  With the spatial fold
+// y+_t = y_t + y_{m-1-t}, y-_t = y_t - y_{m-1-t} (t < ceil(m/2), resp.
+// floor(m/2)) and the spectral order [u+, s = 1, 3, 5, .. | u-, s = 2, 4, ..],
+// where u+- = y+-_0 replace the unit rows 0 and m-1, the analysis and the
+// synthesis become block diagonal (half the products).  Half blocks are
+// padded: spectral and folded-output to a multiple of 128 rows (Hs), folded
+// spatial K to a multiple of 64 (Kh).  The filter d is equal at spectral
+// indices 0 and m-1, so it applies to u+ and u- alike.
+struct FoldDims {
+    int m, h, ha, Hs, Kh;               // h = ceil(m/2), ha = floor(m/2)
+};
+
+__host__ __device__ inline FoldDims fold_dims(int m) {
+    FoldDims f;
+    f.m = m;
+    f.h = (m + 1) / 2;
+    f.ha = m / 2;
+    f.Hs = (f.h + 127) / 128 * 128;
+    f.Kh = (f.h + 63) / 64 * 64;
+    return f;
+}
+
+// spectral folded index kf -> kind (0 u+, 1 odd interior, 2 u-, 3 even interior, -1 padding), s
+__device__ __forceinline__ int spec_of(int kf, const FoldDims& f, int& s) {
+    const bool anti = kf >= f.Hs;
+    const int u = anti ? kf - f.Hs : kf;
+    if (u == 0) {
+        s = 0;
+        return anti ? 2 : 0;
+    }
+    s = anti ? 2 * u : 2 * u - 1;
+    if (s > f.m - 2) return -1;
+    return anti ? 3 : 1;
+}
+
+// T~'_m[s][t] (normalisation dropped), T'_m[s][t] interior columns only
+__device__ __forceinline__ double ar_tt(int s, int t, int m, const double* tab, const double* qp,
+                                       const double* qjp) {
+    if (s == 0) return t == 0 ? 1.0 : 0.0;
+    if (s == m - 1) return t == m - 1 ? 1.0 : 0.0;
+    if (t == 0) return -qp[s - 1];
+    if (t == m - 1) return -qjp[s - 1];
+    return q_entry(tab, s, t, m);
+}
+
+__device__ __forceinline__ double ar_t_interior(int s, int k, int m, const double* tab) {
+    return (s == 0 || s == m - 1) ? 0.0 : q_entry(tab, s, k, m);
+}
+
+__device__ __forceinline__ void store3(uint16_t* T, size_t ps, size_t o, double v) {
+    uint16_t a0, a1, a2;
+    split3_f64(v, a0, a1, a2);
+    T[o] = a0;
+    T[ps + o] = a1;
+    T[2 * ps + o] = a2;
+}
+
+// which: 0 Ttp (analysis, spectral rows folded, natural K), 1 Ttf (analysis,
+// block diagonal over folded K), 2 Tsf (synthesis, folded outputs, block
+// diagonal), 3 Tsp (synthesis, natural outputs, folded spectral K).
+__global__ void fill_folded_kernel(int m, int which, int rows, int K, int ld, const double* tab,
+                                   const double* qp, const double* qjp, uint16_t* T) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)rows * K) return;
+    const int r = (int)(idx / K), c = (int)(idx % K);
+    const FoldDims f = fold_dims(m);
+    double v = 0.0;
+    int s = 0;
+    if (which == 0) {                                   // row: spectral kf, col: t
+        const int kind = spec_of(r, f, s);
+        if (kind == 0) v = (c == 0 || c == m - 1) ? 1.0 : 0.0;
+        else if (kind == 2) v = c == 0 ? 1.0 : (c == m - 1 ? -1.0 : 0.0);
+        else if (kind > 0) v = ar_tt(s, c, m, tab, qp, qjp);
+    } else if (which == 1) {                            // row: spectral kf, col: folded t
+        const int kind = spec_of(r, f, s);
+        const bool anti_row = r >= f.Hs, anti_col = c >= f.Kh;
+        const int t = anti_col ? c - f.Kh : c;
+        if (kind >= 0 && anti_row == anti_col && t < (anti_col ? f.ha : f.h)) {
+            if (kind == 0 || kind == 2) v = t == 0 ? 1.0 : 0.0;
+            else v = ar_tt(s, t, m, tab, qp, qjp) * (t == m - 1 - t ? 0.5 : 1.0);
+        }
+    } else if (which == 2) {                            // row: folded output s, col: spectral kf
+        const bool anti_row = r >= f.Hs, anti_col = c >= f.Hs;
+        const int so = anti_row ? r - f.Hs : r;
+        int k = 0;
+        const int kind = spec_of(c, f, k);
+        if (kind >= 0 && anti_row == anti_col && so < (anti_row ? f.ha : f.h)) {
+            if (kind == 0) v = 0.5;
+            else if (kind == 2) v = 0.5 * (2.0 * (1.0 - (double)so / (double)(m - 1)) - 1.0);
+            else v = ar_t_interior(so, k, m, tab);
+        }
+    } else {                                            // row: natural output s, col: spectral kf
+        int k = 0;
+        const int kind = spec_of(c, f, k);
+        if (kind == 0) v = 0.5;
+        else if (kind == 2) v = 0.5 * (2.0 * (1.0 - (double)r / (double)(m - 1)) - 1.0);
+        else if (kind > 0) v = ar_t_interior(r, k, m, tab);
+    }
+    store3(T, (size_t)rows * ld, (size_t)r * ld + c, v);
+}
+
+// d in the folded spectral order of both axes (0 in the padding).
+__global__ void fold_filter_kernel(const float* __restrict__ d, int n1, int n2,
+                                   float* __restrict__ df) {
+    const FoldDims f1 = fold_dims(n1), f2 = fold_dims(n2);
+    const int N1 = 2 * f1.Hs, N2 = 2 * f2.Hs;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)N1 * N2) return;
+    const int a = (int)(idx / N2), b = (int)(idx % N2);
+    int s1 = 0, s2 = 0;
+    const bool ok = spec_of(a, f1, s1) >= 0 && spec_of(b, f2, s2) >= 0;
+    df[idx] = ok ? d[(size_t)s1 * n2 + s2] : 0.f;
+}
+
 // float32 image -> bf16x3 planes (row pitch ld).
 __global__ void split_image_kernel(const float* __restrict__ y, int n1, int n2, int ld,
                                    uint16_t* planes, size_t pstride) {
@@ -547,12 +752,13 @@ int round_up8(int v) { return (v + 7) & ~7; }
 // 3D map over bf16x3 planes {K (inner), rows, 3 planes} with box
 // {box_k, box_rows, 3}: 64-byte swizzle for operand loads, none for stores.
 ar_status make_map(CUtensorMap* map, const uint16_t* planes, int K, int rows, int ld, int box_k,
-                   int box_rows, int nplanes, bool swizzle) {
+                   int box_rows, int nplanes, bool swizzle, int box_planes = 0) {
     auto enc = encode_fn();
     if (!enc) return fail(AR_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
     cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)nplanes};
     cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)rows * ld * 2};
-    cuuint32_t box[3] = {(cuuint32_t)box_k, (cuuint32_t)box_rows, (cuuint32_t)nplanes};
+    cuuint32_t box[3] = {(cuuint32_t)box_k, (cuuint32_t)box_rows,
+                         (cuuint32_t)(box_planes ? box_planes : nplanes)};
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(planes), dims,
                      strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -568,14 +774,18 @@ struct Operand {               // bf16 planes of a rows x K matrix and its TMA m
     size_t pstride = 0;
     CUtensorMap map[2];        // operand loads, [0]: 3 planes, [1]: 2 planes; box {BK, box_rows, np}, 64B swizzle
     CUtensorMap omap[2];       // epilogue stores (image operands): box {BM, HALF, np}
+    CUtensorMap map64[2];      // paired A tiles: one plane of 64 rows, box {BK, 64, 1}
+    CUtensorMap omapf[2];      // folded epilogue stores: box {64, HALF, np}
 };
+
+enum OperandMaps : int { OM_PAIR_A = 1, OM_FOLD_OUT = 2 };
 
 inline int mode_index(int np) { return np == 3 ? 0 : 1; }
 
 // only_np (0: both) restricts the maps of a per-plan image operand to the
 // plan's precision mode.
 ar_status alloc_operand(Operand& o, int rows, int K, int box_rows, cudaStream_t s,
-                        bool permanent = false, int only_np = 0) {
+                        bool permanent = false, int only_np = 0, int extra = 0) {
     o.rows = rows;
     o.K = K;
     o.ld = round_up8(K);
@@ -588,6 +798,12 @@ ar_status alloc_operand(Operand& o, int rows, int K, int box_rows, cudaStream_t 
         AR_TRY(make_map(&o.map[mode_index(np)], o.planes, K, rows, o.ld, BK, box_rows, np, true));
         if (!permanent)
             AR_TRY(make_map(&o.omap[mode_index(np)], o.planes, K, rows, o.ld, BM, HALF, np, false));
+        if (extra & OM_PAIR_A)
+            AR_TRY(make_map(&o.map64[mode_index(np)], o.planes, K, rows, o.ld, BK, BM / 2, np, true,
+                            1));
+        if (extra & OM_FOLD_OUT)
+            AR_TRY(make_map(&o.omapf[mode_index(np)], o.planes, K, rows, o.ld, BM / 2, HALF, np,
+                            false));
     }
     return AR_OK;
 }
@@ -596,22 +812,21 @@ ar_status alloc_operand(Operand& o, int rows, int K, int box_rows, cudaStream_t 
 // synthesis T matrices, and for Periodic the flipped synthesis Tp.
 struct TransformSet {
     Operand Tt, T, Tp;
+    Operand Ttp, Ttf, Tsf, Tsp;   // AR: the folded forms (the natural Tt, T are not built)
 };
 
 void free_set(TransformSet& ts) {
-    cudaFree(ts.Tt.planes);
-    cudaFree(ts.T.planes);
-    cudaFree(ts.Tp.planes);
+    for (Operand* o : {&ts.Tt, &ts.T, &ts.Tp, &ts.Ttp, &ts.Ttf, &ts.Tsf, &ts.Tsp}) cudaFree(o->planes);
 }
 
-// Builds the operands of (m, bc) on `s` and waits for them.  AR: T~'_m and
-// T'_m of Theorem 1 (eq. Qn for the interior, the boundary columns Q p and
-// Q J p as length-m reductions).
+// Builds the operands of (m, bc) on `s` and waits for them.  AR: the folded
+// forms of T~'_m and T'_m of Theorem 1 (eq. Qn for the interior, the boundary
+// columns Q p and Q J p as length-m reductions).
 ar_status build_transforms(int m, int bc, TransformSet& ts, cudaStream_t s) {
-    AR_TRY(alloc_operand(ts.Tt, m, m, BN, s, true));
-    AR_TRY(alloc_operand(ts.T, m, m, BN, s, true));
-    const size_t mm = (size_t)m * m;
     if (bc != AR_BC_ANTIREFLECTIVE) {
+        AR_TRY(alloc_operand(ts.Tt, m, m, BN, s, true));
+        AR_TRY(alloc_operand(ts.T, m, m, BN, s, true));
+        const size_t mm = (size_t)m * m;
         if (bc == AR_BC_PERIODIC) AR_TRY(alloc_operand(ts.Tp, m, m, BN, s, true));
         fill_bc_transforms_kernel<<<(unsigned)((mm + 255) / 256), 256, 0, s>>>(
             m, ts.Tt.ld, bc, ts.Tt.planes, ts.T.planes, ts.Tp.planes);
@@ -620,6 +835,12 @@ ar_status build_transforms(int m, int bc, TransformSet& ts, cudaStream_t s) {
         AR_CUDA(cudaStreamSynchronize(s));
         return AR_OK;
     }
+    const FoldDims f = fold_dims(m);
+    const int Nf = 2 * f.Hs, Kf = 2 * f.Kh;
+    AR_TRY(alloc_operand(ts.Ttp, Nf, m, BN, s, true));
+    AR_TRY(alloc_operand(ts.Ttf, Nf, Kf, BN, s, true));
+    AR_TRY(alloc_operand(ts.Tsf, Nf, Nf, BN, s, true));
+    AR_TRY(alloc_operand(ts.Tsp, m, Nf, BN, s, true));
     double* tmp = nullptr;
     const int ntab = 2 * (m - 1);
     AR_CUDA(cudaMallocAsync((void**)&tmp, (2 * (size_t)m + ntab) * sizeof(double), s));
@@ -632,11 +853,15 @@ ar_status build_transforms(int m, int bc, TransformSet& ts, cudaStream_t s) {
         count_launch();
         AR_CUDA(cudaGetLastError());
     }
-    fill_transforms_kernel<<<(unsigned)((mm + 255) / 256), 256, 0, s>>>(m, ts.Tt.ld, tab, tmp,
-                                                                       tmp + m, ts.Tt.planes,
-                                                                       ts.T.planes);
-    count_launch();
-    AR_CUDA(cudaGetLastError());
+    const Operand* mats[4] = {&ts.Ttp, &ts.Ttf, &ts.Tsf, &ts.Tsp};
+    for (int w = 0; w < 4; ++w) {
+        const Operand& o = *mats[w];
+        const size_t n = (size_t)o.rows * o.K;
+        fill_folded_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m, w, o.rows, o.K, o.ld, tab,
+                                                                      tmp, tmp + m, o.planes);
+        count_launch();
+        AR_CUDA(cudaGetLastError());
+    }
     AR_CUDA(cudaFreeAsync(tmp, s));
     AR_CUDA(cudaStreamSynchronize(s));
     return AR_OK;
@@ -676,13 +901,15 @@ ar_status contract_np(const Operand& A, const Operand& B, const Operand* O, cons
                                     (int)TcMode<NP>::SMEM_BYTES);
     });
     if (attr != cudaSuccess) return cuda_fail(attr, "tc_contract_kernel smem attribute");
-    dim3 grid((A.rows + BM - 1) / BM, (B.rows + BN - 1) / BN, SPLITK);
+    const int mtiles = ep.pair ? (ep.npair + BM / 2 - 1) / (BM / 2) : (A.rows + BM - 1) / BM;
+    dim3 grid(mtiles, (B.rows + BN - 1) / BN, SPLITK);
     ProfScope prof(AR_PROF_CONTRACTION, s);
     const int mi = mode_index(NP);
     count_launch();
+    const CUtensorMap& omap = !O ? A.map[mi] : (ep.pair == PAIR_MIRROR ? O->omapf[mi] : O->omap[mi]);
     AR_CUDA(launch_pdl(tc_contract_kernel<NP>, grid, dim3(NTHREADS), (size_t)TcMode<NP>::SMEM_BYTES,
-                       s, A.map[mi], B.map[mi], O ? O->omap[mi] : A.map[mi], A.rows, B.rows, A.K,
-                       ep, err));
+                       s, A.map[mi], ep.pair ? A.map64[mi] : A.map[mi], B.map[mi], omap, A.rows,
+                       B.rows, A.K, ep, err));
     return AR_OK;
 }
 
@@ -698,11 +925,15 @@ struct TransformPlan {
     int n1, n2;
     int bc;
     int np;                    // bf16 planes per operand: 3 (float32-grade) or 2 (fast)
+    bool folded;               // AR: the even/odd folded chain
     Operand Tt1, T1, Tt2, T2;  // constant operands (B side), owned by the process-wide cache
     Operand Tp1, Tp2;          // Periodic: flipped synthesis operands (cache-owned)
-    Operand P;                 // n1 x n2 images: Y, then W          (A side)
+    Operand Ttp2, Ttf1, Tsf2, Tsp1;   // AR folded: G1 .. G4 constant operands (cache-owned)
+    Operand P;                 // n1 x n2 images: Y (all BCs), then W (Reflective, Periodic)
     Operand P2;                // Periodic: n1 x n2, the odd-part filtered spectrum
-    Operand Qo;                // n2 x n1 images: U^T, then V^T      (A side)
+    Operand Qo;                // n2 x n1 images: U^T, then V^T (Reflective, Periodic)
+    Operand U, W, V;           // AR folded intermediates (see transform_apply)
+    float* dfold = nullptr;    // AR folded: the filter in folded spectral order
     int* err = nullptr;
 };
 
@@ -714,6 +945,7 @@ ar_status transform_plan_create(int n1, int n2, int bc, int precision, cudaStrea
     p->n2 = n2;
     p->bc = bc;
     p->np = precision == AR_PRECISION_BF16X2 ? 2 : 3;
+    p->folded = bc == AR_BC_ANTIREFLECTIVE;
     TransformSet t1, t2;
     ar_status st = cached_transforms(n1, bc, s, &t1);
     if (st == AR_OK) st = cached_transforms(n2, bc, s, &t2);
@@ -724,10 +956,29 @@ ar_status transform_plan_create(int n1, int n2, int bc, int precision, cudaStrea
         p->Tt2 = t2.Tt;
         p->T2 = t2.T;
         p->Tp2 = t2.Tp;
+        p->Ttf1 = t1.Ttf;
+        p->Tsp1 = t1.Tsp;
+        p->Ttp2 = t2.Ttp;
+        p->Tsf2 = t2.Tsf;
     }
-    if (st == AR_OK) st = alloc_operand(p->P, n1, n2, BM, s, false, p->np);
-    if (st == AR_OK && bc == AR_BC_PERIODIC) st = alloc_operand(p->P2, n1, n2, BM, s, false, p->np);
-    if (st == AR_OK) st = alloc_operand(p->Qo, n2, n1, BM, s, false, p->np);
+    if (p->folded) {
+        const FoldDims f1 = fold_dims(n1), f2 = fold_dims(n2);
+        const int N1 = 2 * f1.Hs, N2 = 2 * f2.Hs, K1 = 2 * f1.Kh;
+        // Y: n1 x n2 (paired row loads in G1); U: N2 x K1 (folded output of G1);
+        // W: N1 x N2; V: N2 x N1 (folded output of G3, paired row loads in G4)
+        if (st == AR_OK) st = alloc_operand(p->P, n1, n2, BM, s, false, p->np, OM_PAIR_A);
+        if (st == AR_OK) st = alloc_operand(p->U, N2, K1, BM, s, false, p->np, OM_FOLD_OUT);
+        if (st == AR_OK) st = alloc_operand(p->W, N1, N2, BM, s, false, p->np);
+        if (st == AR_OK) st = alloc_operand(p->V, N2, N1, BM, s, false, p->np, OM_PAIR_A);
+        if (st == AR_OK &&
+            cudaMallocAsync((void**)&p->dfold, (size_t)N1 * N2 * sizeof(float), s) != cudaSuccess)
+            st = fail(AR_ERR_ALLOC, "folded filter");
+    } else {
+        if (st == AR_OK) st = alloc_operand(p->P, n1, n2, BM, s, false, p->np);
+        if (st == AR_OK && bc == AR_BC_PERIODIC)
+            st = alloc_operand(p->P2, n1, n2, BM, s, false, p->np);
+        if (st == AR_OK) st = alloc_operand(p->Qo, n2, n1, BM, s, false, p->np);
+    }
     if (st == AR_OK && cudaMallocAsync((void**)&p->err, sizeof(int), s) != cudaSuccess)
         st = fail(AR_ERR_ALLOC, "transform error flag");
     if (st == AR_OK && cudaMemsetAsync(p->err, 0, sizeof(int), s) != cudaSuccess)
@@ -740,19 +991,36 @@ ar_status transform_plan_create(int n1, int n2, int bc, int precision, cudaStrea
     return AR_OK;
 }
 
+ar_status transform_set_filter(TransformPlan* p, const float* d32, cudaStream_t s) {
+    if (!p->folded) return AR_OK;
+    const FoldDims f1 = fold_dims(p->n1), f2 = fold_dims(p->n2);
+    const size_t n = (size_t)(2 * f1.Hs) * (2 * f2.Hs);
+    fold_filter_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d32, p->n1, p->n2, p->dfold);
+    count_launch();
+    AR_CUDA(cudaGetLastError());
+    return AR_OK;
+}
+
+static void plan_buffers(TransformPlan* p, void* (&q)[8]) {
+    void* v[8] = {p->P.planes, p->P2.planes, p->Qo.planes, p->U.planes, p->W.planes,
+                  p->V.planes, p->dfold, p->err};
+    for (int i = 0; i < 8; ++i) q[i] = v[i];
+}
+
 void transform_plan_destroy(TransformPlan* p) {
     if (!p) return;
-    cudaFree(p->P.planes);
-    cudaFree(p->P2.planes);
-    cudaFree(p->Qo.planes);
-    cudaFree(p->err);
+    void* q[8];
+    plan_buffers(p, q);
+    for (void* x : q) cudaFree(x);
     delete p;
 }
 
 void transform_plan_release(TransformPlan* p, cudaStream_t s) {
     if (!p) return;
-    for (void* q : {(void*)p->P.planes, (void*)p->P2.planes, (void*)p->Qo.planes, (void*)p->err})
-        if (q) cudaFreeAsync(q, s);
+    void* q[8];
+    plan_buffers(p, q);
+    for (void* x : q)
+        if (x) cudaFreeAsync(x, s);
     delete p;
 }
 
@@ -790,6 +1058,56 @@ ar_status transform_apply(TransformPlan* p, const float* d32, const float* d32_o
                                                                        p->P.planes, p->P.pstride);
         count_launch();
         AR_CUDA(cudaGetLastError());
+    }
+    if (p->folded) {
+        // G1: U = fold_1((Y Ttp2^T)^T)   A = Y rows paired (i, n1-1-i), output K-folded
+        // G2: W = d o (U Ttf1^T)^T       block diagonal in K
+        // G3: V = (W Tsf2^T)^T           block diagonal in K, output rows folded along axis 2
+        // G4: out (+)= unfold_2((V Tsp1^T)^T)   A = V rows paired (j, h + j)
+        const FoldDims f1 = fold_dims(n1), f2 = fold_dims(n2);
+        TcEpiArgs e{};
+        e.mode = TE_SPLIT_T;
+        e.planes = p->U.planes;
+        e.pstride = p->U.pstride;
+        e.ld = p->U.ld;
+        e.pair = PAIR_MIRROR;
+        e.mrows = n1;
+        e.npair = f1.h;
+        e.nminus = f1.ha;
+        e.kout = f1.Kh;
+        AR_TRY(contract(p->np, p->P, p->Ttp2, &p->U, e, p->err, s));
+        TcEpiArgs e2{};
+        e2.mode = TE_SCALE_SPLIT_T;
+        e2.planes = p->W.planes;
+        e2.pstride = p->W.pstride;
+        e2.ld = p->W.ld;
+        e2.d = p->dfold;
+        e2.ldd = 2 * f2.Hs;
+        e2.kdiag = 1;
+        AR_TRY(contract(p->np, p->U, p->Ttf1, &p->W, e2, p->err, s));
+        TcEpiArgs e3{};
+        e3.mode = TE_SPLIT_T;
+        e3.planes = p->V.planes;
+        e3.pstride = p->V.pstride;
+        e3.ld = p->V.ld;
+        e3.kdiag = 1;
+        AR_TRY(contract(p->np, p->W, p->Tsf2, &p->V, e3, p->err, s));
+        TcEpiArgs e4{};
+        e4.mode = dout == DOUT_STORE ? TE_STORE_T : TE_AXPY_T;
+        e4.out = out;
+        e4.ldo = n2;
+        e4.tau = tau;
+        if (dout == DOUT_AXPY) {
+            e4.f = f;
+            e4.sumsq = f ? sumsq : nullptr;
+        }
+        e4.pair = PAIR_HALVES;
+        e4.mhalf = f2.Hs;
+        e4.npair = f2.h;
+        e4.nminus = f2.ha;
+        e4.nout = n2;
+        AR_TRY(contract(p->np, p->V, p->Tsp1, nullptr, e4, p->err, s));
+        return AR_OK;
     }
     TcEpiArgs e{};
     // G1: U^T = (Y T~2^T)^T  -> Q planes
