@@ -300,8 +300,10 @@ def kernel_rooflines(ar, torch, dev, step):
     prof = ar.ar_profile_end()
     k1, k2 = ar_psf_shape()
     stencil_flops = 2.0 * k1 * k2 * N1 * N2                 # per launch
-    # per launch: C = A B^T with M = N = K = 1024, six bf16 products (bf16x3 split)
-    contraction_flops = 6 * 2.0 * N1 * N2 * N1
+    # per iteration, six bf16 products (bf16x3 split) of: G1 (M = n1, N = K = n2) and G4
+    # (M = n2, N = n1, K = n1) dense; G2, G3 block diagonal (the even/odd fold): half of
+    # n^3 each.  Averaged over the four launches: 3/4 of 6 x 2 x n^3 at n = 1024.
+    contraction_flops = 6 * 2.0 * N1 * N2 * N1 * 0.75
     kernels = {}
     for kind, (ms, cnt) in prof.items():
         if cnt:
@@ -319,7 +321,8 @@ def kernel_rooflines(ar, torch, dev, step):
                 "bound": "tensor", "achieved": round(ach, 2), "peak": bf16, "unit": "TFLOP/s",
                 "frac": round(ach / bf16, 4), "traffic": measured_traffic("contraction"),
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; kernel timed alone)",
-                "work_per_launch": "6 x 2 x 1024^3 bf16 flops"}
+                "work_per_launch": "6 x 2 x 1024^3 x 3/4 bf16 flops (mean of G1, G4 dense and "
+                                   "G2, G3 block diagonal)"}
     else:
         ach = stencil_flops / t_st / 1e12
         roof = {"kernel": "conv_tma_kernel<7> (AR pad + 15x15 convolution)", "bound": "alu",
