@@ -207,7 +207,10 @@ ar_status prec_build(const double* psf_host, int q1, int q2, int n1, int n2, dou
         if (st == AR_OK)
             st = setup_eigen(h64, q1, q2, n1, n2, alpha, bc, P->lam64, P->d64, P->d32, P->d32_odd,
                              work, s, delta);
-        if (st == AR_OK) st = transform_plan_create(n1, n2, bc, precision, s, &P->plan);
+        // the reblur stencil writes the transform input folded (q <= 15, TMA path)
+        if (st == AR_OK)
+            st = transform_plan_create(n1, n2, bc, precision, s, &P->plan,
+                                       (q1 > q2 ? q1 : q2) <= 15);
         if (st == AR_OK) st = transform_set_filter(P->plan, P->d32, s);
     }
     if (st != AR_OK) {
@@ -291,7 +294,8 @@ static ar_status restore_run(const float* g, const double* psf_host, int n1, int
             // A' r is written straight into the transform's bf16x3 operand planes
             reblur.out = nullptr;
             reblur.mode = CONV_SPLIT3;
-            reblur.planes = transform_input_planes(PP->plan, &reblur.plane_stride, &reblur.ld);
+            reblur.planes = transform_input_planes(PP->plan, &reblur.plane_stride, &reblur.ld,
+                                                   &reblur.fold);
         } else {
             reblur.out = x_out;
             reblur.mode = CONV_AXPY;

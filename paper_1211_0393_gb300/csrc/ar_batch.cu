@@ -79,7 +79,8 @@ ar_status enqueue_image(ar_batch* B, int j, cudaStream_t s, double tau) {
     if (pc) {
         reblur.out = nullptr;
         reblur.mode = CONV_SPLIT3;
-        reblur.planes = transform_input_planes(B->precs[j]->plan, &reblur.plane_stride, &reblur.ld);
+        reblur.planes = transform_input_planes(B->precs[j]->plan, &reblur.plane_stride, &reblur.ld,
+                                               &reblur.fold);
     } else {
         reblur.out = it.x_out;
         reblur.mode = CONV_AXPY;

@@ -209,11 +209,9 @@ __device__ void fixup_tile(const ConvArgs& a, float* tile, int WP, int r0, int c
 // Each thread computes a vertical strip of RS outputs of one column from the
 // halo tile (row pitch WP) and applies the epilogue.
 template <int Q>
-__device__ __forceinline__ void compute_tile(const ConvArgs& a, const float* tile, int WP,
-                                             const float* coef, int r0, int c0) {
+__device__ __forceinline__ void tile_acc(const float* tile, int WP, const float* coef, int tx,
+                                         int ty, float (&acc)[RS]) {
     constexpr int K = 2 * Q + 1;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    float acc[RS];
 #pragma unroll
     for (int r = 0; r < RS; ++r) acc[r] = 0.f;
 
@@ -242,7 +240,14 @@ __device__ __forceinline__ void compute_tile(const ConvArgs& a, const float* til
             for (int r = 0; r < RS; ++r) acc[r] = fmaf(hv, win[r + 2 * Q - aa], acc[r]);
         }
     }
+}
 
+template <int Q>
+__device__ __forceinline__ void compute_tile(const ConvArgs& a, const float* tile, int WP,
+                                             const float* coef, int r0, int c0) {
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    float acc[RS];
+    tile_acc<Q>(tile, WP, coef, tx, ty, acc);
     const int col = c0 + tx;
     float sq = 0.f;
     if (col < a.n2) {
@@ -397,6 +402,107 @@ conv_tma_kernel(const __grid_constant__ CUtensorMap tmx, const ConvArgs a, int n
     }
 }
 
+// Folding reblur (CONV_SPLIT3 with fold, AR and Reflective, TMA path): each
+// work unit is a tile at columns [c0, c0 + 64) and its mirror at
+// [n2 - c0 - 64, n2 - c0), computed side by side by the two 256-thread halves
+// of the CTA.  Column c0 + j of the first pairs with column n2 - 1 - c0 - j,
+// which is column 63 - j of the mirror tile; the halves swap their results
+// through their (consumed) halo boxes and write the bf16x3 split of y+ (first
+// half) and y- (second half) for t = c0 + j, zeros past ceil(n2/2) resp.
+// floor(n2/2).
+template <int Q>
+struct FoldTile {
+    static_assert(TmaTile<Q>::BYTES >= (uint32_t)TH * TX * 4, "a box holds a tile of results");
+    static constexpr size_t SMEM = 2 * TmaTile<Q>::NBUF * (size_t)TmaTile<Q>::BUF +
+                                   (size_t)Coefs<Q>::COUNT * 4 + 8 * TmaTile<Q>::NBUF + 128;
+};
+
+template <int Q>
+__global__ void __launch_bounds__(2 * TX * TY)
+conv_tma_fold_kernel(const __grid_constant__ CUtensorMap tmx, const ConvArgs a, int ncp,
+                     int nunits) {
+    using namespace tc;
+    using T = TmaTile<Q>;
+    constexpr int WB = T::WB, NBUF = T::NBUF;
+    extern __shared__ __align__(128) uint8_t smem_raw_c[];
+    uint8_t* sbase = smem_raw_c + ((128u - (smem_u32(smem_raw_c) & 127u)) & 127u);
+    float* coef = reinterpret_cast<float*>(sbase + 2 * NBUF * T::BUF);
+    const uint32_t bar0 = smem_u32(coef + Coefs<Q>::COUNT);
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    const int grp = threadIdx.y / TY, gty = threadIdx.y % TY, gtid = tid % (TX * TY);
+    const int h = (a.n2 + 1) / 2, ha = a.n2 / 2, kh = (h + 63) / 64 * 64;
+    // box of buffer i, half g
+    auto buffer = [&](int i, int g) {
+        return reinterpret_cast<float*>(sbase + (2 * i + g) * T::BUF);
+    };
+
+    if (tid == 0) {
+        for (int i = 0; i < NBUF; ++i) mbar_init(bar0 + 8u * i, 1);
+        fence_mbar_init();
+        prefetch_tmap(&tmx);
+    }
+    load_coefs<Q>(a, coef, tid, 2 * TX * TY);
+    __syncthreads();
+    pdl_wait();
+
+    auto request = [&](int i) {
+        const int u = blockIdx.x + i * gridDim.x;
+        const int r0 = (u / ncp) * TH, c0 = (u % ncp) * TX, cm = a.n2 - c0 - TX;
+        const uint32_t bar = bar0 + 8u * (i % NBUF);
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar, 2 * T::BYTES);
+        tma_load_2d(smem_u32(buffer(i % NBUF, 0)), &tmx, c0 - T::PADL, r0 - Q, bar);
+        tma_load_2d(smem_u32(buffer(i % NBUF, 1)), &tmx, cm - T::PADL, r0 - Q, bar);
+    };
+    const int nmine = blockIdx.x < nunits ? (nunits - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    if (tid == 0)
+        for (int i = 0; i < NBUF - 1 && i < nmine; ++i) request(i);
+    int li = 0;
+    bool failed = false;
+    for (; li < nmine; ++li) {
+        if (tid == 0 && li + NBUF - 1 < nmine) request(li + NBUF - 1);
+        const bool ok = mbar_wait(bar0 + 8u * (li % NBUF), (li / NBUF) & 1);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        const int u = blockIdx.x + li * gridDim.x;
+        const int r0 = (u / ncp) * TH, c0 = (u % ncp) * TX;
+        const int cg = grp == 0 ? c0 : a.n2 - c0 - TX;
+        float* tile = buffer(li % NBUF, grp) + (T::PADL - Q);
+        // a tile and its mirror reach past the same image borders, so both
+        // halves take the same barriers inside the fix-up
+        if (r0 - Q < 0 || r0 + TH + Q > a.n1 || c0 - Q < 0 || c0 + TX + Q > a.n2)
+            fixup_tile<Q>(a, tile, WB, r0, cg, gtid, TX * TY);
+        if (li == nmine - 1) pdl_trigger();
+        float acc[RS];
+        tile_acc<Q>(tile, WB, coef, threadIdx.x, gty, acc);
+        __syncthreads();                 // both boxes consumed: they take the results
+        float* mine = buffer(li % NBUF, grp);
+#pragma unroll
+        for (int r = 0; r < RS; ++r) mine[(gty * RS + r) * TX + threadIdx.x] = acc[r];
+        __syncthreads();
+        const float* other = buffer(li % NBUF, 1 - grp);
+        const int t = grp == 0 ? c0 + threadIdx.x : c0 + TX - 1 - threadIdx.x;
+        const bool tv = grp == 0 ? t < h : t < ha;
+        const int ocol = grp == 0 ? t : kh + t;
+#pragma unroll
+        for (int r = 0; r < RS; ++r) {
+            const int rr = gty * RS + r, row = r0 + rr;
+            if (row >= a.n1 || t >= kh) continue;
+            const float partner = other[rr * TX + (TX - 1 - threadIdx.x)];
+            const float v = tv ? (grp == 0 ? acc[r] + partner : partner - acc[r]) : 0.f;
+            split3_store(a.planes, a.plane_stride, (size_t)row * a.ld + ocol, v);
+        }
+        __syncthreads();                 // the boxes are refilled for unit li + NBUF
+    }
+    if (failed && tid == 0) {
+        atomicExch(&g_conv_timeout, 1);
+        for (int i = li + 1; i < li + NBUF && i < nmine; ++i)
+            mbar_wait(bar0 + 8u * (i % NBUF), (i / NBUF) & 1);
+    }
+}
+
 // Generic path for large supports: one output per thread, taps read straight
 // from the (L2-resident) input through the virtual extension.
 __global__ void __launch_bounds__(256)
@@ -436,7 +542,40 @@ bool make_image_map(const ConvArgs& a, CUtensorMap* map) {
 }
 
 template <int Q>
+cudaError_t launch_fold(const ConvArgs& a, cudaStream_t s) {
+    using F = FoldTile<Q>;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    static int per_sm = 1;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(conv_tma_fold_kernel<Q>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::SMEM);
+        if (attr == cudaSuccess)
+            attr = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_tma_fold_kernel<Q>,
+                                                                 2 * TX * TY, F::SMEM);
+        if (per_sm < 1) per_sm = 1;
+    });
+    if (attr != cudaSuccess) return attr;
+    CUtensorMap map;
+    if (!make_image_map<Q>(a, &map)) return cudaErrorInvalidValue;
+    const int h = (a.n2 + 1) / 2;
+    const int ncp = (h + TX - 1) / TX, nty = (a.n1 + TH - 1) / TH;
+    const int nunits = ncp * nty;
+    const int cap = sm_count() * per_sm;
+    const int grid = nunits < cap ? nunits : cap;
+    count_launch();
+    conv_tma_fold_kernel<Q><<<dim3(grid), dim3(TX, 2 * TY), F::SMEM, s>>>(map, a, ncp, nunits);
+    return cudaGetLastError();
+}
+
+template <int Q>
 cudaError_t launch_fast(const ConvArgs& a, cudaStream_t s) {
+    if (a.fold) {
+        if (a.mode != CONV_SPLIT3 || a.bc == AR_BC_PERIODIC ||
+            (reinterpret_cast<uintptr_t>(a.x) & 15) != 0 || (a.n2 & 3) != 0)
+            return cudaErrorInvalidValue;            // callers request the fold only where it runs
+        return launch_fold<Q>(a, s);
+    }
     // TMA path: AR / Reflective, 16-byte aligned image and row pitch
     if (a.bc != AR_BC_PERIODIC && (reinterpret_cast<uintptr_t>(a.x) & 15) == 0 &&
         (a.n2 & 3) == 0) {
@@ -488,6 +627,7 @@ ar_status conv_launch(const ConvArgs& a, cudaStream_t s) {
     if (a.n1 <= 0 || a.n2 <= 0) return AR_OK;
     ProfScope prof(AR_PROF_STENCIL, s);
     const int q = a.q1 > a.q2 ? a.q1 : a.q2;
+    if (a.fold && q > QMAX_FAST) return fail(AR_ERR_UNSUPPORTED, "folded output needs q <= 15");
     cudaError_t e;
     switch (q) {
         case 0: e = launch_fast<0>(a, s); break;

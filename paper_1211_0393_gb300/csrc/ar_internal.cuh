@@ -79,6 +79,9 @@ struct ConvArgs {
     const float* f;      // CONV_AXPY: true image or null
     double* sumsq;       // CONV_AXPY with f: += sum (x_new - f)^2 (float64)
     int bc;              // AR_BC_ANTIREFLECTIVE / AR_BC_REFLECTIVE / AR_BC_PERIODIC
+    int fold;            // CONV_SPLIT3: write the even/odd fold along the columns,
+                         // y+_t = y_t + y_{n2-1-t} at column t and y-_t at column
+                         // Kh + t (Kh = ceil(n2/2) rounded up to 64); needs the TMA path
 };
 
 // Launches the AR stencil on `stream` (validated arguments).
@@ -99,8 +102,10 @@ struct TransformPlan;
 
 // precision: AR_PRECISION_FP32 (three bf16 planes, six products) or
 // AR_PRECISION_BF16X2 (two planes, three products); bc: an ar_bc value.
+// fold_input: the stencil producing the DIN_SPLIT input can write it folded
+// along the columns (AR plans then take it so when n2 is a multiple of 4).
 ar_status transform_plan_create(int n1, int n2, int bc, int precision, cudaStream_t stream,
-                                TransformPlan** out);
+                                TransformPlan** out, bool fold_input = false);
 void transform_plan_destroy(TransformPlan* p);
 // Frees the plan's buffers in the order of stream s (after its pending work).
 void transform_plan_release(TransformPlan* p, cudaStream_t s);
@@ -122,8 +127,10 @@ enum DOutput : int {
 // every change of d); other plans read d32 as given to transform_apply.
 ar_status transform_set_filter(TransformPlan* p, const float* d32, cudaStream_t stream);
 
-// Pointer to the operand planes the stencil must fill for DIN_SPLIT.
-uint16_t* transform_input_planes(TransformPlan* p, size_t* plane_stride, int* ld);
+// Pointer to the operand planes the stencil must fill for DIN_SPLIT; *folded
+// (may be null) tells whether they take the column-folded form (ConvArgs::fold).
+uint16_t* transform_input_planes(TransformPlan* p, size_t* plane_stride, int* ld,
+                                 int* folded = nullptr);
 
 // d32 is the filter in the transform domain; for Periodic it is the part of d
 // even in each frequency and d32_odd minus the part odd in both (null for the

@@ -710,6 +710,29 @@ __global__ void fold_filter_kernel(const float* __restrict__ d, int n1, int n2,
     df[idx] = ok ? d[(size_t)s1 * n2 + s2] : 0.f;
 }
 
+// float32 image -> bf16x3 planes of its fold along the columns: y+ at column
+// t < ceil(n2/2), y- at Kh + t (t < floor(n2/2)), zeros in the padding.
+__global__ void split_fold_kernel(const float* __restrict__ y, int n1, int n2, int ld,
+                                  uint16_t* planes, size_t pstride) {
+    const FoldDims f = fold_dims(n2);
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)n1 * f.Kh) return;
+    const int i = (int)(idx / f.Kh), t = (int)(idx % f.Kh);
+    const float* row = y + (size_t)i * n2;
+    const float a = t < n2 ? __ldg(row + t) : 0.f;
+    const float b = t < n2 ? __ldg(row + n2 - 1 - t) : 0.f;
+    uint16_t h0, h1, h2;
+    const size_t o = (size_t)i * ld + t;
+    split3(t < f.h ? a + b : 0.f, h0, h1, h2);
+    planes[o] = h0;
+    planes[pstride + o] = h1;
+    planes[2 * pstride + o] = h2;
+    split3(t < f.ha ? a - b : 0.f, h0, h1, h2);
+    planes[o + f.Kh] = h0;
+    planes[pstride + o + f.Kh] = h1;
+    planes[2 * pstride + o + f.Kh] = h2;
+}
+
 // float32 image -> bf16x3 planes (row pitch ld).
 __global__ void split_image_kernel(const float* __restrict__ y, int n1, int n2, int ld,
                                    uint16_t* planes, size_t pstride) {
@@ -926,9 +949,11 @@ struct TransformPlan {
     int bc;
     int np;                    // bf16 planes per operand: 3 (float32-grade) or 2 (fast)
     bool folded;               // AR: the even/odd folded chain
+    bool fold_y;               // AR: Y arrives folded along the columns (G1 block diagonal)
     Operand Tt1, T1, Tt2, T2;  // constant operands (B side), owned by the process-wide cache
     Operand Tp1, Tp2;          // Periodic: flipped synthesis operands (cache-owned)
     Operand Ttp2, Ttf1, Tsf2, Tsp1;   // AR folded: G1 .. G4 constant operands (cache-owned)
+    Operand Ttf2;              // AR folded, Y folded: G1's block-diagonal operand
     Operand P;                 // n1 x n2 images: Y (all BCs), then W (Reflective, Periodic)
     Operand P2;                // Periodic: n1 x n2, the odd-part filtered spectrum
     Operand Qo;                // n2 x n1 images: U^T, then V^T (Reflective, Periodic)
@@ -938,7 +963,7 @@ struct TransformPlan {
 };
 
 ar_status transform_plan_create(int n1, int n2, int bc, int precision, cudaStream_t s,
-                                TransformPlan** out) {
+                                TransformPlan** out, bool fold_input) {
     TransformPlan* p = new (std::nothrow) TransformPlan();
     if (!p) return fail(AR_ERR_ALLOC, "host allocation of the transform plan");
     p->n1 = n1;
@@ -946,6 +971,7 @@ ar_status transform_plan_create(int n1, int n2, int bc, int precision, cudaStrea
     p->bc = bc;
     p->np = precision == AR_PRECISION_BF16X2 ? 2 : 3;
     p->folded = bc == AR_BC_ANTIREFLECTIVE;
+    p->fold_y = p->folded && fold_input && (n2 % 4) == 0;
     TransformSet t1, t2;
     ar_status st = cached_transforms(n1, bc, s, &t1);
     if (st == AR_OK) st = cached_transforms(n2, bc, s, &t2);
@@ -959,14 +985,17 @@ ar_status transform_plan_create(int n1, int n2, int bc, int precision, cudaStrea
         p->Ttf1 = t1.Ttf;
         p->Tsp1 = t1.Tsp;
         p->Ttp2 = t2.Ttp;
+        p->Ttf2 = t2.Ttf;
         p->Tsf2 = t2.Tsf;
     }
     if (p->folded) {
         const FoldDims f1 = fold_dims(n1), f2 = fold_dims(n2);
         const int N1 = 2 * f1.Hs, N2 = 2 * f2.Hs, K1 = 2 * f1.Kh;
-        // Y: n1 x n2 (paired row loads in G1); U: N2 x K1 (folded output of G1);
-        // W: N1 x N2; V: N2 x N1 (folded output of G3, paired row loads in G4)
-        if (st == AR_OK) st = alloc_operand(p->P, n1, n2, BM, s, false, p->np, OM_PAIR_A);
+        // Y: n1 x n2, or n1 x 2 Kh2 folded along the columns (paired row loads in
+        // G1); U: N2 x K1 (folded output of G1); W: N1 x N2; V: N2 x N1 (folded
+        // output of G3, paired row loads in G4)
+        if (st == AR_OK)
+            st = alloc_operand(p->P, n1, p->fold_y ? 2 * f2.Kh : n2, BM, s, false, p->np, OM_PAIR_A);
         if (st == AR_OK) st = alloc_operand(p->U, N2, K1, BM, s, false, p->np, OM_FOLD_OUT);
         if (st == AR_OK) st = alloc_operand(p->W, N1, N2, BM, s, false, p->np);
         if (st == AR_OK) st = alloc_operand(p->V, N2, N1, BM, s, false, p->np, OM_PAIR_A);
@@ -1024,9 +1053,10 @@ void transform_plan_release(TransformPlan* p, cudaStream_t s) {
     delete p;
 }
 
-uint16_t* transform_input_planes(TransformPlan* p, size_t* plane_stride, int* ld) {
+uint16_t* transform_input_planes(TransformPlan* p, size_t* plane_stride, int* ld, int* folded) {
     if (plane_stride) *plane_stride = p->P.pstride;
     if (ld) *ld = p->P.ld;
+    if (folded) *folded = p->fold_y ? 1 : 0;
     return p->P.planes;
 }
 
@@ -1052,10 +1082,16 @@ ar_status transform_apply(TransformPlan* p, const float* d32, const float* d32_o
     const bool periodic = p->bc == AR_BC_PERIODIC;
     if (periodic && !d32_odd) return fail(AR_ERR_INVALID_ARG, "periodic filter without odd part");
     if (din == DIN_FP32) {
-        const size_t n = (size_t)n1 * n2;
         ProfScope prof(AR_PROF_OTHER, s);
-        split_image_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(y, n1, n2, p->P.ld,
-                                                                       p->P.planes, p->P.pstride);
+        if (p->fold_y) {
+            const size_t n = (size_t)n1 * fold_dims(n2).Kh;
+            split_fold_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(y, n1, n2, p->P.ld,
+                                                                          p->P.planes, p->P.pstride);
+        } else {
+            const size_t n = (size_t)n1 * n2;
+            split_image_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(y, n1, n2, p->P.ld,
+                                                                           p->P.planes, p->P.pstride);
+        }
         count_launch();
         AR_CUDA(cudaGetLastError());
     }
@@ -1075,7 +1111,8 @@ ar_status transform_apply(TransformPlan* p, const float* d32, const float* d32_o
         e.npair = f1.h;
         e.nminus = f1.ha;
         e.kout = f1.Kh;
-        AR_TRY(contract(p->np, p->P, p->Ttp2, &p->U, e, p->err, s));
+        e.kdiag = p->fold_y ? 1 : 0;     // Y folded along the columns: G1 block diagonal too
+        AR_TRY(contract(p->np, p->P, p->fold_y ? p->Ttf2 : p->Ttp2, &p->U, e, p->err, s));
         TcEpiArgs e2{};
         e2.mode = TE_SCALE_SPLIT_T;
         e2.planes = p->W.planes;

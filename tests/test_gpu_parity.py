@@ -245,6 +245,32 @@ def test_restore_matches_oracle(ar, n, psf, scene, cidx, nu, alpha, iters, pc):
         assert to[best - 1] <= to.min() * (1 + 1e-4)
 
 
+FOLD_CASES = [
+    # n1, n2, q1, q2: the reblur writes the transform input folded along the
+    # columns when n2 % 4 == 0 and q <= 15 (AR); the rest keep the plain input
+    (40, 40, 3, 3),        # one column pair whose mirror tile starts left of the image
+    (72, 120, 7, 5),       # rectangular, ragged column pairs
+    (36, 52, 15, 15),      # widest folded halo
+    (44, 48, 16, 2),       # q > 15: plain input, generic stencil
+    (45, 51, 4, 4),        # odd sides: plain input
+    (50, 50, 2, 2),        # n2 % 4 == 2: plain input
+]
+
+
+@pytest.mark.parametrize("n1,n2,q1,q2", FOLD_CASES)
+def test_restore_folded_input_shapes(ar, n1, n2, q1, q2):
+    rng = np.random.default_rng(n1 * 31 + n2 + q1)
+    h = rand_psf(rng, q1, q2)
+    f = rng.uniform(0, 1, (n1, n2))
+    g = (O.ar_blur(f, h) + 0.01 * rng.standard_normal((n1, n2))).astype(np.float32)
+    alpha = 0.05
+    x, tr, _ = ar.ar_restore(dev(g), h, alpha, 1.0, 6, True, f_true=dev(f.astype(np.float32)))
+    xo, to, _ = O.restore(g.astype(np.float64), h, alpha, 1.0, 6, True,
+                          f_true=f.astype(np.float32).astype(np.float64))
+    assert rel_l2(x.cpu().numpy(), xo) <= tol_alpha(alpha)
+    assert_trace_close(tr, to, tol_alpha(alpha))
+
+
 def test_restore_warm_start_and_in_place(ar):
     h = W.psf_config1()
     g, f = _workload(64, h, "blocks", 0, 0.01)
