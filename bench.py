@@ -300,10 +300,11 @@ def kernel_rooflines(ar, torch, dev, step):
     prof = ar.ar_profile_end()
     k1, k2 = ar_psf_shape()
     stencil_flops = 2.0 * k1 * k2 * N1 * N2                 # per launch
-    # per iteration, six bf16 products (bf16x3 split) of: G1 (M = n1, N = K = n2) and G4
-    # (M = n2, N = n1, K = n1) dense; G2, G3 block diagonal (the even/odd fold): half of
-    # n^3 each.  Averaged over the four launches: 3/4 of 6 x 2 x n^3 at n = 1024.
-    contraction_flops = 6 * 2.0 * N1 * N2 * N1 * 0.75
+    # per iteration, six bf16 products (bf16x3 split) of: G1, G2, G3 block diagonal (the
+    # even/odd fold; G1's input arrives folded from the reblur): half of n^3 each; G4
+    # (M = n2, N = n1, K = n1) dense.  Averaged over the four launches: 5/8 of
+    # 6 x 2 x n^3 at n = 1024.
+    contraction_flops = 6 * 2.0 * N1 * N2 * N1 * 0.625
     kernels = {}
     for kind, (ms, cnt) in prof.items():
         if cnt:
@@ -321,11 +322,12 @@ def kernel_rooflines(ar, torch, dev, step):
                 "bound": "tensor", "achieved": round(ach, 2), "peak": bf16, "unit": "TFLOP/s",
                 "frac": round(ach / bf16, 4), "traffic": measured_traffic("contraction"),
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; kernel timed alone)",
-                "work_per_launch": "6 x 2 x 1024^3 x 3/4 bf16 flops (mean of G1, G4 dense and "
-                                   "G2, G3 block diagonal)"}
+                "work_per_launch": "6 x 2 x 1024^3 x 5/8 bf16 flops (mean of G1, G2, G3 block "
+                                   "diagonal and G4 dense)"}
     else:
         ach = stencil_flops / t_st / 1e12
-        roof = {"kernel": "conv_tma_kernel<7> (AR pad + 15x15 convolution)", "bound": "alu",
+        roof = {"kernel": "conv_tma_kernel<7, true> (AR pad + 15x15 convolution, residual)",
+                "bound": "alu",
                 "achieved": round(ach, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
                 "frac": round(ach / fp32_peak, 4), "traffic": measured_traffic("stencil"),
                 "peak_source": "derived: SMs x 128 FP32 lanes x 2 x sm_max_mhz of MEASURED_PEAKS.json",

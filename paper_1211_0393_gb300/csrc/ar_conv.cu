@@ -242,7 +242,56 @@ __device__ __forceinline__ void tile_acc(const float* tile, int WP, const float*
     }
 }
 
-template <int Q>
+// The epilogue of one thread's strip of RS rows at column col, from row row0
+// on, for the modes that read global memory (residual, AXPY): the arithmetic
+// of conv_epilogue, with the loads of EB rows issued before their stores, so
+// that they do not wait on one another.
+template <int EB>
+__device__ __forceinline__ float strip_epilogue(const ConvArgs& a, int row0, int col,
+                                                const float (&acc)[RS]) {
+    const int nr = min(RS, a.n1 - row0);
+    float sq = 0.f;
+#pragma unroll
+    for (int c = 0; c < RS; c += EB) {
+        // a chunk's loads stay after the previous chunk's stores (and after the
+        // tap loop): hoisted, they would hold registers through it
+        asm volatile("" ::: "memory");
+        const size_t o0 = (size_t)(row0 + c) * a.n2 + col;
+        if (a.mode == CONV_RESIDUAL) {
+            float gv[EB];
+#pragma unroll
+            for (int r = 0; r < EB; ++r)
+                gv[r] = c + r < nr ? __ldg(a.aux + o0 + (size_t)r * a.n2) : 0.f;
+#pragma unroll
+            for (int r = 0; r < EB; ++r)
+                if (c + r < nr) a.out[o0 + (size_t)r * a.n2] = gv[r] - acc[c + r];
+        } else {
+            float xv[EB], fv[EB];
+#pragma unroll
+            for (int r = 0; r < EB; ++r) {
+                xv[r] = c + r < nr ? a.out[o0 + (size_t)r * a.n2] : 0.f;
+                fv[r] = c + r < nr && a.f ? __ldg(a.f + o0 + (size_t)r * a.n2) : 0.f;
+            }
+#pragma unroll
+            for (int r = 0; r < EB; ++r) {
+                if (c + r < nr) {
+                    const float xn = fmaf(a.tau, acc[c + r], xv[r]);
+                    a.out[o0 + (size_t)r * a.n2] = xn;
+                    if (a.f) {
+                        const float e = xn - fv[r];
+                        sq += e * e;
+                    }
+                }
+            }
+        }
+    }
+    return sq;
+}
+
+// RW: the mode reads global memory in its epilogue (residual, AXPY); the
+// kernels are instantiated for both kinds, so that the store modes keep their
+// own (smaller) register allocation.
+template <int Q, bool RW>
 __device__ __forceinline__ void compute_tile(const ConvArgs& a, const float* tile, int WP,
                                              const float* coef, int r0, int c0) {
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -250,11 +299,14 @@ __device__ __forceinline__ void compute_tile(const ConvArgs& a, const float* til
     tile_acc<Q>(tile, WP, coef, tx, ty, acc);
     const int col = c0 + tx;
     float sq = 0.f;
-    if (col < a.n2) {
+    if (col < a.n2 && r0 + ty * RS < a.n1) {
+        if (RW) {
+            sq = strip_epilogue<(Q >= 5 ? 8 : 4)>(a, r0 + ty * RS, col, acc);
+        } else {
+            const int row0 = r0 + ty * RS;
 #pragma unroll
-        for (int r = 0; r < RS; ++r) {
-            const int row = r0 + ty * RS + r;
-            if (row < a.n1) sq += conv_epilogue(a, row, col, acc[r]);
+            for (int r = 0; r < RS; ++r)
+                if (row0 + r < a.n1) sq += conv_epilogue(a, row0 + r, col, acc[r]);
         }
     }
     if (a.sumsq) add_sumsq(a.sumsq, sq);
@@ -263,7 +315,7 @@ __device__ __forceinline__ void compute_tile(const ConvArgs& a, const float* til
 // Fast path: support padded to Q x Q (Q = max(q1, q2) <= 15, zero taps outside
 // the true support), tile TH x TX, R = RS rows per thread; the halo tile is
 // loaded by the threads (any row pitch and alignment, every BC).
-template <int Q>
+template <int Q, bool RW>
 __global__ void __launch_bounds__(TX * TY)
 conv_fast_kernel(const ConvArgs a) {
     constexpr int W = TX + 2 * Q;        // tile row length
@@ -315,7 +367,7 @@ conv_fast_kernel(const ConvArgs a) {
         fixup_tile<Q>(a, tile, W, r0, c0, tid, TX * TY);
 
     pdl_trigger();
-    compute_tile<Q>(a, tile, W, coef, r0, c0);
+    compute_tile<Q, RW>(a, tile, W, coef, r0, c0);
 }
 
 __device__ int g_conv_timeout;
@@ -341,7 +393,7 @@ struct TmaTile {
 // of the next NBUF - 1 tiles requested by TMA (zeros outside the image) while
 // the CTA works on the current one.  Out-of-image samples of the extended
 // domain are then filled in shared memory.
-template <int Q>
+template <int Q, bool RW>
 __global__ void __launch_bounds__(TX * TY)
 conv_tma_kernel(const __grid_constant__ CUtensorMap tmx, const ConvArgs a, int ntx, int ntiles) {
     using namespace tc;
@@ -391,7 +443,7 @@ conv_tma_kernel(const __grid_constant__ CUtensorMap tmx, const ConvArgs a, int n
         if (r0 - Q < 0 || r0 + TH + Q > a.n1 || c0 - Q < 0 || c0 + TX + Q > a.n2)
             fixup_tile<Q>(a, tile, WB, r0, c0, tid, TX * TY);
         if (li == nmine - 1) pdl_trigger();
-        compute_tile<Q>(a, tile, WB, coef, r0, c0);
+        compute_tile<Q, RW>(a, tile, WB, coef, r0, c0);
         __syncthreads();                 // the buffer is refilled for tile li + NBUF
     }
     if (failed && tid == 0) {
@@ -568,6 +620,9 @@ cudaError_t launch_fold(const ConvArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <int Q, bool RW>
+cudaError_t launch_tiles(const ConvArgs& a, cudaStream_t s);
+
 template <int Q>
 cudaError_t launch_fast(const ConvArgs& a, cudaStream_t s) {
     if (a.fold) {
@@ -576,6 +631,12 @@ cudaError_t launch_fast(const ConvArgs& a, cudaStream_t s) {
             return cudaErrorInvalidValue;            // callers request the fold only where it runs
         return launch_fold<Q>(a, s);
     }
+    if (a.mode == CONV_RESIDUAL || a.mode == CONV_AXPY) return launch_tiles<Q, true>(a, s);
+    return launch_tiles<Q, false>(a, s);
+}
+
+template <int Q, bool RW>
+cudaError_t launch_tiles(const ConvArgs& a, cudaStream_t s) {
     // TMA path: AR / Reflective, 16-byte aligned image and row pitch
     if (a.bc != AR_BC_PERIODIC && (reinterpret_cast<uintptr_t>(a.x) & 15) == 0 &&
         (a.n2 & 3) == 0) {
@@ -584,10 +645,10 @@ cudaError_t launch_fast(const ConvArgs& a, cudaStream_t s) {
         static cudaError_t attr = cudaSuccess;
         static int per_sm = 1;
         std::call_once(once, [] {
-            attr = cudaFuncSetAttribute(conv_tma_kernel<Q>,
+            attr = cudaFuncSetAttribute(conv_tma_kernel<Q, RW>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
             if (attr == cudaSuccess)
-                attr = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_tma_kernel<Q>,
+                attr = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_tma_kernel<Q, RW>,
                                                                      TX * TY, T::SMEM);
             if (per_sm < 1) per_sm = 1;
         });
@@ -600,13 +661,13 @@ cudaError_t launch_fast(const ConvArgs& a, cudaStream_t s) {
             // plain stream order: launched early (programmatic serialization) the
             // stencil's CTAs cost the iteration more than they save (measured)
             count_launch();
-            conv_tma_kernel<Q><<<dim3(grid), dim3(TX, TY), T::SMEM, s>>>(map, a, ntx, ntiles);
+            conv_tma_kernel<Q, RW><<<dim3(grid), dim3(TX, TY), T::SMEM, s>>>(map, a, ntx, ntiles);
             return cudaGetLastError();
         }
     }
     dim3 grid((a.n2 + TX - 1) / TX, (a.n1 + TH - 1) / TH);
     count_launch();
-    conv_fast_kernel<Q><<<grid, dim3(TX, TY), 0, s>>>(a);
+    conv_fast_kernel<Q, RW><<<grid, dim3(TX, TY), 0, s>>>(a);
     return cudaGetLastError();
 }
 
