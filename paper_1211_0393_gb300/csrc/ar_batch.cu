@@ -86,6 +86,8 @@ ar_status enqueue_image(ar_batch* B, int j, cudaStream_t s, double tau) {
         reblur.mode = CONV_AXPY;
         reblur.tau = (float)tau;
     }
+    // trigger placement as in the restoration loop of ar_restore
+    reblur.early_trigger = pc ? 1 : 0;
     for (int k = 0; k < B->iters; ++k) {
         AR_TRY(conv_launch(blur, s));
         if (!pc) reblur.sumsq = it.f_true ? B->sums[j] + k : nullptr;

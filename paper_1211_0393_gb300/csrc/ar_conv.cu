@@ -442,10 +442,11 @@ conv_tma_kernel(const __grid_constant__ CUtensorMap tmx, const ConvArgs a, int n
         float* tile = buffer(li % NBUF) + (T::PADL - Q);
         if (r0 - Q < 0 || r0 + TH + Q > a.n1 || c0 - Q < 0 || c0 + TX + Q > a.n2)
             fixup_tile<Q>(a, tile, WB, r0, c0, tid, TX * TY);
-        if (li == nmine - 1) pdl_trigger();
+        if (a.early_trigger && li == nmine - 1) pdl_trigger();
         compute_tile<Q, RW>(a, tile, WB, coef, r0, c0);
         __syncthreads();                 // the buffer is refilled for tile li + NBUF
     }
+    if (!a.early_trigger) pdl_trigger();
     if (failed && tid == 0) {
         atomicExch(&g_conv_timeout, 1);
         // copies still in flight (tiles li + 1 .. li + NBUF - 1): wait for them (bounded)
@@ -616,8 +617,8 @@ cudaError_t launch_fold(const ConvArgs& a, cudaStream_t s) {
     const int cap = sm_count() * per_sm;
     const int grid = nunits < cap ? nunits : cap;
     count_launch();
-    conv_tma_fold_kernel<Q><<<dim3(grid), dim3(TX, 2 * TY), F::SMEM, s>>>(map, a, ncp, nunits);
-    return cudaGetLastError();
+    return launch_pdl(conv_tma_fold_kernel<Q>, dim3(grid), dim3(TX, 2 * TY), F::SMEM, s, map, a,
+                      ncp, nunits);
 }
 
 template <int Q, bool RW>
@@ -658,11 +659,13 @@ cudaError_t launch_tiles(const ConvArgs& a, cudaStream_t s) {
             const int ntiles = ntx * nty;
             const int cap = sm_count() * per_sm;
             const int grid = ntiles < cap ? ntiles : cap;
-            // plain stream order: launched early (programmatic serialization) the
-            // stencil's CTAs cost the iteration more than they save (measured)
+            // a programmatic dependent: the CTAs are placed while the predecessor
+            // drains; predecessors that could leave SMs idle for long (the last
+            // contraction, stencils) let it launch only at their end, so that
+            // early CTAs do not pile onto those SMs
             count_launch();
-            conv_tma_kernel<Q, RW><<<dim3(grid), dim3(TX, TY), T::SMEM, s>>>(map, a, ntx, ntiles);
-            return cudaGetLastError();
+            return launch_pdl(conv_tma_kernel<Q, RW>, dim3(grid), dim3(TX, TY), T::SMEM, s, map, a,
+                              ntx, ntiles);
         }
     }
     dim3 grid((a.n2 + TX - 1) / TX, (a.n1 + TH - 1) / TH);

@@ -82,6 +82,10 @@ struct ConvArgs {
     int fold;            // CONV_SPLIT3: write the even/odd fold along the columns,
                          // y+_t = y_t + y_{n2-1-t} at column t and y-_t at column
                          // Kh + t (Kh = ceil(n2/2) rounded up to 64); needs the TMA path
+    int early_trigger;   // the successor cannot crowd the SMs (a contraction, which
+                         // needs a whole SM): let it launch when the last tile
+                         // starts, not after it (TMA path; the TMA stencils launch
+                         // as programmatic dependents)
 };
 
 // Launches the AR stencil on `stream` (validated arguments).

@@ -122,6 +122,10 @@ struct TcEpiArgs {
     int kdiag;
     int pair;
     int mrows, mhalf, npair, nminus, kout, nout;
+    // late_trigger: the successor may launch only once this grid's epilogues are
+    // done (it is a stencil, whose CTAs would otherwise crowd the SMs that this
+    // grid leaves idle); else it may launch as soon as the accumulators are ready
+    int late_trigger;
 };
 
 enum TcPair : int { PAIR_NONE = 0, PAIR_MIRROR = 1, PAIR_HALVES = 2 };
@@ -336,7 +340,7 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     const bool ready = mbar_wait(done_bar, 0);
     __syncwarp();
     fence_after_sync();
-    pdl_trigger();
+    if (!ep.late_trigger) pdl_trigger();
     const bool ok = ready && *sflag == 0;
     const int nacc = ok ? (2 * nk < NACC ? 2 * nk : NACC) : 0;
     const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
@@ -459,6 +463,7 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         }
     }
 
+    if (ep.late_trigger) pdl_trigger();
     fence_before_sync();
     __syncthreads();
     if (warp == 1) {
@@ -1143,6 +1148,7 @@ ar_status transform_apply(TransformPlan* p, const float* d32, const float* d32_o
         e4.npair = f2.h;
         e4.nminus = f2.ha;
         e4.nout = n2;
+        e4.late_trigger = 1;
         AR_TRY(contract(p->np, p->V, p->Tsp1, nullptr, e4, p->err, s));
         return AR_OK;
     }
@@ -1183,6 +1189,7 @@ ar_status transform_apply(TransformPlan* p, const float* d32, const float* d32_o
         e4.f = f;
         e4.sumsq = f ? sumsq : nullptr;
     }
+    e4.late_trigger = periodic ? 0 : 1;
     AR_TRY(contract(p->np, p->Qo, p->T1, nullptr, e4, p->err, s));
     if (periodic) {
         // G3': V'^T = (W' H'2^T)^T -> Q planes;  G4': out += tau (V'^T H'1^T)^T
@@ -1193,6 +1200,7 @@ ar_status transform_apply(TransformPlan* p, const float* d32, const float* d32_o
             e4.f = f;
             e4.sumsq = f ? sumsq : nullptr;
         }
+        e4.late_trigger = 1;
         AR_TRY(contract(p->np, p->Qo, p->Tp1, nullptr, e4, p->err, s));
     }
     return AR_OK;
