@@ -246,6 +246,7 @@ def run_own(args):
                     "d2h_bytes_per_step": int(g.nbytes + 8 * ITERS + 8 * (ITERS + 1))},
             "roofline": roof,
             "kernels": kernels,
+            "iteration_dram": iteration_dram(),
             "gpu_launches": int(launches),
             "clocks": clocks,
             "rre_last_step": {"best_iter": best, "rre_best": float(np.min(trace)),
@@ -343,6 +344,28 @@ PROFILES = {
     "contraction": ("profiles/tc_contract_kernel_ellipses1024.md", "paper_1211_0393_gb300/csrc/ar_transform.cu"),
     "stencil": ("profiles/conv_tma_kernel_q7_ellipses1024.md", "paper_1211_0393_gb300/csrc/ar_conv.cu"),
 }
+
+
+def iteration_dram():
+    """DRAM bytes per pixel of one restoration iteration in the warm loop (ncu, caches
+    not flushed between launches), from the committed summary while both kernel sources
+    are unchanged; against the 32 B/px of a two-pass schedule."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles/iteration_dram_ellipses1024.md")
+    try:
+        fields = dict(line.split(": ", 1) for line in open(prof).read().splitlines()
+                      if line.startswith(("dram_bytes_per_iteration:", "source_sha256_prefix_")))
+        for key, src in (("source_sha256_prefix_conv", PROFILES["stencil"][1]),
+                         ("source_sha256_prefix_transform", PROFILES["contraction"][1])):
+            sha = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()
+            if not sha.startswith(fields[key].strip()):
+                return None
+        b = int(fields["dram_bytes_per_iteration"])
+        return {"bytes_per_iter": b, "bytes_per_px": round(b / (N1 * N2), 2),
+                "two_pass_schedule_bytes_per_px": 32, "floor_bytes_per_px": 16,
+                "source": "profiles/iteration_dram_ellipses1024.md"}
+    except Exception:
+        return None
 
 
 def measured_traffic(kind):
