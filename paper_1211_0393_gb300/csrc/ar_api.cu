@@ -305,6 +305,7 @@ static ar_status restore_run(const float* g, const double* psf_host, int n1, int
         // the blur; the blur's is a stencil (launched early beside the blur, the
         // folding reblur's CTAs ran slower: measured)
         reblur.early_trigger = reblur.mode == CONV_SPLIT3 ? 1 : 0;
+        blur.spread = reblur.spread = 1;
         reblur.f = f_true;
         for (int it = 0; st == AR_OK && it < iters; ++it) {
             // the RRE numerator ||x_{k+1} - f||^2 is accumulated by the kernel that writes x_{k+1}

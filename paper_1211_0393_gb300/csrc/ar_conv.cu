@@ -34,9 +34,19 @@ namespace ar {
 namespace {
 
 constexpr int TX = 64;   // tile columns, one per thread
-constexpr int TY = 4;    // row strips per CTA
-constexpr int RS = 16;   // rows per strip
-constexpr int TH = TY * RS;
+// Tile geometries: TY row strips of RS rows, a TH = TY RS row tile per CTA (per
+// half-CTA in the folding reblur).  G64 (8 warps, 64-row tiles) serves every
+// launch but the single-wave ones that G54 (6 warps, 54-row tiles) balances
+// better (the choice depends on the image size only, so that a batch and a
+// single restoration of the same image give identical results): a 1024-row image splits into 19 tiles of 54 rows, and the 304 tiles
+// of a 1024^2 image give every SM two where 256 tiles of 64 rows give 104 SMs
+// two and 48 SMs one (the folding reblur: 152 units instead of 128).
+template <int TY_, int RS_>
+struct Geo {
+    static constexpr int TY = TY_, RS = RS_, TH = TY_ * RS_;
+};
+using G64 = Geo<4, 16>;
+using G54 = Geo<3, 18>;
 constexpr int QMAX_FAST = 15;
 
 // Index of the sample that an out-of-image index j maps to under the
@@ -111,7 +121,7 @@ __device__ __forceinline__ float conv_epilogue(const ConvArgs& a, int row, int c
 }
 
 // *sumsq += the block's sum of v (one float64 atomic per block).  Each thread's
-// v is a float32 sum of at most RS squares (relative error ~RS 2^-24); the
+// v is a float32 sum of at most RS squares (relative error ~RS 2^-24, RS <= 18); the
 // block reduction is float64.  Called by every thread of the block.
 __device__ __forceinline__ void add_sumsq(double* sumsq, float vf) {
     __shared__ double part[32];
@@ -165,10 +175,10 @@ __device__ __forceinline__ void load_coefs(const ConvArgs& a, float* coef, int t
 // x_{-1-i} = x_i, x_{n+i} = x_{n-1-i}.  Edge and mirror samples lie in the
 // tile.  Only the out-of-image strips (at most q rows or columns per side) are
 // visited.
-template <int Q>
+template <int Q, class G>
 __device__ void fixup_tile(const ConvArgs& a, float* tile, int WP, int r0, int c0, int tid,
                            int nthreads) {
-    constexpr int W = TX + 2 * Q, H = TH + 2 * Q;
+    constexpr int W = TX + 2 * Q, H = G::TH + 2 * Q;
     const bool ar = a.bc == AR_BC_ANTIREFLECTIVE;
     const int rb = r0 - Q, cb = c0 - Q;                 // image coordinates of tile (0, 0)
     // tile rows with j1 in [-q1, 0) and in [n1, n1 + q1), clipped to the tile
@@ -208,10 +218,10 @@ __device__ void fixup_tile(const ConvArgs& a, float* tile, int WP, int r0, int c
 
 // Each thread computes a vertical strip of RS outputs of one column from the
 // halo tile (row pitch WP) and applies the epilogue.
-template <int Q>
+template <int Q, class G>
 __device__ __forceinline__ void tile_acc(const float* tile, int WP, const float* coef, int tx,
-                                         int ty, float (&acc)[RS]) {
-    constexpr int K = 2 * Q + 1;
+                                         int ty, float (&acc)[G::RS]) {
+    constexpr int K = 2 * Q + 1, RS = G::RS;
 #pragma unroll
     for (int r = 0; r < RS; ++r) acc[r] = 0.f;
 
@@ -246,9 +256,11 @@ __device__ __forceinline__ void tile_acc(const float* tile, int WP, const float*
 // on, for the modes that read global memory (residual, AXPY): the arithmetic
 // of conv_epilogue, with the loads of EB rows issued before their stores, so
 // that they do not wait on one another.
-template <int EB>
+template <int EB, class G>
 __device__ __forceinline__ float strip_epilogue(const ConvArgs& a, int row0, int col,
-                                                const float (&acc)[RS]) {
+                                                const float (&acc)[G::RS]) {
+    constexpr int RS = G::RS;
+    static_assert(RS % EB == 0, "chunks tile the strip");
     const int nr = min(RS, a.n1 - row0);
     float sq = 0.f;
 #pragma unroll
@@ -291,17 +303,20 @@ __device__ __forceinline__ float strip_epilogue(const ConvArgs& a, int row0, int
 // RW: the mode reads global memory in its epilogue (residual, AXPY); the
 // kernels are instantiated for both kinds, so that the store modes keep their
 // own (smaller) register allocation.
-template <int Q, bool RW>
+template <int Q, bool RW, class G>
 __device__ __forceinline__ void compute_tile(const ConvArgs& a, const float* tile, int WP,
                                              const float* coef, int r0, int c0) {
+    constexpr int RS = G::RS;
+    // rows whose loads the residual / AXPY epilogue issues together
+    constexpr int EB = Q >= 5 ? (RS % 8 == 0 ? 8 : 6) : (RS % 4 == 0 ? 4 : 3);
     const int tx = threadIdx.x, ty = threadIdx.y;
     float acc[RS];
-    tile_acc<Q>(tile, WP, coef, tx, ty, acc);
+    tile_acc<Q, G>(tile, WP, coef, tx, ty, acc);
     const int col = c0 + tx;
     float sq = 0.f;
     if (col < a.n2 && r0 + ty * RS < a.n1) {
         if (RW) {
-            sq = strip_epilogue<(Q >= 5 ? 8 : 4)>(a, r0 + ty * RS, col, acc);
+            sq = strip_epilogue<EB, G>(a, r0 + ty * RS, col, acc);
         } else {
             const int row0 = r0 + ty * RS;
 #pragma unroll
@@ -316,11 +331,12 @@ __device__ __forceinline__ void compute_tile(const ConvArgs& a, const float* til
 // the true support), tile TH x TX, R = RS rows per thread; the halo tile is
 // loaded by the threads (any row pitch and alignment, every BC).
 template <int Q, bool RW>
-__global__ void __launch_bounds__(TX * TY)
+__global__ void __launch_bounds__(TX * G64::TY)
 conv_fast_kernel(const ConvArgs a) {
+    using G = G64;
+    constexpr int TY = G::TY, TH = G::TH;
     constexpr int W = TX + 2 * Q;        // tile row length
     constexpr int H = TH + 2 * Q;        // tile rows
-    constexpr int K = 2 * Q + 1;
     __shared__ float tile[H * W];
     __shared__ __align__(16) float coef[Coefs<Q>::COUNT];   // see load_coefs
 
@@ -364,10 +380,10 @@ conv_fast_kernel(const ConvArgs a) {
     // Phase 2 (AR tiles that reach past the image only): the anti-reflected samples.
     if (a.bc == AR_BC_ANTIREFLECTIVE &&
         (r0 - Q < 0 || r0 + TH + Q > a.n1 || c0 - Q < 0 || c0 + TX + Q > a.n2))
-        fixup_tile<Q>(a, tile, W, r0, c0, tid, TX * TY);
+        fixup_tile<Q, G>(a, tile, W, r0, c0, tid, TX * TY);
 
     pdl_trigger();
-    compute_tile<Q, RW>(a, tile, W, coef, r0, c0);
+    compute_tile<Q, RW, G>(a, tile, W, coef, r0, c0);
 }
 
 __device__ int g_conv_timeout;
@@ -377,11 +393,11 @@ __device__ int g_conv_timeout;
 // is WB = TX + 2 PADL wide, HB = TH + 2Q high.  Two boxes per CTA: one in
 // use, one in flight (a third was faster on 4096^2 images alone but cost
 // resident CTAs and time inside the restoration loop).
-template <int Q>
+template <int Q, class G>
 struct TmaTile {
     static constexpr int PADL = (Q + 3) & ~3;
     static constexpr int WB = TX + 2 * PADL;
-    static constexpr int HB = TH + 2 * Q;
+    static constexpr int HB = G::TH + 2 * Q;
     static constexpr uint32_t BYTES = (uint32_t)WB * HB * 4;
     static constexpr uint32_t BUF = (BYTES + 127u) & ~127u;   // buffers start 128-byte aligned
     static constexpr int NBUF = 2;
@@ -393,11 +409,12 @@ struct TmaTile {
 // of the next NBUF - 1 tiles requested by TMA (zeros outside the image) while
 // the CTA works on the current one.  Out-of-image samples of the extended
 // domain are then filled in shared memory.
-template <int Q, bool RW>
-__global__ void __launch_bounds__(TX * TY)
+template <int Q, bool RW, class G>
+__global__ void __launch_bounds__(TX * G::TY)
 conv_tma_kernel(const __grid_constant__ CUtensorMap tmx, const ConvArgs a, int ntx, int ntiles) {
     using namespace tc;
-    using T = TmaTile<Q>;
+    using T = TmaTile<Q, G>;
+    constexpr int TY = G::TY, TH = G::TH;
     constexpr int WB = T::WB, NBUF = T::NBUF;
     extern __shared__ __align__(128) uint8_t smem_raw_c[];
     // TMA destinations: 128-byte aligned (the allocation has 128 bytes of slack)
@@ -441,9 +458,9 @@ conv_tma_kernel(const __grid_constant__ CUtensorMap tmx, const ConvArgs a, int n
         const int r0 = (t / ntx) * TH, c0 = (t % ntx) * TX;
         float* tile = buffer(li % NBUF) + (T::PADL - Q);
         if (r0 - Q < 0 || r0 + TH + Q > a.n1 || c0 - Q < 0 || c0 + TX + Q > a.n2)
-            fixup_tile<Q>(a, tile, WB, r0, c0, tid, TX * TY);
+            fixup_tile<Q, G>(a, tile, WB, r0, c0, tid, TX * TY);
         if (a.early_trigger && li == nmine - 1) pdl_trigger();
-        compute_tile<Q, RW>(a, tile, WB, coef, r0, c0);
+        compute_tile<Q, RW, G>(a, tile, WB, coef, r0, c0);
         __syncthreads();                 // the buffer is refilled for tile li + NBUF
     }
     if (!a.early_trigger) pdl_trigger();
@@ -463,19 +480,21 @@ conv_tma_kernel(const __grid_constant__ CUtensorMap tmx, const ConvArgs a, int n
 // through their (consumed) halo boxes and write the bf16x3 split of y+ (first
 // half) and y- (second half) for t = c0 + j, zeros past ceil(n2/2) resp.
 // floor(n2/2).
-template <int Q>
+template <int Q, class G>
 struct FoldTile {
-    static_assert(TmaTile<Q>::BYTES >= (uint32_t)TH * TX * 4, "a box holds a tile of results");
-    static constexpr size_t SMEM = 2 * TmaTile<Q>::NBUF * (size_t)TmaTile<Q>::BUF +
-                                   (size_t)Coefs<Q>::COUNT * 4 + 8 * TmaTile<Q>::NBUF + 128;
+    using T = TmaTile<Q, G>;
+    static_assert(T::BYTES >= (uint32_t)G::TH * TX * 4, "a box holds a tile of results");
+    static constexpr size_t SMEM = 2 * T::NBUF * (size_t)T::BUF + (size_t)Coefs<Q>::COUNT * 4 +
+                                   8 * T::NBUF + 128;
 };
 
-template <int Q>
-__global__ void __launch_bounds__(2 * TX * TY)
+template <int Q, class G>
+__global__ void __launch_bounds__(2 * TX * G::TY)
 conv_tma_fold_kernel(const __grid_constant__ CUtensorMap tmx, const ConvArgs a, int ncp,
                      int nunits) {
     using namespace tc;
-    using T = TmaTile<Q>;
+    using T = TmaTile<Q, G>;
+    constexpr int TY = G::TY, TH = G::TH, RS = G::RS;
     constexpr int WB = T::WB, NBUF = T::NBUF;
     extern __shared__ __align__(128) uint8_t smem_raw_c[];
     uint8_t* sbase = smem_raw_c + ((128u - (smem_u32(smem_raw_c) & 127u)) & 127u);
@@ -526,10 +545,10 @@ conv_tma_fold_kernel(const __grid_constant__ CUtensorMap tmx, const ConvArgs a, 
         // a tile and its mirror reach past the same image borders, so both
         // halves take the same barriers inside the fix-up
         if (r0 - Q < 0 || r0 + TH + Q > a.n1 || c0 - Q < 0 || c0 + TX + Q > a.n2)
-            fixup_tile<Q>(a, tile, WB, r0, cg, gtid, TX * TY);
+            fixup_tile<Q, G>(a, tile, WB, r0, cg, gtid, TX * TY);
         if (li == nmine - 1) pdl_trigger();
         float acc[RS];
-        tile_acc<Q>(tile, WB, coef, threadIdx.x, gty, acc);
+        tile_acc<Q, G>(tile, WB, coef, threadIdx.x, gty, acc);
         __syncthreads();                 // both boxes consumed: they take the results
         float* mine = buffer(li % NBUF, grp);
 #pragma unroll
@@ -579,14 +598,14 @@ conv_generic_kernel(const ConvArgs a) {
     if (a.sumsq) add_sumsq(a.sumsq, sq);
 }
 
-// TMA map of the float32 image x (n1 rows of n2) with the halo box of Q.
-template <int Q>
+// TMA map of the float32 image x (n1 rows of n2) with the halo box of Q and G.
+template <int Q, class G>
 bool make_image_map(const ConvArgs& a, CUtensorMap* map) {
     auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder());
     if (!enc) return false;
     cuuint64_t dims[2] = {(cuuint64_t)a.n2, (cuuint64_t)a.n1};
     cuuint64_t strides[1] = {(cuuint64_t)a.n2 * 4};
-    cuuint32_t box[2] = {(cuuint32_t)TmaTile<Q>::WB, (cuuint32_t)TmaTile<Q>::HB};
+    cuuint32_t box[2] = {(cuuint32_t)TmaTile<Q, G>::WB, (cuuint32_t)TmaTile<Q, G>::HB};
     cuuint32_t es[2] = {1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(a.x), dims, strides, box,
                es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -594,31 +613,53 @@ bool make_image_map(const ConvArgs& a, CUtensorMap* map) {
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int Q>
-cudaError_t launch_fold(const ConvArgs& a, cudaStream_t s) {
-    using F = FoldTile<Q>;
+// Work units per SM of a launch of `units` that fits in one wave of `per` units per
+// SM (0 when it does not fit): the most any SM gets, times the rows of a unit.
+inline int wave_rows(int units, int per, int th) {
+    const int nsm = sm_count();
+    if (units > per * nsm) return 0;
+    return (units + nsm - 1) / nsm * th;
+}
+
+// G54 where a single wave of it leaves the busiest SM at least 10% fewer rows.
+inline bool prefer_g54(int units64, int units54, int per) {
+    const int r64 = wave_rows(units64, per, G64::TH), r54 = wave_rows(units54, per, G54::TH);
+    return r64 > 0 && r54 > 0 && 10 * r54 < 9 * r64;
+}
+
+template <int Q, class G>
+cudaError_t launch_fold_g(const ConvArgs& a, cudaStream_t s) {
+    using F = FoldTile<Q, G>;
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     static int per_sm = 1;
     std::call_once(once, [] {
-        attr = cudaFuncSetAttribute(conv_tma_fold_kernel<Q>,
+        attr = cudaFuncSetAttribute(conv_tma_fold_kernel<Q, G>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::SMEM);
         if (attr == cudaSuccess)
-            attr = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_tma_fold_kernel<Q>,
-                                                                 2 * TX * TY, F::SMEM);
+            attr = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, conv_tma_fold_kernel<Q, G>, 2 * TX * G::TY, F::SMEM);
         if (per_sm < 1) per_sm = 1;
     });
     if (attr != cudaSuccess) return attr;
     CUtensorMap map;
-    if (!make_image_map<Q>(a, &map)) return cudaErrorInvalidValue;
+    if (!make_image_map<Q, G>(a, &map)) return cudaErrorInvalidValue;
     const int h = (a.n2 + 1) / 2;
-    const int ncp = (h + TX - 1) / TX, nty = (a.n1 + TH - 1) / TH;
+    const int ncp = (h + TX - 1) / TX, nty = (a.n1 + G::TH - 1) / G::TH;
     const int nunits = ncp * nty;
     const int cap = sm_count() * per_sm;
     const int grid = nunits < cap ? nunits : cap;
     count_launch();
-    return launch_pdl(conv_tma_fold_kernel<Q>, dim3(grid), dim3(TX, 2 * TY), F::SMEM, s, map, a,
-                      ncp, nunits);
+    return launch_pdl(conv_tma_fold_kernel<Q, G>, dim3(grid), dim3(TX, 2 * G::TY), F::SMEM, s, map,
+                      a, ncp, nunits);
+}
+
+template <int Q>
+cudaError_t launch_fold(const ConvArgs& a, cudaStream_t s) {
+    const int ncp = ((a.n2 + 1) / 2 + TX - 1) / TX;
+    const int u64 = ncp * ((a.n1 + G64::TH - 1) / G64::TH);
+    const int u54 = ncp * ((a.n1 + G54::TH - 1) / G54::TH);
+    return prefer_g54(u64, u54, 1) ? launch_fold_g<Q, G54>(a, s) : launch_fold_g<Q, G64>(a, s);
 }
 
 template <int Q, bool RW>
@@ -636,41 +677,58 @@ cudaError_t launch_fast(const ConvArgs& a, cudaStream_t s) {
     return launch_tiles<Q, false>(a, s);
 }
 
+// The persistent TMA path with geometry G; false in *ok when the map cannot be made.
+template <int Q, bool RW, class G>
+cudaError_t launch_tma(const ConvArgs& a, cudaStream_t s, bool* ok) {
+    using T = TmaTile<Q, G>;
+    // a.spread: one wave of at most two CTAs per SM, by the shared-memory request,
+    // so that CTAs placed while the predecessor drains cannot pile onto the SMs
+    // that free up first
+    constexpr size_t SMEM2 = T::SMEM > 80 * 1024 ? T::SMEM : 80 * 1024;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    static int per_sm = 1;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(conv_tma_kernel<Q, RW, G>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM2);
+        if (attr == cudaSuccess)
+            attr = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_tma_kernel<Q, RW, G>,
+                                                                 TX * G::TY, T::SMEM);
+        if (per_sm < 1) per_sm = 1;
+    });
+    CUtensorMap map;
+    *ok = attr == cudaSuccess && make_image_map<Q, G>(a, &map);
+    if (!*ok) return cudaSuccess;
+    const int ntx = (a.n2 + TX - 1) / TX, nty = (a.n1 + G::TH - 1) / G::TH;
+    const int ntiles = ntx * nty;
+    const bool two = a.spread && ntiles <= 2 * sm_count();
+    const int cap = sm_count() * per_sm;
+    const int grid = ntiles < cap ? ntiles : cap;
+    // a programmatic dependent: the CTAs are placed while the predecessor
+    // drains; predecessors that could leave SMs idle for long (the last
+    // contraction, stencils) let it launch only at their end, so that early
+    // CTAs do not pile onto those SMs
+    count_launch();
+    return launch_pdl(conv_tma_kernel<Q, RW, G>, dim3(grid), dim3(TX, G::TY),
+                      two ? SMEM2 : T::SMEM, s, map, a, ntx, ntiles);
+}
+
 template <int Q, bool RW>
 cudaError_t launch_tiles(const ConvArgs& a, cudaStream_t s) {
     // TMA path: AR / Reflective, 16-byte aligned image and row pitch
     if (a.bc != AR_BC_PERIODIC && (reinterpret_cast<uintptr_t>(a.x) & 15) == 0 &&
         (a.n2 & 3) == 0) {
-        using T = TmaTile<Q>;
-        static std::once_flag once;
-        static cudaError_t attr = cudaSuccess;
-        static int per_sm = 1;
-        std::call_once(once, [] {
-            attr = cudaFuncSetAttribute(conv_tma_kernel<Q, RW>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
-            if (attr == cudaSuccess)
-                attr = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_tma_kernel<Q, RW>,
-                                                                     TX * TY, T::SMEM);
-            if (per_sm < 1) per_sm = 1;
-        });
-        CUtensorMap map;
-        if (attr == cudaSuccess && make_image_map<Q>(a, &map)) {
-            const int ntx = (a.n2 + TX - 1) / TX, nty = (a.n1 + TH - 1) / TH;
-            const int ntiles = ntx * nty;
-            const int cap = sm_count() * per_sm;
-            const int grid = ntiles < cap ? ntiles : cap;
-            // a programmatic dependent: the CTAs are placed while the predecessor
-            // drains; predecessors that could leave SMs idle for long (the last
-            // contraction, stencils) let it launch only at their end, so that
-            // early CTAs do not pile onto those SMs
-            count_launch();
-            return launch_pdl(conv_tma_kernel<Q, RW>, dim3(grid), dim3(TX, TY), T::SMEM, s, map, a,
-                              ntx, ntiles);
-        }
+        const int ntx = (a.n2 + TX - 1) / TX;
+        const int t64 = ntx * ((a.n1 + G64::TH - 1) / G64::TH);
+        const int t54 = ntx * ((a.n1 + G54::TH - 1) / G54::TH);
+        bool ok = false;
+        const cudaError_t e = prefer_g54(t64, t54, 2) ? launch_tma<Q, RW, G54>(a, s, &ok)
+                                                      : launch_tma<Q, RW, G64>(a, s, &ok);
+        if (ok || e != cudaSuccess) return e;
     }
-    dim3 grid((a.n2 + TX - 1) / TX, (a.n1 + TH - 1) / TH);
+    dim3 grid((a.n2 + TX - 1) / TX, (a.n1 + G64::TH - 1) / G64::TH);
     count_launch();
-    conv_fast_kernel<Q, RW><<<grid, dim3(TX, TY), 0, s>>>(a);
+    conv_fast_kernel<Q, RW><<<grid, dim3(TX, G64::TY), 0, s>>>(a);
     return cudaGetLastError();
 }
 

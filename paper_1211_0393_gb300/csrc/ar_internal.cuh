@@ -86,6 +86,8 @@ struct ConvArgs {
                          // needs a whole SM): let it launch when the last tile
                          // starts, not after it (TMA path; the TMA stencils launch
                          // as programmatic dependents)
+    int spread;          // the launch owns the GPU (the single-image loop): a grid
+                         // that fits one wave takes at most two CTAs per SM
 };
 
 // Launches the AR stencil on `stream` (validated arguments).

@@ -131,6 +131,7 @@ extern "C" ar_status ar_restore_plain_static(const float* g, const double* psf_h
     blur.q2 = q2;
     blur.flip = 0;
     blur.mode = CONV_RESIDUAL;
+    blur.spread = 1;
     ConvArgs reblur = blur;
     reblur.x = r;
     reblur.aux = nullptr;
