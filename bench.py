@@ -327,7 +327,7 @@ def kernel_rooflines(ar, torch, dev, step):
                                    "diagonal and G4 dense)"}
     else:
         ach = stencil_flops / t_st / 1e12
-        roof = {"kernel": "conv_tma_kernel<7, true> (AR pad + 15x15 convolution, residual)",
+        roof = {"kernel": "conv_tma_kernel<7, true, G54> (AR pad + 15x15 convolution, residual)",
                 "bound": "alu",
                 "achieved": round(ach, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
                 "frac": round(ach / fp32_peak, 4), "traffic": measured_traffic("stencil"),
