@@ -346,6 +346,19 @@ PROFILES = {
 }
 
 
+def source_digest(path):
+    """sha256 of a source file's code: // comments, trailing blanks and empty lines
+    dropped, so that a comment edit does not mark the committed counters stale."""
+    import hashlib
+    import re
+    lines = []
+    for line in open(path, encoding="utf-8").read().splitlines():
+        line = re.sub(r"//.*$", "", line).rstrip()
+        if line:
+            lines.append(line)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()
+
+
 def iteration_dram():
     """DRAM bytes per pixel of one restoration iteration in the warm loop (ncu, caches
     not flushed between launches), from the committed summary while both kernel sources
@@ -354,11 +367,10 @@ def iteration_dram():
     prof = os.path.join(ROOT, "profiles/iteration_dram_ellipses1024.md")
     try:
         fields = dict(line.split(": ", 1) for line in open(prof).read().splitlines()
-                      if line.startswith(("dram_bytes_per_iteration:", "source_sha256_prefix_")))
-        for key, src in (("source_sha256_prefix_conv", PROFILES["stencil"][1]),
-                         ("source_sha256_prefix_transform", PROFILES["contraction"][1])):
-            sha = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()
-            if not sha.startswith(fields[key].strip()):
+                      if line.startswith(("dram_bytes_per_iteration:", "source_code_sha256_prefix_")))
+        for key, src in (("source_code_sha256_prefix_conv", PROFILES["stencil"][1]),
+                         ("source_code_sha256_prefix_transform", PROFILES["contraction"][1])):
+            if not source_digest(os.path.join(ROOT, src)).startswith(fields[key].strip()):
                 return None
         b = int(fields["dram_bytes_per_iteration"])
         return {"bytes_per_iter": b, "bytes_per_px": round(b / (N1 * N2), 2),
@@ -370,15 +382,13 @@ def iteration_dram():
 
 def measured_traffic(kind):
     """DRAM bytes per launch from the committed ncu summary, or None when the
-    kernel's source changed since those counters were taken."""
-    import hashlib
+    kernel's code changed since those counters were taken."""
     prof, src = PROFILES[kind]
     try:
         text = open(os.path.join(ROOT, prof)).read()
         fields = dict(line.split(": ", 1) for line in text.splitlines()
-                      if line.startswith(("dram_bytes_per_launch:", "source_sha256_prefix:")))
-        sha = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()
-        if sha.startswith(fields["source_sha256_prefix:".rstrip(":")].strip()):
+                      if line.startswith(("dram_bytes_per_launch:", "source_code_sha256_prefix:")))
+        if source_digest(os.path.join(ROOT, src)).startswith(fields["source_code_sha256_prefix"].strip()):
             return int(fields["dram_bytes_per_launch"])
     except Exception:
         pass

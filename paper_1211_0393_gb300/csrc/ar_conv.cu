@@ -14,11 +14,12 @@
 // when the image rows are 16-byte aligned; otherwise by the threads,
 // all loads of a thread in flight at once) and, on tiles that reach past the
 // image, overwrites the out-of-image samples with their anti-reflections
-// computed from in-tile samples.  Each thread then computes a vertical strip of R outputs of one
-// column, sliding a register window down the tile: per PSF column it loads
-// R + 2Q values from shared memory (consecutive lanes read consecutive
-// columns: conflict-free) and issues R (2Q+1) FMAs against broadcast PSF
-// coefficients.  The kernel is FP32-FMA bound for Q >= 2.
+// computed from in-tile samples.  Each thread then computes a vertical strip of
+// R outputs of one column (R = 16 or 18, by the tile geometry), sliding a
+// register window down the tile: per PSF column it loads R + 2Q values from
+// shared memory (consecutive lanes read consecutive columns: conflict-free)
+// and issues R (2Q+1) FMAs against broadcast PSF coefficients.  The kernel is
+// FP32-FMA bound for Q >= 2.
 
 #include "ar_internal.cuh"
 #include "ar_tc.cuh"
@@ -328,8 +329,8 @@ __device__ __forceinline__ void compute_tile(const ConvArgs& a, const float* til
 }
 
 // Fast path: support padded to Q x Q (Q = max(q1, q2) <= 15, zero taps outside
-// the true support), tile TH x TX, R = RS rows per thread; the halo tile is
-// loaded by the threads (any row pitch and alignment, every BC).
+// the true support), 64 x 64 tiles (geometry G64), 16 rows per thread; the halo
+// tile is loaded by the threads (any row pitch and alignment, every BC).
 template <int Q, bool RW>
 __global__ void __launch_bounds__(TX * G64::TY)
 conv_fast_kernel(const ConvArgs a) {

@@ -271,6 +271,25 @@ def test_restore_folded_input_shapes(ar, n1, n2, q1, q2):
     assert_trace_close(tr, to, tol_alpha(alpha))
 
 
+def test_restore_past_one_wave_matches_oracle(ar):
+    """1104 x 1536: too many tiles for one wave, so the stencils (the residual blur
+    and the folding reblur) take their 64-row geometry; two iterations against the
+    oracle, then the plain-mode stencil with the x update."""
+    rng = np.random.default_rng(1104)
+    n1, n2 = 1104, 1536
+    h = rand_psf(rng, 7, 6)
+    f = rng.uniform(0, 1, (n1, n2))
+    g = (O.ar_blur(f, h) + 0.005 * rng.standard_normal((n1, n2))).astype(np.float32)
+    f32 = f.astype(np.float32)
+    for pc, alpha in ((True, 0.3), (False, 0.0)):
+        x, tr, _ = ar.ar_restore(dev(g), h, alpha, 1.0, 2, pc, f_true=dev(f32))
+        xo, to, _ = O.restore(g.astype(np.float64), h, alpha, 1.0, 2, pc,
+                              f_true=f32.astype(np.float64))
+        tol = tol_alpha(alpha) if pc else 1e-5
+        assert rel_l2(x.cpu().numpy(), xo) <= tol
+        assert_trace_close(tr, to, tol)
+
+
 def test_restore_warm_start_and_in_place(ar):
     h = W.psf_config1()
     g, f = _workload(64, h, "blocks", 0, 0.01)
