@@ -522,36 +522,6 @@ __device__ __forceinline__ void split3_f64(double v, uint16_t& h0, uint16_t& h1,
     h2 = __bfloat16_as_ushort(p2);
 }
 
-// T~'_m (analysis) and T'_m (synthesis) as bf16x3 planes, row pitch ld.
-__global__ void fill_transforms_kernel(int m, int ld, const double* tab, const double* qp,
-                                       const double* qjp, uint16_t* Tt, uint16_t* T) {
-    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (size_t)m * m) return;
-    const int s = (int)(idx / m), t = (int)(idx % m);
-    double vt, v;
-    if (s == 0 || s == m - 1) {
-        vt = v = (t == s) ? 1.0 : 0.0;
-    } else if (t == 0) {
-        vt = -qp[s - 1];
-        v = 1.0 - (double)s / (double)(m - 1);
-    } else if (t == m - 1) {
-        vt = -qjp[s - 1];
-        v = (double)s / (double)(m - 1);
-    } else {
-        vt = v = q_entry(tab, s, t, m);
-    }
-    const size_t ps = (size_t)m * ld, o = (size_t)s * ld + t;
-    uint16_t a0, a1, a2;
-    split3_f64(vt, a0, a1, a2);
-    Tt[o] = a0;
-    Tt[ps + o] = a1;
-    Tt[2 * ps + o] = a2;
-    split3_f64(v, a0, a1, a2);
-    T[o] = a0;
-    T[ps + o] = a1;
-    T[2 * ps + o] = a2;
-}
-
 // Comparison-BC transforms as bf16x3 planes, row pitch ld, entry (s, t):
 //  Reflective (eq. Rn, DCT-III): Tt = R^T, T = R with
 //    R[t][k] = sqrt((2 - delta_{k,0}) / m) cos(k (2t + 1) pi / (2m));
