@@ -301,11 +301,10 @@ def kernel_rooflines(ar, torch, dev, step):
     prof = ar.ar_profile_end()
     k1, k2 = ar_psf_shape()
     stencil_flops = 2.0 * k1 * k2 * N1 * N2                 # per launch
-    # per iteration, six bf16 products (bf16x3 split) of: G1, G2, G3 block diagonal (the
-    # even/odd fold; G1's input arrives folded from the reblur): half of n^3 each; G4
-    # (M = n2, N = n1, K = n1) dense.  Averaged over the four launches: 5/8 of
-    # 6 x 2 x n^3 at n = 1024.
-    contraction_flops = 6 * 2.0 * N1 * N2 * N1 * 0.625
+    # per iteration, six bf16 products (bf16x3 split) of G1..G4, all four block diagonal
+    # (the even/odd fold; G1's input arrives folded from the reblur, G4 pairs its parity
+    # tiles in clusters of four): half of n^3 each, i.e. 1/2 of 6 x 2 x n^3 per launch.
+    contraction_flops = 6 * 2.0 * N1 * N2 * N1 * 0.5
     kernels = {}
     for kind, (ms, cnt) in prof.items():
         if cnt:
@@ -323,8 +322,7 @@ def kernel_rooflines(ar, torch, dev, step):
                 "bound": "tensor", "achieved": round(ach, 2), "peak": bf16, "unit": "TFLOP/s",
                 "frac": round(ach / bf16, 4), "traffic": measured_traffic("contraction"),
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; kernel timed alone)",
-                "work_per_launch": "6 x 2 x 1024^3 x 5/8 bf16 flops (mean of G1, G2, G3 block "
-                                   "diagonal and G4 dense)"}
+                "work_per_launch": "6 x 2 x 1024^3 x 1/2 bf16 flops (G1-G4 block diagonal)"}
     else:
         ach = stencil_flops / t_st / 1e12
         roof = {"kernel": "conv_tma_kernel<7, true, G54> (AR pad + 15x15 convolution, residual)",

@@ -196,6 +196,18 @@ __device__ __forceinline__ uint32_t cluster_ctarank() {
     return r;
 }
 
+__device__ __forceinline__ uint32_t cluster_ctaid_y() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctaid.y;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t cluster_ctaid_z() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctaid.z;" : "=r"(r));
+    return r;
+}
+
 // All threads of every CTA of the cluster; release/acquire orders the
 // distributed shared-memory stores made before it.
 __device__ __forceinline__ void cluster_sync() {

@@ -122,6 +122,13 @@ struct TcEpiArgs {
     int kdiag;
     int pair;
     int mrows, mhalf, npair, nminus, kout, nout;
+    // npar: the N index is folded too (B block diagonal, its first nhalf rows the
+    // sums and the others the differences of the output columns s and noutn - 1 - s):
+    // a cluster of four CTAs pairs the tiles at n and nhalf + n, which swap their
+    // results through distributed shared memory; column s gets sum + difference
+    // (s < npairn), column noutn - 1 - s sum - difference (s < nminusn)
+    int npar;
+    int nhalf, npairn, nminusn, noutn;
     // late_trigger: the successor may launch only once this grid's epilogues are
     // done (it is a stencil, whose CTAs would otherwise crowd the SMs that this
     // grid leaves idle); else it may launch as soon as the accumulators are ready
@@ -159,11 +166,12 @@ __device__ __forceinline__ void acc_sum16(uint32_t trow, int col0, int nacc, flo
 constexpr int NTHREADS = 256;           // 8 warps: two per TMEM lane quarter in the epilogue
 constexpr int WCOLS = HALF / 2;         // columns of the CTA's half handled by one warp
 
-template <int NP>
-__global__ void __cluster_dims__(1, 1, SPLITK) __launch_bounds__(NTHREADS, 1)
-tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA64,
-                   const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmO,
-                   int M, int N, int K, const TcEpiArgs ep, int* err) {
+// The body of both contraction kernels: clusters of (1, 1, SPLITK) CTAs, or
+// (1, 2, SPLITK) with the parity pairs of N (NPAR, ep.npar set).
+template <int NP, bool NPAR>
+__device__ __forceinline__ void tc_contract_body(const CUtensorMap& tmA, const CUtensorMap& tmA64,
+                                                 const CUtensorMap& tmB, const CUtensorMap& tmO,
+                                                 int M, int N, int K, const TcEpiArgs& ep, int* err) {
     using namespace tc;
     using Mode = TcMode<NP>;
     constexpr int STAGES = Mode::STAGES;
@@ -185,16 +193,25 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int quarter = warp & 3, sub = warp >> 2;
-    const int m0 = blockIdx.x * (ep.pair ? BM / 2 : BM), n0 = blockIdx.y * BN;
-    const uint32_t rank = cluster_ctarank();
+    // cluster ranks run x fastest: (cy, cz) is rank cy + 2 cz with NPAR, cz without
+    const uint32_t crank = cluster_ctarank();
+    const uint32_t ks = NPAR ? crank >> 1 : crank;                // split-K half
+    const uint32_t kpeer = NPAR ? crank ^ 2u : crank ^ 1u;        // the other split-K half
+    const int parity = NPAR ? (int)(crank & 1u) : 0;
+    const int m0 = blockIdx.x * (ep.pair ? BM / 2 : BM);
+    const int n0 = NPAR ? (int)(blockIdx.y >> 1) * BN + parity * ep.nhalf : (int)blockIdx.y * BN;
+    // with NPAR the cluster is (1, 2, SPLITK): checked, not assumed
+    const bool rank_ok = !NPAR || (cluster_ctaid_y() == (blockIdx.y & 1u) &&
+                                   cluster_ctaid_z() == blockIdx.z &&
+                                   crank == (blockIdx.y & 1u) + 2u * blockIdx.z);
     int nk_all = (K + BK - 1) / BK, kb0 = 0;
     if (ep.kdiag) {                      // block-diagonal operands: this tile's half of K
         nk_all /= 2;
         if (n0 >= N / 2) kb0 = nk_all;
     }
     const int nk_first = (nk_all + 1) / 2;
-    const int kb_begin = kb0 + (rank == 0 ? 0 : nk_first);
-    const int nk = rank == 0 ? nk_first : nk_all - nk_first;
+    const int kb_begin = kb0 + (ks == 0 ? 0 : nk_first);
+    const int nk = ks == 0 ? nk_first : nk_all - nk_first;
     // A tile of k-block kb into dst: one 3D box, or two 64-row boxes per plane
     auto load_a = [&](uint32_t dst, int kb, uint32_t bar) {
         if (!ep.pair) {
@@ -315,15 +332,28 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         row = lrow < BM / 2 ? j : ep.nout - 1 - j;
         row_ok = lrow < BM / 2 ? j < ep.npair : j < ep.nminus;
     }
-    const uint32_t peer = rank ^ 1u;
-    const int ocol0 = (int)rank * HALF + sub * WCOLS;    // tile-relative own columns
-    const int pcol0 = (int)peer * HALF + sub * WCOLS;    // tile-relative peer columns
+    const int ocol0 = (int)ks * HALF + sub * WCOLS;           // tile-relative own columns
+    const int pcol0 = (int)(ks ^ 1u) * HALF + sub * WCOLS;    // tile-relative peer columns
+    // output column of tile column c (N index n0 + c) and whether it is written
+    auto out_col = [&](int c, bool& valid) {
+        const int n = n0 + c;
+        if constexpr (!NPAR) {
+            valid = n < N;
+            return n;
+        } else {
+            const int sidx = n - parity * ep.nhalf;
+            valid = sidx < (parity ? ep.nminusn : ep.npairn);
+            return parity ? ep.noutn - 1 - sidx : sidx;
+        }
+    };
+
     float pre[WCOLS];
     float pref[WCOLS];
 #pragma unroll
     for (int j = 0; j < WCOLS; ++j) {
-        const int col = n0 + ocol0 + j;
-        const bool in = row_ok && col < N;
+        bool cin;
+        const int col = out_col(ocol0 + j, cin);
+        const bool in = row_ok && cin;
         pre[j] = 0.f;
         pref[j] = 0.f;
         if (ep.mode == TE_SCALE_SPLIT_T) {
@@ -341,12 +371,12 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     __syncwarp();
     fence_after_sync();
     if (!ep.late_trigger) pdl_trigger();
-    const bool ok = ready && *sflag == 0;
+    const bool ok = ready && *sflag == 0 && rank_ok;
     const int nacc = ok ? (2 * nk < NACC ? 2 * nk : NACC) : 0;
     const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
 
     // 1) the peer's columns -> the peer's receive buffer [HALF][BM]
-    const uint32_t rrecv = mapa(recv, peer);
+    const uint32_t rrecv = mapa(recv, kpeer);
 #pragma unroll
     for (int c = 0; c < WCOLS / 16; ++c) {
         float v[16];
@@ -386,6 +416,24 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             xv[jj] = first ? xv[jj] + xp : xp - xv[jj];
         }
     }
+    if constexpr (NPAR) {
+        // the parity pair: sums (parity 0) and differences (parity 1) of the same
+        // columns swap through the partner's pipeline area past the pair buffer
+        // ([HALF][BM] float32 at byte 4 HALF BM); every CTA of the cluster left its
+        // main loop before the split-K barrier above, so that area is free
+        const uint32_t pbuf = base + 4u * HALF * BM;
+        const uint32_t prx = mapa(pbuf, crank ^ 1u);
+#pragma unroll
+        for (int jj = 0; jj < WCOLS; ++jj)
+            st_cluster_f32(prx + 4u * ((sub * WCOLS + jj) * BM + lrow), xv[jj]);
+        cluster_sync();
+        const float* pown = reinterpret_cast<const float*>(gbase) + HALF * BM;
+#pragma unroll
+        for (int jj = 0; jj < WCOLS; ++jj) {
+            const float o = pown[(sub * WCOLS + jj) * BM + lrow];
+            xv[jj] = parity == 0 ? xv[jj] + o : o - xv[jj];
+        }
+    }
     float sq = 0.f;                       // this thread's (x_new - f)^2, at most WCOLS terms
     if (ep.pair == PAIR_MIRROR) {
         // fold: lanes < 64 hold the sums of rows i = m0 + lrow, the others the
@@ -415,8 +463,11 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 stage[(0 * HALF + hc) * BM + lrow] = h0;
                 stage[(1 * HALF + hc) * BM + lrow] = h1;
                 if (NP == 3) stage[(2 * HALF + hc) * BM + lrow] = h2;
-            } else if (ok && row_ok && n0 + ocol0 + jj < N) {
-                const size_t o = (size_t)(n0 + ocol0 + jj) * ep.ldo + row;
+            } else {
+                bool cin;
+                const int col = out_col(ocol0 + jj, cin);
+                if (!(ok && row_ok && cin)) continue;
+                const size_t o = (size_t)col * ep.ldo + row;
                 if (ep.mode == TE_STORE_T) {
                     ep.out[o] = x;
                 } else {
@@ -452,11 +503,11 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         if (threadIdx.x == 0 && ok) {
             const uint32_t sb = base + (ep.pair ? 2u * HALF * BM * 2u : 0u);
             if (ep.pair == PAIR_MIRROR) {
-                tma_store_3d(&tmO, m0, n0 + (int)rank * HALF, 0, sb);
-                tma_store_3d(&tmO, ep.kout + m0, n0 + (int)rank * HALF, 0,
+                tma_store_3d(&tmO, m0, n0 + (int)ks * HALF, 0, sb);
+                tma_store_3d(&tmO, ep.kout + m0, n0 + (int)ks * HALF, 0,
                              sb + (uint32_t)(NP * HALF * (BM / 2) * 2));
             } else {
-                tma_store_3d(&tmO, m0, n0 + (int)rank * HALF, 0, sb);
+                tma_store_3d(&tmO, m0, n0 + (int)ks * HALF, 0, sb);
             }
             bulk_commit();
             bulk_wait_read();
@@ -471,6 +522,23 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         tmem_dealloc(tmem, TMEM_COLS);
     }
     if (threadIdx.x == 0 && !ok) atomicExch(err, 1);
+}
+
+template <int NP>
+__global__ void __cluster_dims__(1, 1, SPLITK) __launch_bounds__(NTHREADS, 1)
+tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA64,
+                   const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmO,
+                   int M, int N, int K, const TcEpiArgs ep, int* err) {
+    tc_contract_body<NP, false>(tmA, tmA64, tmB, tmO, M, N, K, ep, err);
+}
+
+// npar: the parity pairs of N in the same cluster
+template <int NP>
+__global__ void __cluster_dims__(1, 2, SPLITK) __launch_bounds__(NTHREADS, 1)
+tc_contract_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA64,
+                        const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmO,
+                        int M, int N, int K, const TcEpiArgs ep, int* err) {
+    tc_contract_body<NP, true>(tmA, tmA64, tmB, tmO, M, N, K, ep, err);
 }
 
 // ---------------------------------------------------------------- matrices --
@@ -897,17 +965,27 @@ ar_status contract_np(const Operand& A, const Operand& B, const Operand* O, cons
         attr = cudaFuncSetAttribute(tc_contract_kernel<NP>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)TcMode<NP>::SMEM_BYTES);
+        if (attr == cudaSuccess)
+            attr = cudaFuncSetAttribute(tc_contract_pair_kernel<NP>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)TcMode<NP>::SMEM_BYTES);
     });
     if (attr != cudaSuccess) return cuda_fail(attr, "tc_contract_kernel smem attribute");
     const int mtiles = ep.pair ? (ep.npair + BM / 2 - 1) / (BM / 2) : (A.rows + BM - 1) / BM;
-    dim3 grid(mtiles, (B.rows + BN - 1) / BN, SPLITK);
+    const int ntiles = (B.rows + BN - 1) / BN;
+    // npar: the two halves of N (nhalf rows of B each, a multiple of BN) pair
+    // tile by tile, y = 2 c + parity
+    if (ep.npar && (ep.nhalf % BN != 0 || B.rows != 2 * ep.nhalf))
+        return fail(AR_ERR_UNSUPPORTED, "paired N halves need nhalf a multiple of %d", BN);
+    dim3 grid(mtiles, ntiles, SPLITK);
     ProfScope prof(AR_PROF_CONTRACTION, s);
     const int mi = mode_index(NP);
     count_launch();
     const CUtensorMap& omap = !O ? A.map[mi] : (ep.pair == PAIR_MIRROR ? O->omapf[mi] : O->omap[mi]);
-    AR_CUDA(launch_pdl(tc_contract_kernel<NP>, grid, dim3(NTHREADS), (size_t)TcMode<NP>::SMEM_BYTES,
-                       s, A.map[mi], ep.pair ? A.map64[mi] : A.map[mi], B.map[mi], omap, A.rows,
-                       B.rows, A.K, ep, err));
+    AR_CUDA(launch_pdl(ep.npar ? tc_contract_pair_kernel<NP> : tc_contract_kernel<NP>, grid,
+                       dim3(NTHREADS), (size_t)TcMode<NP>::SMEM_BYTES, s, A.map[mi],
+                       ep.pair ? A.map64[mi] : A.map[mi], B.map[mi], omap, A.rows, B.rows, A.K, ep,
+                       err));
     return AR_OK;
 }
 
@@ -915,6 +993,26 @@ ar_status contract_np(const Operand& A, const Operand& B, const Operand* O, cons
 ar_status contract(int np, const Operand& A, const Operand& B, const Operand* O,
                    const TcEpiArgs& ep, int* err, cudaStream_t s) {
     return np == 2 ? contract_np<2>(A, B, O, ep, err, s) : contract_np<3>(A, B, O, ep, err, s);
+}
+
+// Clusters of four contraction CTAs that can be resident at once (0 on error).
+template <int NP>
+int max_quad_clusters() {
+    static std::once_flag once;
+    static int n = 0;
+    std::call_once(once, [] {
+        if (cudaFuncSetAttribute(tc_contract_pair_kernel<NP>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)TcMode<NP>::SMEM_BYTES) != cudaSuccess)
+            return;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(1, 2, SPLITK);
+        cfg.blockDim = dim3(NTHREADS);
+        cfg.dynamicSmemBytes = TcMode<NP>::SMEM_BYTES;
+        if (cudaOccupancyMaxActiveClusters(&n, tc_contract_pair_kernel<NP>, &cfg) != cudaSuccess) n = 0;
+        cudaGetLastError();
+    });
+    return n;
 }
 
 }  // namespace
@@ -929,6 +1027,8 @@ struct TransformPlan {
     Operand Tp1, Tp2;          // Periodic: flipped synthesis operands (cache-owned)
     Operand Ttp2, Ttf1, Tsf2, Tsp1;   // AR folded: G1 .. G4 constant operands (cache-owned)
     Operand Ttf2;              // AR folded, Y folded: G1's block-diagonal operand
+    Operand Tsf1;              // AR folded, N folded: G4's block-diagonal operand
+    bool fold_out;             // AR: G4 folds its N index too (clusters of four)
     Operand P;                 // n1 x n2 images: Y (all BCs), then W (Reflective, Periodic)
     Operand P2;                // Periodic: n1 x n2, the odd-part filtered spectrum
     Operand Qo;                // n2 x n1 images: U^T, then V^T (Reflective, Periodic)
@@ -947,6 +1047,14 @@ ar_status transform_plan_create(int n1, int n2, int bc, int precision, cudaStrea
     p->np = precision == AR_PRECISION_BF16X2 ? 2 : 3;
     p->folded = bc == AR_BC_ANTIREFLECTIVE;
     p->fold_y = p->folded && fold_input && (n2 % 4) == 0;
+    if (p->folded) {
+        // G4 with its N index folded runs in clusters of four: taken when they all
+        // fit at once, or when there are so many that waves are unavoidable anyway
+        const FoldDims f1 = fold_dims(n1), f2 = fold_dims(n2);
+        const int need = ((f2.h + BM / 2 - 1) / (BM / 2)) * (f1.Hs / BN);
+        const int fit = p->np == 2 ? max_quad_clusters<2>() : max_quad_clusters<3>();
+        p->fold_out = fit > 0 && (need <= fit || need > 2 * fit);
+    }
     TransformSet t1, t2;
     ar_status st = cached_transforms(n1, bc, s, &t1);
     if (st == AR_OK) st = cached_transforms(n2, bc, s, &t2);
@@ -962,6 +1070,7 @@ ar_status transform_plan_create(int n1, int n2, int bc, int precision, cudaStrea
         p->Ttp2 = t2.Ttp;
         p->Ttf2 = t2.Ttf;
         p->Tsf2 = t2.Tsf;
+        p->Tsf1 = t1.Tsf;
     }
     if (p->folded) {
         const FoldDims f1 = fold_dims(n1), f2 = fold_dims(n2);
@@ -1119,7 +1228,15 @@ ar_status transform_apply(TransformPlan* p, const float* d32, const float* d32_o
         e4.nminus = f2.ha;
         e4.nout = n2;
         e4.late_trigger = 1;
-        AR_TRY(contract(p->np, p->V, p->Tsp1, nullptr, e4, p->err, s));
+        if (p->fold_out) {             // N folded too: block diagonal, parity tiles paired
+            e4.kdiag = 1;
+            e4.npar = 1;
+            e4.nhalf = f1.Hs;
+            e4.npairn = f1.h;
+            e4.nminusn = f1.ha;
+            e4.noutn = n1;
+        }
+        AR_TRY(contract(p->np, p->V, p->fold_out ? p->Tsf1 : p->Tsp1, nullptr, e4, p->err, s));
         return AR_OK;
     }
     TcEpiArgs e{};
