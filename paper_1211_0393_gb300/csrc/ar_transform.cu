@@ -90,7 +90,7 @@ struct TcMode {
     static constexpr uint32_t A_STAGE = PLANES * A_PLANE;
     static constexpr uint32_t B_STAGE = PLANES * B_PLANE;
     static constexpr uint32_t STAGE_BYTES = A_STAGE + B_STAGE;   // 48 KiB / 32 KiB
-    static constexpr uint32_t CTRL_BYTES = 8 * (2 * STAGES + 1) + 16;
+    static constexpr uint32_t CTRL_BYTES = 8 * (2 * STAGES + 2) + 16;
     static constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + RECV_BYTES + CTRL_BYTES + 1024;
 };
 static_assert(TcMode<3>::SMEM_BYTES <= 232448 && TcMode<2>::SMEM_BYTES <= 232448, "smem budget");
@@ -185,8 +185,9 @@ __device__ __forceinline__ void tc_contract_body(const CUtensorMap& tmA, const C
     const float* recv_ptr = reinterpret_cast<const float*>(gbase + STAGES * STAGE_BYTES);
     const uint32_t bars = recv + RECV_BYTES;
     const uint32_t done_bar = bars + 8u * (2 * STAGES);
+    const uint32_t issued_bar = bars + 8u * (2 * STAGES + 1);   // the last MMA was issued
     uint32_t* tslot = reinterpret_cast<uint32_t*>(gbase + STAGES * STAGE_BYTES + RECV_BYTES +
-                                                  8 * (2 * STAGES + 1));
+                                                  8 * (2 * STAGES + 2));
     volatile int* sflag = reinterpret_cast<volatile int*>(tslot + 1);
     // after the main loop the stage area stages the split output tile [NP][HALF][BM]
     uint16_t* stage_out = reinterpret_cast<uint16_t*>(gbase);
@@ -232,6 +233,7 @@ __device__ __forceinline__ void tc_contract_body(const CUtensorMap& tmA, const C
             mbar_init(bars + 8u * (STAGES + s), 1);      // empty[s]: MMAs reading it done
         }
         mbar_init(done_bar, 1);
+        mbar_init(issued_bar, 1);
         *sflag = 0;
         fence_mbar_init();
         prefetch_tmap(&tmA);
@@ -313,6 +315,8 @@ __device__ __forceinline__ void tc_contract_body(const CUtensorMap& tmA, const C
             }
             mma_commit(bars + 8u * (STAGES + s));        // frees the stage when its MMAs finish
         }
+        // every operand has landed: the epilogue's own loads no longer compete with TMA
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(issued_bar) : "memory");
         if (nk > 0) {
             mma_commit(done_bar);                        // accumulators complete
         } else {
@@ -349,6 +353,9 @@ __device__ __forceinline__ void tc_contract_body(const CUtensorMap& tmA, const C
 
     float pre[WCOLS];
     float pref[WCOLS];
+    // the filter / iterate / true-image tiles are fetched once the main loop's
+    // operands are in (while the last MMAs run): earlier they slowed its TMA loads
+    if (ep.mode == TE_SCALE_SPLIT_T || ep.mode == TE_AXPY_T) mbar_wait(issued_bar, 0);
 #pragma unroll
     for (int j = 0; j < WCOLS; ++j) {
         bool cin;
