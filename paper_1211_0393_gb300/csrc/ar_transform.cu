@@ -40,6 +40,12 @@
 // split of the next operand, the filter d, or x += tau * result.  Full-rate
 // MMA at M = 128 needs N >= 128: with smaller N the six products' operand
 // reads exceed the shared-memory bandwidth.
+//
+// For AR the chain runs on the even/odd folds of both axes (see transform_apply):
+// every product is block diagonal in K, so a tile reads half of K.  G4 also folds
+// its N index: tc_contract_pair_kernel runs clusters of four CTAs (the split-K
+// pair times the two parities of N), whose parity tiles swap their sums and
+// differences through distributed shared memory before the unfolding epilogue.
 
 #include "ar_internal.cuh"
 #include "ar_tc.cuh"
