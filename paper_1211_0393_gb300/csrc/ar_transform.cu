@@ -1196,7 +1196,8 @@ ar_status transform_apply(TransformPlan* p, const float* d32, const float* d32_o
         // G1: U = fold_1((Y Ttp2^T)^T)   A = Y rows paired (i, n1-1-i), output K-folded
         // G2: W = d o (U Ttf1^T)^T       block diagonal in K
         // G3: V = (W Tsf2^T)^T           block diagonal in K, output rows folded along axis 2
-        // G4: out (+)= unfold_2((V Tsp1^T)^T)   A = V rows paired (j, h + j)
+        // G4: out (+)= unfold_2((V Tsp1^T)^T)   A = V rows paired (j, h + j); with fold_out
+        //     block diagonal against Tsf1, unfold_1 across the parity pair of CTAs
         const FoldDims f1 = fold_dims(n1), f2 = fold_dims(n2);
         TcEpiArgs e{};
         e.mode = TE_SPLIT_T;
