@@ -191,7 +191,10 @@ def test_setup_eigenvalues_match_oracle(ar, n1, n2, q1, q2, alpha):
 
 
 SOLVE_CASES = [(8, 8, 2, 2, 0.1), (64, 64, 4, 4, 0.03), (37, 53, 5, 3, 0.01), (130, 257, 7, 7, 0.3),
-               (3, 3, 0, 0, 1.0), (256, 256, 7, 7, 0.3), (1024, 1024, 7, 7, 0.3)]
+               (3, 3, 0, 0, 1.0), (256, 256, 7, 7, 0.3), (1024, 1024, 7, 7, 0.3),
+               # odd n1 (G4's middle column s1 = (n1-1)/2 belongs to one parity) with a
+               # folded input (n2 % 4 == 0)
+               (37, 64, 5, 5, 0.1), (129, 200, 7, 3, 0.3)]
 
 
 @pytest.mark.parametrize("n1,n2,q1,q2,alpha", SOLVE_CASES)
