@@ -125,3 +125,29 @@ def test_solve_applies_D_and_its_inverse_is_A2_plus_alpha_for_symmetric_psf():
     As = O.ar_matrix_dense(s, n1, n2)
     back = (As @ As + 0.03 * np.eye(n1 * n2)) @ z.ravel()
     np.testing.assert_allclose(back, y.ravel(), atol=1e-11)
+
+
+def test_bench_alpha_is_the_smallest_stable_half_decade_value():
+    """Reading of the unstated alpha (Section 4 leaves it to the user): with tau = 1
+    a frequency of the D-Landweber iteration grows when |h^(w)|^2 / (f_s(w)^2 + alpha)
+    exceeds 2 (|1 - tau r| > 1), f_s the symbol of the symmetrized PSF and h^ the
+    Fourier series of the PSF over both sign flips of w.  For the bench's 15 x 15
+    motion PSF the largest ratio over [0, pi]^2 is below 2 at alpha = 0.3 and above 2
+    at 0.1, so 0.3 is the smallest stable value of the half-decade grid."""
+    from paper_1211_0393_gb300 import workloads as W
+    h = W.psf_config2()
+    q1, q2 = O.psf_support(h)
+    x = np.linspace(0, np.pi, 181)
+    x1, x2 = x[:, None], x[None, :]
+
+    def energy(s1, s2):
+        acc = np.zeros((x.size, x.size), dtype=complex)
+        for a in range(-q1, q1 + 1):
+            for b in range(-q2, q2 + 1):
+                acc += h[a + q1, b + q2] * np.exp(-1j * (a * s1 * x1 + b * s2 * x2))
+        return np.abs(acc) ** 2
+
+    e = np.maximum(energy(1, 1), energy(-1, 1))
+    fs2 = O.symbol(O.symmetrize(h), x, x) ** 2
+    ratio = {alpha: float((e / (fs2 + alpha)).max()) for alpha in (1.0, 0.3, 0.1)}
+    assert ratio[1.0] < ratio[0.3] < 2.0 < ratio[0.1]
