@@ -261,6 +261,23 @@ AR_API ar_status ar_restore_bc(const float* g, const double* psf_host,
                                double* rre_trace, int* best_iter, void* stream);
 
 /*
+ * ar_restore_bc that also returns the residual norms of the iterates:
+ * res_trace[k] = ||g - A x_k||_F for k = 0 .. iters (iters + 1 entries, x_0 the
+ * start), A the blurring matrix of bc (the residual step of eq. DLandweberMeth).
+ * The squares are summed in the blur's residual epilogue, float32 partials of a
+ * thread's rows reduced in float64 (one atomic per CTA), and one more blur of the
+ * final iterate gives k = iters.
+ *   res_trace  host float64, iters + 1 entries, required (AR_ERR_INVALID_ARG if null).
+ * Other arguments, ownership and errors as ar_restore_bc.
+ */
+AR_API ar_status ar_restore_residuals(const float* g, const double* psf_host,
+                                      int n1, int n2, int q1, int q2, double alpha, double tau,
+                                      int iters, int bc, int precondition, int precision,
+                                      const float* x0, const float* f_true, float* x_out,
+                                      double* rre_trace, int* best_iter, double* res_trace,
+                                      void* stream);
+
+/*
  * Batched restoration of many independent images (each with its own size,
  * PSF and alpha).  ar_batch_create builds every image's preconditioner
  * (as ar_symprec_setup) and scratch, then captures the whole restoration of

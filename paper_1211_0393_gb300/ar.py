@@ -33,7 +33,7 @@ EXPORTS = [
     "ar_blur_apply_bc", "ar_reblur_apply_bc", "ar_symprec_setup_bc", "ar_restore_bc",
     "ar_corr_param_count", "ar_corr_create", "ar_corr_params", "ar_corr_destroy",
     "ar_corr_targets", "ar_corr_train", "ar_corr_predict", "ar_symprec_setup_corrected",
-    "ar_restore_prec",
+    "ar_restore_prec", "ar_restore_residuals",
 ]
 
 CORR_GRID = 33      # the correction model's delta table is CORR_GRID x CORR_GRID
@@ -81,6 +81,8 @@ def lib() -> ctypes.CDLL:
             "ar_symprec_setup_bc": [_vp, _i, _i, _i, _i, _d, _i, _i, _vp, ctypes.POINTER(_vp)],
             "ar_restore_bc": [_vp, _vp, _i, _i, _i, _i, _d, _d, _i, _i, _i, _i, _vp, _vp, _vp, _vp,
                               _vp, _vp],
+            "ar_restore_residuals": [_vp, _vp, _i, _i, _i, _i, _d, _d, _i, _i, _i, _i, _vp, _vp, _vp,
+                                     _vp, _vp, _vp, _vp],
             "ar_symprec_setup": [_vp, _i, _i, _i, _i, _d, _vp, ctypes.POINTER(_vp)],
             "ar_symprec_setup_ex": [_vp, _i, _i, _i, _i, _d, _i, _vp, ctypes.POINTER(_vp)],
             "ar_restore_ex": [_vp, _vp, _i, _i, _i, _i, _d, _d, _i, _i, _i, _vp, _vp, _vp, _vp, _vp,
@@ -297,6 +299,38 @@ def ar_restore(g: torch.Tensor, psf, alpha: float, tau: float = 1.0, iters: int 
         ctypes.addressof(best) if want else None,
         _stream(stream)), "ar_restore")
     return x_out, (tr[:iters] if want else None), (best.value if want else None)
+
+
+def ar_restore_residuals(g: torch.Tensor, psf, alpha: float, tau: float = 1.0, iters: int = 20,
+                         precondition: bool = True, x0: torch.Tensor | None = None,
+                         f_true: torch.Tensor | None = None, x_out: torch.Tensor | None = None,
+                         stream=None, precision: str = "fp32", bc: str = "ar"):
+    """``ar_restore`` that also returns the residual norms ``||g - A x_k||_F`` of the
+    iterates, k = 0 .. iters.
+
+    Returns ``(x, rre_trace or None, best_iter or None, residual_norms)``."""
+    _image(g, "g")
+    h = _host_psf(psf)
+    q1, q2 = _support(h.shape)
+    n1, n2 = g.shape
+    if x_out is None:
+        x_out = torch.empty_like(g)
+    _image(x_out, "x_out")
+    want = f_true is not None
+    tr = np.zeros(max(iters, 1), dtype=np.float64) if want else None
+    res = np.zeros(iters + 1, dtype=np.float64)
+    best = _i(0)
+    _check(lib().ar_restore_residuals(
+        g.data_ptr(), h.ctypes.data, n1, n2, q1, q2, float(alpha), float(tau), int(iters),
+        BC[bc], 1 if precondition else 0, PRECISION[precision],
+        _image(x0, "x0").data_ptr() if x0 is not None else None,
+        _image(f_true, "f_true").data_ptr() if f_true is not None else None,
+        x_out.data_ptr(),
+        tr.ctypes.data if want else None,
+        ctypes.addressof(best) if want else None,
+        res.ctypes.data,
+        _stream(stream)), "ar_restore_residuals")
+    return x_out, (tr[:iters] if want else None), (best.value if want else None), res
 
 
 def ar_profile_begin() -> None:

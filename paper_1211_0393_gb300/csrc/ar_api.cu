@@ -226,11 +226,14 @@ ar_status prec_build(const double* psf_host, int q1, int q2, int n1, int n2, dou
 namespace ar {
 
 // The (D-)Landweber loop of ar_restore_bc on validated arguments; with Pext
-// non-null its preconditioner is used instead of building one.
+// non-null its preconditioner is used instead of building one; with res_trace
+// non-null the blur also accumulates ||g - A x_k||^2 (k = 0 .. iters, the last
+// from one more blur of the final iterate).
 static ar_status restore_run(const float* g, const double* psf_host, int n1, int n2, int q1, int q2,
                              double alpha, double tau, int iters, int bc, bool pc, int precision,
                              const float* x0, const float* f_true, float* x_out, double* rre_trace,
-                             int* best_iter, void* stream, const ar_prec* Pext) {
+                             int* best_iter, void* stream, const ar_prec* Pext,
+                             double* res_trace = nullptr) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     set_pool_threshold_once();
     const size_t n = (size_t)n1 * n2;
@@ -246,6 +249,7 @@ static ar_status restore_run(const float* g, const double* psf_host, int n1, int
     int* conv_err = conv_error_flag();
     if (!conv_err) return fail(AR_ERR_CUDA, "stencil error flag unavailable");
     std::vector<double> sums((size_t)iters + 1, 0.0);
+    std::vector<double> rsums(res_trace ? (size_t)iters + 1 : 0, 0.0);
     ar_status st = AR_OK;
     {
         Scratch ws(s);
@@ -255,11 +259,15 @@ static ar_status restore_run(const float* g, const double* psf_host, int n1, int
         st = ws.get(&psf, k);
         if (st == AR_OK) st = ws.get(&r, n);
         if (st == AR_OK) st = ws.get(&dsum, (size_t)iters + 1);
+        double* dres = nullptr;
+        if (st == AR_OK && res_trace) st = ws.get(&dres, (size_t)iters + 1);
         if (st == AR_OK) st = ws.get(&dbad, 1);
         if (st == AR_OK) {
             cudaError_t e = cudaMemcpyAsync(psf, h32.data(), k * sizeof(float),
                                             cudaMemcpyHostToDevice, s);
             if (e == cudaSuccess) e = cudaMemsetAsync(dsum, 0, ((size_t)iters + 1) * sizeof(double), s);
+            if (e == cudaSuccess && dres)
+                e = cudaMemsetAsync(dres, 0, ((size_t)iters + 1) * sizeof(double), s);
             if (e == cudaSuccess) e = cudaMemsetAsync(dbad, 0, sizeof(unsigned long long), s);
             if (e == cudaSuccess) e = cudaMemsetAsync(conv_err, 0, sizeof(int), s);
             if (e == cudaSuccess) {
@@ -309,6 +317,7 @@ static ar_status restore_run(const float* g, const double* psf_host, int n1, int
         reblur.f = f_true;
         for (int it = 0; st == AR_OK && it < iters; ++it) {
             // the RRE numerator ||x_{k+1} - f||^2 is accumulated by the kernel that writes x_{k+1}
+            blur.sumsq = dres ? dres + it : nullptr;             // ||r||^2 when requested
             st = conv_launch(blur, s);                           // r = g - A x_k
             if (!pc) reblur.sumsq = f_true ? dsum + it : nullptr;
             if (st == AR_OK) st = conv_launch(reblur, s);        // z = A' r  (or x += tau A' r)
@@ -317,11 +326,18 @@ static ar_status restore_run(const float* g, const double* psf_host, int n1, int
                                      DOUT_AXPY, (float)tau, s, f_true,
                                      f_true ? dsum + it : nullptr);
         }
+        if (st == AR_OK && dres) {                               // ||g - A x_iters||^2
+            blur.sumsq = dres + iters;
+            st = conv_launch(blur, s);
+        }
         if (st == AR_OK) st = count_nonfinite(x_out, n, dbad, s);
         if (st == AR_OK) {
             cudaError_t e = cudaMemcpyAsync(sums.data(), dsum, sums.size() * sizeof(double),
                                             cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, dbad, sizeof(bad), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess && dres)
+                e = cudaMemcpyAsync(rsums.data(), dres, rsums.size() * sizeof(double),
+                                    cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess && PP)
                 e = cudaMemcpyAsync(&timeout, transform_error_flag(PP->plan), sizeof(int),
                                     cudaMemcpyDeviceToHost, s);
@@ -334,6 +350,8 @@ static ar_status restore_run(const float* g, const double* psf_host, int n1, int
     if (P) prec_release(P, s);       // after the synchronize above: no work pending
     if (st != AR_OK) return st;
     if (e != cudaSuccess) return cuda_fail(e, "restore");
+    if (res_trace)
+        for (int k = 0; k <= iters; ++k) res_trace[k] = std::sqrt(rsums[(size_t)k]);
     if (f_true) {
         const double fn = sums[(size_t)iters];
         int best = 0;
@@ -546,6 +564,37 @@ ar_status ar_restore_bc(const float* g, const double* psf_host, int n1, int n2, 
         return fail(AR_ERR_ALIAS, "x0 partially overlaps x_out");
     return restore_run(g, psf_host, n1, n2, q1, q2, alpha, tau, iters, bc, pc, precision, x0, f_true,
                        x_out, rre_trace, best_iter, stream, nullptr);
+}
+
+ar_status ar_restore_residuals(const float* g, const double* psf_host, int n1, int n2, int q1,
+                               int q2, double alpha, double tau, int iters, int bc,
+                               int precondition, int precision, const float* x0,
+                               const float* f_true, float* x_out, double* rre_trace,
+                               int* best_iter, double* res_trace, void* stream) {
+    if (!res_trace) return fail(AR_ERR_INVALID_ARG, "null pointer argument (res_trace)");
+    if (!g || !psf_host || !x_out) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
+    if (precision != AR_PRECISION_FP32 && precision != AR_PRECISION_BF16X2)
+        return fail(AR_ERR_INVALID_ARG, "unknown precision %d", precision);
+    AR_TRY(check_bc(bc));
+    const bool pc = precondition != 0;
+    AR_TRY(check_image_sizes(n1, n2, pc ? 3 : 1));
+    AR_TRY(check_support(n1, n2, q1, q2, pc && bc == AR_BC_ANTIREFLECTIVE ? 3 : 1));
+    if (iters < 0) return fail(AR_ERR_INVALID_ARG, "iters must be >= 0 (got %d)", iters);
+    if (!(tau > 0.0) || !std::isfinite(tau))
+        return fail(AR_ERR_INVALID_ARG, "tau must be finite and > 0 (got %g)", tau);
+    if (pc && (!(alpha > 0.0) || !std::isfinite(alpha)))
+        return fail(AR_ERR_INVALID_ARG, "alpha must be finite and > 0 (got %g)", alpha);
+    if ((rre_trace || best_iter) && !f_true)
+        return fail(AR_ERR_INVALID_ARG, "rre_trace/best_iter need f_true");
+    AR_TRY(check_psf_host(psf_host, q1, q2));
+    const size_t n = (size_t)n1 * n2;
+    const size_t nb = n * sizeof(float);
+    if (overlaps(x_out, nb, g, nb)) return fail(AR_ERR_ALIAS, "x_out overlaps g");
+    if (f_true && overlaps(x_out, nb, f_true, nb)) return fail(AR_ERR_ALIAS, "x_out overlaps f_true");
+    if (x0 && x0 != x_out && overlaps(x0, nb, x_out, nb))
+        return fail(AR_ERR_ALIAS, "x0 partially overlaps x_out");
+    return restore_run(g, psf_host, n1, n2, q1, q2, alpha, tau, iters, bc, pc, precision, x0, f_true,
+                       x_out, rre_trace, best_iter, stream, nullptr, res_trace);
 }
 
 ar_status ar_restore_prec(const ar_prec* P, const float* g, const double* psf_host, double tau,

@@ -101,12 +101,18 @@ __device__ __forceinline__ void split3_store(uint16_t* planes, size_t pstride, s
     planes[2 * pstride + off] = __bfloat16_as_ushort(p2);
 }
 
-// Writes one output; returns (x_new - f)^2 for CONV_AXPY with a true image, else 0.
+// Writes one output; returns (x_new - f)^2 for CONV_AXPY with a true image, r^2
+// for CONV_RESIDUAL when the residual norm is accumulated (sumsq set), else 0.
 __device__ __forceinline__ float conv_epilogue(const ConvArgs& a, int row, int col, float v) {
     const size_t o = (size_t)row * a.n2 + col;
     switch (a.mode) {
         case CONV_STORE: a.out[o] = v; break;
-        case CONV_RESIDUAL: a.out[o] = __ldg(a.aux + o) - v; break;
+        case CONV_RESIDUAL: {
+            const float r = __ldg(a.aux + o) - v;
+            a.out[o] = r;
+            if (a.sumsq) return r * r;
+            break;
+        }
         case CONV_AXPY: {
             const float xn = fmaf(a.tau, v, a.out[o]);
             a.out[o] = xn;
@@ -276,8 +282,13 @@ __device__ __forceinline__ float strip_epilogue(const ConvArgs& a, int row0, int
             for (int r = 0; r < EB; ++r)
                 gv[r] = c + r < nr ? __ldg(a.aux + o0 + (size_t)r * a.n2) : 0.f;
 #pragma unroll
-            for (int r = 0; r < EB; ++r)
-                if (c + r < nr) a.out[o0 + (size_t)r * a.n2] = gv[r] - acc[c + r];
+            for (int r = 0; r < EB; ++r) {
+                if (c + r < nr) {
+                    const float rv = gv[r] - acc[c + r];
+                    a.out[o0 + (size_t)r * a.n2] = rv;
+                    if (a.sumsq) sq += rv * rv;          // ||g - A x||^2 when requested
+                }
+            }
         } else {
             float xv[EB], fv[EB];
 #pragma unroll

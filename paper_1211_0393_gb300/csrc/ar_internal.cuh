@@ -77,7 +77,8 @@ struct ConvArgs {
     int mode;
     float tau;
     const float* f;      // CONV_AXPY: true image or null
-    double* sumsq;       // CONV_AXPY with f: += sum (x_new - f)^2 (float64)
+    double* sumsq;       // CONV_AXPY with f: += sum (x_new - f)^2; CONV_RESIDUAL:
+                         // += sum r^2 (float64, float32 per-thread partials)
     int bc;              // AR_BC_ANTIREFLECTIVE / AR_BC_REFLECTIVE / AR_BC_PERIODIC
     int fold;            // CONV_SPLIT3: write the even/odd fold along the columns,
                          // y+_t = y_t + y_{n2-1-t} at column t and y-_t at column

@@ -171,3 +171,19 @@ def test_correction_validation(L):
                                         ctypes.byref(out)) == 1
     assert L.ar_restore_prec(None, FAKE, h3.ctypes.data, 1.0, 3, None, None, FAKE * 64, None,
                              None, None) == 1
+
+
+def test_residual_restore_validation(L):
+    hp = _psf(2, 2).ctypes.data
+    res = np.zeros(4)
+
+    def call(x=FAKE * 64, r=res.ctypes.data, bc=0, pc=1, q1=2, tr=None):
+        return L.ar_restore_residuals(FAKE, hp, 16, 16, q1, 2, 0.1, 1.0, 3, bc, pc, 0, None,
+                                      None, x, tr, None, r, None)
+
+    assert call(r=None) == 1                      # the residual trace is the point of the call
+    assert call(x=None) == 1
+    assert call(bc=5) == 1
+    assert call(tr=FAKE) == 1                     # RRE trace without f_true
+    assert call(x=FAKE + 64) == 2                 # x_out overlaps g
+    assert call(q1=14) == 1                       # q > n-3 with the preconditioner

@@ -293,6 +293,36 @@ def test_restore_past_one_wave_matches_oracle(ar):
         assert_trace_close(tr, to, tol)
 
 
+@pytest.mark.parametrize("pc,alpha,bc", [(True, 0.03, "ar"), (False, 0.0, "ar"),
+                                         (True, 0.05, "reflective")])
+def test_residual_norms_match_oracle(ar, pc, alpha, bc):
+    """||g - A x_k||_F of every iterate k = 0 .. iters (the residual step of eq.
+    DLandweberMeth), against the oracle's iterates.  x_k differs from the oracle's
+    by at most tol ||x_k|| (rel-L2 per iterate), so the norms differ by at most
+    ||A|| tol ||x_k|| plus the float32 rounding of r."""
+    h = W.psf_config1()
+    g, f = _workload(64, h, "blocks", 0, 0.01)
+    iters = 6
+    x, tr, best, res = ar.ar_restore_residuals(dev(g), h, alpha, 1.0, iters, pc, f_true=dev(f),
+                                               bc=bc)
+    assert res.shape == (iters + 1,)
+    g64 = g.astype(np.float64)
+    blur = O.ar_blur if bc == "ar" else (lambda v, k_: O.blur_bc(v, k_, O.BC_REFLECTIVE))
+    tol = tol_alpha(alpha) if pc else 1e-5
+    for k in range(iters + 1):
+        if k == 0:
+            xk = np.zeros_like(g64)
+        elif bc == "ar":
+            xk = O.restore(g64, h, alpha, 1.0, k, pc)[0]
+        else:
+            xk = O.restore_bc(g64, h, alpha, O.BC_REFLECTIVE, 1.0, k, pc)[0]
+        want = np.linalg.norm(g64 - blur(xk, h))
+        assert abs(res[k] - want) <= 2 * tol * np.linalg.norm(xk) + 1e-5 * want, (k, res[k], want)
+    xo, _, _ = (O.restore(g64, h, alpha, 1.0, iters, pc) if bc == "ar"
+                else O.restore_bc(g64, h, alpha, O.BC_REFLECTIVE, 1.0, iters, pc))
+    assert rel_l2(x.cpu().numpy(), xo) <= tol
+
+
 def test_restore_warm_start_and_in_place(ar):
     h = W.psf_config1()
     g, f = _workload(64, h, "blocks", 0, 0.01)
