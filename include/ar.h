@@ -220,7 +220,8 @@ AR_API ar_status ar_restore(const float* g, const double* psf_host,
  *
  * Its scratch (the residual image, the float32 PSF copy and the float64 RRE
  * accumulators) lives in one file-scope static device array of about 4.1 MiB
- * that every GPU loading this library keeps until the process exits; no
+ * that every GPU loading this library keeps until the process exits; the
+ * stencils' bounded-wait flag is a static device int as well.  No
  * cudaMalloc, cudaFree or other allocating routine is called.  Limits:
  * n1*n2 <= AR_STATIC_MAX_PIXELS, (2q1+1)(2q2+1) <= AR_STATIC_MAX_PSF,
  * iters <= AR_STATIC_MAX_ITERS; larger requests return AR_ERR_INVALID_ARG
@@ -230,6 +231,8 @@ AR_API ar_status ar_restore(const float* g, const double* psf_host,
  * share the array and the call clears what must start at zero; calls whose
  * GPU work overlaps (different streams or host threads) race.
  * Synchronizes `stream` before returning.
+ * Errors: as ar_restore, plus AR_ERR_TIMEOUT when a stencil's bounded wait
+ * for its halo tile gave up (x_out is then incomplete).
  */
 #define AR_STATIC_MAX_PIXELS (1u << 20)
 #define AR_STATIC_MAX_PSF 4096u
@@ -413,6 +416,30 @@ AR_API ar_status ar_profile_end(double* ms, unsigned long long* launches, int nk
 /* Number of kernels this library has launched in this process (all devices,
  * all threads), for launch accounting by benchmarks. */
 AR_API unsigned long long ar_kernel_launches(void);
+
+/*
+ * Failure-detection controls (no counterpart in the paper; they exist so that
+ * the library's error paths can be tested without faulting a GPU).
+ *
+ * ar_set_stencil_wait_polls: the number of mbarrier polls a stencil kernel
+ * spends waiting for a halo tile before it gives up, on the current device.
+ * A kernel that gives up waits (with the default bound) for its copies still
+ * in flight, records the failure in a device flag and returns; ar_restore*,
+ * ar_restore_prec and ar_restore_plain_static then return AR_ERR_TIMEOUT.
+ * polls = 0 makes every wait give up at once; AR_DEFAULT_WAIT_POLLS restores
+ * the default.  Synchronous (a copy to a device variable); errors: AR_ERR_CUDA.
+ *
+ * ar_inject_alloc_failures: of the next device allocations of the
+ * restoration scratch and of the preconditioner buffers (ar_restore*,
+ * ar_restore_prec, ar_symprec_setup*), the first `skip` succeed and the
+ * following `count` fail as if the allocator had returned
+ * cudaErrorMemoryAllocation, without calling it; the failing call returns
+ * AR_ERR_ALLOC and frees what it had allocated.  count <= 0 clears the
+ * injection.  Process-wide, all threads.
+ */
+#define AR_DEFAULT_WAIT_POLLS (1u << 24)
+AR_API ar_status ar_set_stencil_wait_polls(unsigned polls);
+AR_API void ar_inject_alloc_failures(int skip, int count);
 
 /* Library version string. */
 AR_API const char* ar_version(void);

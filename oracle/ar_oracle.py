@@ -455,20 +455,23 @@ def rre(x: np.ndarray, f: np.ndarray) -> float:
     return float(np.linalg.norm(x - f) / np.linalg.norm(f))
 
 
-def restore(g, h, alpha, tau=1.0, iters=20, precondition=True, x0=None, f_true=None):
+def restore(g, h, alpha, tau=1.0, iters=20, precondition=True, x0=None, f_true=None,
+            each=None):
     """(D-)Landweber with reblurring: eqs. LandweberMeth / DLandweberMeth.
 
     ``x_{k+1} = x_k + tau D A'(g - A x_k)``, ``D = I`` when ``precondition`` is
     false.  Returns ``(x, rre_trace, best_iter)``; ``rre_trace[k]`` is the RRE
     of ``x_{k+1}`` and ``best_iter`` the first ``k+1`` attaining the minimum
-    (the tables' IT), both ``None`` without ``f_true``.
+    (the tables' IT), both ``None`` without ``f_true``.  ``each(k, x_k)``, when
+    given, is called with every iterate ``k = 1 .. iters`` (for per-iterate
+    comparisons; it does not change the iteration).
     """
     g = np.asarray(g, dtype=np.float64)
     n1, n2 = g.shape
     prec = symprec_setup(h, n1, n2, alpha) if precondition else None
     x = np.zeros((n1, n2)) if x0 is None else np.array(x0, dtype=np.float64)
     trace = [] if f_true is not None else None
-    for _ in range(iters):
+    for k in range(1, iters + 1):
         r = g - ar_blur(x, h)
         z = ar_reblur(r, h)
         if precondition:
@@ -476,6 +479,8 @@ def restore(g, h, alpha, tau=1.0, iters=20, precondition=True, x0=None, f_true=N
         x = x + tau * z
         if trace is not None:
             trace.append(rre(x, f_true))
+        if each is not None:
+            each(k, x)
     best = None
     if trace is not None and trace:
         best = int(np.argmin(np.asarray(trace))) + 1

@@ -33,8 +33,11 @@ EXPORTS = [
     "ar_blur_apply_bc", "ar_reblur_apply_bc", "ar_symprec_setup_bc", "ar_restore_bc",
     "ar_corr_param_count", "ar_corr_create", "ar_corr_params", "ar_corr_destroy",
     "ar_corr_targets", "ar_corr_train", "ar_corr_predict", "ar_symprec_setup_corrected",
-    "ar_restore_prec", "ar_restore_residuals",
+    "ar_restore_prec", "ar_restore_residuals", "ar_set_stencil_wait_polls",
+    "ar_inject_alloc_failures",
 ]
+
+DEFAULT_WAIT_POLLS = 1 << 24
 
 CORR_GRID = 33      # the correction model's delta table is CORR_GRID x CORR_GRID
 
@@ -114,6 +117,10 @@ def lib() -> ctypes.CDLL:
         L.ar_batch_results.restype = _i
         L.ar_batch_destroy.argtypes = [_vp]
         L.ar_batch_destroy.restype = None
+        L.ar_set_stencil_wait_polls.argtypes = [ctypes.c_uint]
+        L.ar_set_stencil_wait_polls.restype = _i
+        L.ar_inject_alloc_failures.argtypes = [_i, _i]
+        L.ar_inject_alloc_failures.restype = None
         L.ar_profile_begin.argtypes = []
         L.ar_profile_begin.restype = _i
         L.ar_profile_end.argtypes = [_vp, _vp, _i]
@@ -523,6 +530,18 @@ def ar_restore_prec(P: Prec, g: torch.Tensor, psf, tau: float = 1.0, iters: int 
         x_out.data_ptr(), tr.ctypes.data if want else None,
         ctypes.addressof(best) if want else None, _stream(stream)), "ar_restore_prec")
     return x_out, (tr[:iters] if want else None), (best.value if want else None)
+
+
+def set_stencil_wait_polls(polls: int = DEFAULT_WAIT_POLLS) -> None:
+    """Polls of the stencils' halo-tile waits before they give up (failure-detection
+    tests; ``0`` makes every wait give up, the default restores the normal bound)."""
+    _check(lib().ar_set_stencil_wait_polls(int(polls)), "ar_set_stencil_wait_polls")
+
+
+def inject_alloc_failures(count: int, skip: int = 0) -> None:
+    """Let the library's next ``skip`` scratch / preconditioner allocations succeed and
+    make the ``count`` after them fail (``count=0`` clears the injection)."""
+    lib().ar_inject_alloc_failures(int(skip), int(count))
 
 
 def kernel_launches() -> int:

@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -31,6 +32,25 @@ ar_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 static std::atomic<unsigned long long> g_launches{0};
+// Injected allocation failures: `skip` more allocations succeed, then `fail` fail.
+static std::mutex g_inject_mu;
+static int g_inject_skip = 0, g_inject_fail = 0;
+
+cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t s) {
+    {
+        std::lock_guard<std::mutex> lock(g_inject_mu);
+        if (g_inject_fail > 0) {
+            if (g_inject_skip > 0) {
+                --g_inject_skip;
+            } else {
+                --g_inject_fail;
+                *p = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+        }
+    }
+    return cudaMallocAsync(p, bytes, s);
+}
 
 void count_launch(unsigned k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
@@ -109,7 +129,7 @@ struct Scratch {
     template <class T>
     ar_status get(T** p, size_t count) {
         void* q = nullptr;
-        cudaError_t e = cudaMallocAsync(&q, count * sizeof(T) + 16, s);
+        cudaError_t e = dev_malloc_async(&q, count * sizeof(T) + 16, s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (scratch)");
         ptrs.push_back(q);
         *p = static_cast<T*>(q);
@@ -186,14 +206,14 @@ ar_status prec_build(const double* psf_host, int q1, int q2, int n1, int n2, dou
             if (e != cudaSuccess) st = cuda_fail(e, "PSF upload");
         }
         if (st == AR_OK && keep64) {
-            if (cudaMallocAsync((void**)&P->lam64, n * sizeof(double), s) != cudaSuccess ||
-                cudaMallocAsync((void**)&P->d64, n * sizeof(double), s) != cudaSuccess)
+            if (dev_malloc_async((void**)&P->lam64, n * sizeof(double), s) != cudaSuccess ||
+                dev_malloc_async((void**)&P->d64, n * sizeof(double), s) != cudaSuccess)
                 st = fail(AR_ERR_ALLOC, "eigenvalue buffers");
         }
-        if (st == AR_OK && cudaMallocAsync((void**)&P->d32, n * sizeof(float), s) != cudaSuccess)
+        if (st == AR_OK && dev_malloc_async((void**)&P->d32, n * sizeof(float), s) != cudaSuccess)
             st = fail(AR_ERR_ALLOC, "filter buffer");
         if (st == AR_OK && bc == AR_BC_PERIODIC &&
-            cudaMallocAsync((void**)&P->d32_odd, n * sizeof(float), s) != cudaSuccess)
+            dev_malloc_async((void**)&P->d32_odd, n * sizeof(float), s) != cudaSuccess)
             st = fail(AR_ERR_ALLOC, "odd filter buffer");
         double* delta = nullptr;
         if (st == AR_OK && correction) {
@@ -246,8 +266,7 @@ static ar_status restore_run(const float* g, const double* psf_host, int n1, int
     const ar_prec* PP = Pext;
     unsigned long long bad = 0;
     int timeout = 0, conv_timeout = 0;
-    int* conv_err = conv_error_flag();
-    if (!conv_err) return fail(AR_ERR_CUDA, "stencil error flag unavailable");
+    int* conv_err = nullptr;
     std::vector<double> sums((size_t)iters + 1, 0.0);
     std::vector<double> rsums(res_trace ? (size_t)iters + 1 : 0, 0.0);
     ar_status st = AR_OK;
@@ -262,6 +281,8 @@ static ar_status restore_run(const float* g, const double* psf_host, int n1, int
         double* dres = nullptr;
         if (st == AR_OK && res_trace) st = ws.get(&dres, (size_t)iters + 1);
         if (st == AR_OK) st = ws.get(&dbad, 1);
+        if (st == AR_OK && !(conv_err = conv_error_flag()))
+            st = fail(AR_ERR_CUDA, "stencil error flag unavailable");
         if (st == AR_OK) {
             cudaError_t e = cudaMemcpyAsync(psf, h32.data(), k * sizeof(float),
                                             cudaMemcpyHostToDevice, s);
@@ -372,6 +393,36 @@ static ar_status restore_run(const float* g, const double* psf_host, int n1, int
     return AR_OK;
 }
 
+// Argument checks shared by every entry point that takes ar_restore_bc's
+// arguments, so that they accept exactly the same inputs.
+static ar_status validate_restore_args(const float* g, const double* psf_host, int n1, int n2,
+                                       int q1, int q2, double alpha, double tau, int iters, int bc,
+                                       int precondition, int precision, const float* x0,
+                                       const float* f_true, const float* x_out,
+                                       const double* rre_trace, const int* best_iter) {
+    if (!g || !psf_host || !x_out) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
+    if (precision != AR_PRECISION_FP32 && precision != AR_PRECISION_BF16X2)
+        return fail(AR_ERR_INVALID_ARG, "unknown precision %d", precision);
+    AR_TRY(check_bc(bc));
+    const bool pc = precondition != 0;
+    AR_TRY(check_image_sizes(n1, n2, pc ? 3 : 1));
+    AR_TRY(check_support(n1, n2, q1, q2, pc && bc == AR_BC_ANTIREFLECTIVE ? 3 : 1));
+    if (iters < 0) return fail(AR_ERR_INVALID_ARG, "iters must be >= 0 (got %d)", iters);
+    if (!(tau > 0.0) || !std::isfinite(tau))
+        return fail(AR_ERR_INVALID_ARG, "tau must be finite and > 0 (got %g)", tau);
+    if (pc && (!(alpha > 0.0) || !std::isfinite(alpha)))
+        return fail(AR_ERR_INVALID_ARG, "alpha must be finite and > 0 (got %g)", alpha);
+    if ((rre_trace || best_iter) && !f_true)
+        return fail(AR_ERR_INVALID_ARG, "rre_trace/best_iter need f_true");
+    AR_TRY(check_psf_host(psf_host, q1, q2));
+    const size_t nb = (size_t)n1 * n2 * sizeof(float);
+    if (overlaps(x_out, nb, g, nb)) return fail(AR_ERR_ALIAS, "x_out overlaps g");
+    if (f_true && overlaps(x_out, nb, f_true, nb)) return fail(AR_ERR_ALIAS, "x_out overlaps f_true");
+    if (x0 && x0 != x_out && overlaps(x0, nb, x_out, nb))
+        return fail(AR_ERR_ALIAS, "x0 partially overlaps x_out");
+    return AR_OK;
+}
+
 }  // namespace ar
 
 extern "C" {
@@ -396,6 +447,14 @@ const char* ar_last_error_detail(void) { return g_detail; }
 const char* ar_version(void) { return "ar-gb300 0.1 (sm_103a)"; }
 
 unsigned long long ar_kernel_launches(void) { return g_launches.load(); }
+
+ar_status ar_set_stencil_wait_polls(unsigned polls) { return conv_set_wait_polls(polls); }
+
+void ar_inject_alloc_failures(int skip, int count) {
+    std::lock_guard<std::mutex> lock(g_inject_mu);
+    g_inject_skip = skip > 0 ? skip : 0;
+    g_inject_fail = count > 0 ? count : 0;
+}
 
 ar_status ar_blur_apply(const float* x, float* y, int n1, int n2, const float* psf, int q1, int q2,
                         void* stream) {
@@ -541,29 +600,10 @@ ar_status ar_restore_bc(const float* g, const double* psf_host, int n1, int n2, 
                         double alpha, double tau, int iters, int bc, int precondition,
                         int precision, const float* x0, const float* f_true, float* x_out,
                         double* rre_trace, int* best_iter, void* stream) {
-    if (!g || !psf_host || !x_out) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
-    if (precision != AR_PRECISION_FP32 && precision != AR_PRECISION_BF16X2)
-        return fail(AR_ERR_INVALID_ARG, "unknown precision %d", precision);
-    AR_TRY(check_bc(bc));
-    const bool pc = precondition != 0;
-    AR_TRY(check_image_sizes(n1, n2, pc ? 3 : 1));
-    AR_TRY(check_support(n1, n2, q1, q2, pc && bc == AR_BC_ANTIREFLECTIVE ? 3 : 1));
-    if (iters < 0) return fail(AR_ERR_INVALID_ARG, "iters must be >= 0 (got %d)", iters);
-    if (!(tau > 0.0) || !std::isfinite(tau))
-        return fail(AR_ERR_INVALID_ARG, "tau must be finite and > 0 (got %g)", tau);
-    if (pc && (!(alpha > 0.0) || !std::isfinite(alpha)))
-        return fail(AR_ERR_INVALID_ARG, "alpha must be finite and > 0 (got %g)", alpha);
-    if ((rre_trace || best_iter) && !f_true)
-        return fail(AR_ERR_INVALID_ARG, "rre_trace/best_iter need f_true");
-    AR_TRY(check_psf_host(psf_host, q1, q2));
-    const size_t n = (size_t)n1 * n2;
-    const size_t nb = n * sizeof(float);
-    if (overlaps(x_out, nb, g, nb)) return fail(AR_ERR_ALIAS, "x_out overlaps g");
-    if (f_true && overlaps(x_out, nb, f_true, nb)) return fail(AR_ERR_ALIAS, "x_out overlaps f_true");
-    if (x0 && x0 != x_out && overlaps(x0, nb, x_out, nb))
-        return fail(AR_ERR_ALIAS, "x0 partially overlaps x_out");
-    return restore_run(g, psf_host, n1, n2, q1, q2, alpha, tau, iters, bc, pc, precision, x0, f_true,
-                       x_out, rre_trace, best_iter, stream, nullptr);
+    AR_TRY(validate_restore_args(g, psf_host, n1, n2, q1, q2, alpha, tau, iters, bc, precondition,
+                                 precision, x0, f_true, x_out, rre_trace, best_iter));
+    return restore_run(g, psf_host, n1, n2, q1, q2, alpha, tau, iters, bc, precondition != 0,
+                       precision, x0, f_true, x_out, rre_trace, best_iter, stream, nullptr);
 }
 
 ar_status ar_restore_residuals(const float* g, const double* psf_host, int n1, int n2, int q1,
@@ -572,29 +612,11 @@ ar_status ar_restore_residuals(const float* g, const double* psf_host, int n1, i
                                const float* f_true, float* x_out, double* rre_trace,
                                int* best_iter, double* res_trace, void* stream) {
     if (!res_trace) return fail(AR_ERR_INVALID_ARG, "null pointer argument (res_trace)");
-    if (!g || !psf_host || !x_out) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
-    if (precision != AR_PRECISION_FP32 && precision != AR_PRECISION_BF16X2)
-        return fail(AR_ERR_INVALID_ARG, "unknown precision %d", precision);
-    AR_TRY(check_bc(bc));
-    const bool pc = precondition != 0;
-    AR_TRY(check_image_sizes(n1, n2, pc ? 3 : 1));
-    AR_TRY(check_support(n1, n2, q1, q2, pc && bc == AR_BC_ANTIREFLECTIVE ? 3 : 1));
-    if (iters < 0) return fail(AR_ERR_INVALID_ARG, "iters must be >= 0 (got %d)", iters);
-    if (!(tau > 0.0) || !std::isfinite(tau))
-        return fail(AR_ERR_INVALID_ARG, "tau must be finite and > 0 (got %g)", tau);
-    if (pc && (!(alpha > 0.0) || !std::isfinite(alpha)))
-        return fail(AR_ERR_INVALID_ARG, "alpha must be finite and > 0 (got %g)", alpha);
-    if ((rre_trace || best_iter) && !f_true)
-        return fail(AR_ERR_INVALID_ARG, "rre_trace/best_iter need f_true");
-    AR_TRY(check_psf_host(psf_host, q1, q2));
-    const size_t n = (size_t)n1 * n2;
-    const size_t nb = n * sizeof(float);
-    if (overlaps(x_out, nb, g, nb)) return fail(AR_ERR_ALIAS, "x_out overlaps g");
-    if (f_true && overlaps(x_out, nb, f_true, nb)) return fail(AR_ERR_ALIAS, "x_out overlaps f_true");
-    if (x0 && x0 != x_out && overlaps(x0, nb, x_out, nb))
-        return fail(AR_ERR_ALIAS, "x0 partially overlaps x_out");
-    return restore_run(g, psf_host, n1, n2, q1, q2, alpha, tau, iters, bc, pc, precision, x0, f_true,
-                       x_out, rre_trace, best_iter, stream, nullptr, res_trace);
+    AR_TRY(validate_restore_args(g, psf_host, n1, n2, q1, q2, alpha, tau, iters, bc, precondition,
+                                 precision, x0, f_true, x_out, rre_trace, best_iter));
+    return restore_run(g, psf_host, n1, n2, q1, q2, alpha, tau, iters, bc, precondition != 0,
+                       precision, x0, f_true, x_out, rre_trace, best_iter, stream, nullptr,
+                       res_trace);
 }
 
 ar_status ar_restore_prec(const ar_prec* P, const float* g, const double* psf_host, double tau,

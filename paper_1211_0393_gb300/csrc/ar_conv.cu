@@ -399,6 +399,10 @@ conv_fast_kernel(const ConvArgs a) {
 }
 
 __device__ int g_conv_timeout;
+// Polls of a stencil's wait for its halo tile before it gives up (settable
+// from the host for failure-detection tests; the drain of copies still in
+// flight after a give-up always waits the full tc::kMaxPolls).
+__device__ uint32_t g_conv_wait_polls = tc::kMaxPolls;
 
 // Halo tile of the TMA path: the box starts PADL >= Q columns left of the
 // tile (a multiple of 4, so the box's x coordinate is 16-byte aligned) and
@@ -455,13 +459,14 @@ conv_tma_kernel(const __grid_constant__ CUtensorMap tmx, const ConvArgs a, int n
         tma_load_2d(smem_u32(buffer(i % NBUF)), &tmx, c0 - T::PADL, r0 - Q, bar);
     };
     const int nmine = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const uint32_t polls = g_conv_wait_polls;
     if (tid == 0)
         for (int i = 0; i < NBUF - 1 && i < nmine; ++i) request(i);
     int li = 0;
     bool failed = false;
     for (; li < nmine; ++li) {
         if (tid == 0 && li + NBUF - 1 < nmine) request(li + NBUF - 1);   // buffer of tile li-1
-        const bool ok = mbar_wait(bar0 + 8u * (li % NBUF), (li / NBUF) & 1);
+        const bool ok = mbar_wait(bar0 + 8u * (li % NBUF), (li / NBUF) & 1, polls);
         if (__syncthreads_or(!ok)) {
             failed = true;
             break;
@@ -478,8 +483,9 @@ conv_tma_kernel(const __grid_constant__ CUtensorMap tmx, const ConvArgs a, int n
     if (!a.early_trigger) pdl_trigger();
     if (failed && tid == 0) {
         atomicExch(&g_conv_timeout, 1);
-        // copies still in flight (tiles li + 1 .. li + NBUF - 1): wait for them (bounded)
-        for (int i = li + 1; i < li + NBUF && i < nmine; ++i)
+        // copies possibly still in flight (tiles li .. li + NBUF - 1): wait for
+        // them (bounded) before the CTA's shared memory is released
+        for (int i = li; i < li + NBUF && i < nmine; ++i)
             mbar_wait(bar0 + 8u * (i % NBUF), (i / NBUF) & 1);
     }
 }
@@ -539,13 +545,14 @@ conv_tma_fold_kernel(const __grid_constant__ CUtensorMap tmx, const ConvArgs a, 
         tma_load_2d(smem_u32(buffer(i % NBUF, 1)), &tmx, cm - T::PADL, r0 - Q, bar);
     };
     const int nmine = blockIdx.x < nunits ? (nunits - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const uint32_t polls = g_conv_wait_polls;
     if (tid == 0)
         for (int i = 0; i < NBUF - 1 && i < nmine; ++i) request(i);
     int li = 0;
     bool failed = false;
     for (; li < nmine; ++li) {
         if (tid == 0 && li + NBUF - 1 < nmine) request(li + NBUF - 1);
-        const bool ok = mbar_wait(bar0 + 8u * (li % NBUF), (li / NBUF) & 1);
+        const bool ok = mbar_wait(bar0 + 8u * (li % NBUF), (li / NBUF) & 1, polls);
         if (__syncthreads_or(!ok)) {
             failed = true;
             break;
@@ -582,7 +589,7 @@ conv_tma_fold_kernel(const __grid_constant__ CUtensorMap tmx, const ConvArgs a, 
     }
     if (failed && tid == 0) {
         atomicExch(&g_conv_timeout, 1);
-        for (int i = li + 1; i < li + NBUF && i < nmine; ++i)
+        for (int i = li; i < li + NBUF && i < nmine; ++i)
             mbar_wait(bar0 + 8u * (i % NBUF), (i / NBUF) & 1);
     }
 }
@@ -755,6 +762,11 @@ int* conv_error_flag() {
         if (cudaGetSymbolAddress(&q, g_conv_timeout) == cudaSuccess) p[dev] = static_cast<int*>(q);
     }
     return p[dev];
+}
+
+ar_status conv_set_wait_polls(unsigned polls) {
+    AR_CUDA(cudaMemcpyToSymbol(g_conv_wait_polls, &polls, sizeof(polls)));
+    return AR_OK;
 }
 
 ar_status conv_launch(const ConvArgs& a, cudaStream_t s) {

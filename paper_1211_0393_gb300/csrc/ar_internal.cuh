@@ -98,6 +98,9 @@ ar_status conv_launch(const ConvArgs& a, cudaStream_t stream);
 // (cleared by the caller that reads it).
 int* conv_error_flag();
 
+// Sets the polls of the stencils' halo-tile waits on the current device.
+ar_status conv_set_wait_polls(unsigned polls);
+
 // cuTensorMapEncodeTiled from the driver (null if unavailable), as void*.
 void* tensor_map_encoder();
 
@@ -176,6 +179,11 @@ ar_status reduce_sq(const float* f, size_t n, double* acc, cudaStream_t s);
 ar_status count_nonfinite(const float* x, size_t n, unsigned long long* cnt, cudaStream_t s);
 
 int sm_count();
+
+// cudaMallocAsync of the restoration's scratch and preconditioner buffers; fails
+// with cudaErrorMemoryAllocation without calling the allocator while failures
+// injected by ar_inject_alloc_failures() remain.
+cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t s);
 
 // ------------------------------------------------------ shared host helpers
 bool overlaps(const void* a, size_t abytes, const void* b, size_t bbytes);

@@ -104,6 +104,9 @@ extern "C" ar_status ar_restore_plain_static(const float* g, const double* psf_h
 
     unsigned char* base = nullptr;
     AR_TRY(scratch_base(&base));
+    // the stencils' bounded-wait flag is a static device int too (no allocation)
+    int* conv_err = conv_error_flag();
+    if (!conv_err) return fail(AR_ERR_CUDA, "stencil error flag unavailable");
     float* r = reinterpret_cast<float*>(base + kOffR);
     float* psf = reinterpret_cast<float*>(base + kOffPsf);
     double* dsum = reinterpret_cast<double*>(base + kOffSums);
@@ -116,6 +119,7 @@ extern "C" ar_status ar_restore_plain_static(const float* g, const double* psf_h
     AR_CUDA(cudaMemcpyAsync(psf, h32, k * sizeof(float), cudaMemcpyHostToDevice, s));
     AR_CUDA(cudaMemsetAsync(dsum, 0, ((size_t)iters + 1) * sizeof(double), s));
     AR_CUDA(cudaMemsetAsync(dbad, 0, sizeof(unsigned long long), s));
+    AR_CUDA(cudaMemsetAsync(conv_err, 0, sizeof(int), s));
     if (!x0) AR_CUDA(cudaMemsetAsync(x_out, 0, nb, s));
     else if (x0 != x_out) AR_CUDA(cudaMemcpyAsync(x_out, x0, nb, cudaMemcpyDeviceToDevice, s));
     if (f_true) AR_TRY(reduce_sq(f_true, n, dsum + iters, s));
@@ -148,9 +152,11 @@ extern "C" ar_status ar_restore_plain_static(const float* g, const double* psf_h
     AR_TRY(count_nonfinite(x_out, n, dbad, s));
     double sums[kMaxIters + 1];
     unsigned long long bad = 0;
+    int conv_timeout = 0;
     AR_CUDA(cudaMemcpyAsync(sums, dsum, ((size_t)iters + 1) * sizeof(double),
                             cudaMemcpyDeviceToHost, s));
     AR_CUDA(cudaMemcpyAsync(&bad, dbad, sizeof(bad), cudaMemcpyDeviceToHost, s));
+    AR_CUDA(cudaMemcpyAsync(&conv_timeout, conv_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     AR_CUDA(cudaStreamSynchronize(s));
     if (f_true) {
         const double fn = sums[iters];
@@ -166,6 +172,7 @@ extern "C" ar_status ar_restore_plain_static(const float* g, const double* psf_h
         }
         if (best_iter) *best_iter = best;
     }
+    if (conv_timeout) return fail(AR_ERR_TIMEOUT, "a stencil gave up waiting for its halo tile");
     if (bad) return fail(AR_ERR_NONFINITE, "%llu non-finite entries in the final iterate", bad);
     return AR_OK;
 }

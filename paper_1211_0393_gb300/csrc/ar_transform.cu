@@ -871,7 +871,7 @@ ar_status alloc_operand(Operand& o, int rows, int K, int box_rows, cudaStream_t 
     o.pstride = (size_t)rows * o.ld;
     const size_t bytes = MAX_PLANES * o.pstride * sizeof(uint16_t);
     if (permanent) AR_CUDA(cudaMalloc((void**)&o.planes, bytes));
-    else AR_CUDA(cudaMallocAsync((void**)&o.planes, bytes, s));
+    else AR_CUDA(dev_malloc_async((void**)&o.planes, bytes, s));
     for (int np = 3; np >= 2; --np) {
         if (only_np && np != only_np) continue;
         AR_TRY(make_map(&o.map[mode_index(np)], o.planes, K, rows, o.ld, BK, box_rows, np, true));
@@ -1097,7 +1097,7 @@ ar_status transform_plan_create(int n1, int n2, int bc, int precision, cudaStrea
         if (st == AR_OK) st = alloc_operand(p->W, N1, N2, BM, s, false, p->np);
         if (st == AR_OK) st = alloc_operand(p->V, N2, N1, BM, s, false, p->np, OM_PAIR_A);
         if (st == AR_OK &&
-            cudaMallocAsync((void**)&p->dfold, (size_t)N1 * N2 * sizeof(float), s) != cudaSuccess)
+            dev_malloc_async((void**)&p->dfold, (size_t)N1 * N2 * sizeof(float), s) != cudaSuccess)
             st = fail(AR_ERR_ALLOC, "folded filter");
     } else {
         if (st == AR_OK) st = alloc_operand(p->P, n1, n2, BM, s, false, p->np);
@@ -1105,7 +1105,7 @@ ar_status transform_plan_create(int n1, int n2, int bc, int precision, cudaStrea
             st = alloc_operand(p->P2, n1, n2, BM, s, false, p->np);
         if (st == AR_OK) st = alloc_operand(p->Qo, n2, n1, BM, s, false, p->np);
     }
-    if (st == AR_OK && cudaMallocAsync((void**)&p->err, sizeof(int), s) != cudaSuccess)
+    if (st == AR_OK && dev_malloc_async((void**)&p->err, sizeof(int), s) != cudaSuccess)
         st = fail(AR_ERR_ALLOC, "transform error flag");
     if (st == AR_OK && cudaMemsetAsync(p->err, 0, sizeof(int), s) != cudaSuccess)
         st = fail(AR_ERR_CUDA, "transform error flag init");

@@ -187,3 +187,27 @@ def test_residual_restore_validation(L):
     assert call(tr=FAKE) == 1                     # RRE trace without f_true
     assert call(x=FAKE + 64) == 2                 # x_out overlaps g
     assert call(q1=14) == 1                       # q > n-3 with the preconditioner
+
+
+def test_injected_allocation_failure_is_reported(L):
+    """A host-side fake of a failing device allocation (no GPU involved): the
+    restoration and the preconditioner setup return AR_ERR_ALLOC before any GPU
+    work, name the failed allocation, and the injection is used up."""
+    hp = _psf(2, 2).ctypes.data
+    out = ctypes.c_void_p()
+    try:
+        L.ar_inject_alloc_failures(0, 1)
+        st = L.ar_restore(FAKE, hp, 16, 16, 2, 2, 0.1, 1.0, 3, 1, None, None, FAKE * 64, None,
+                          None, None)
+        assert st == 4, st
+        assert "cudaMallocAsync" in L.ar_last_error_detail().decode()
+        L.ar_inject_alloc_failures(0, 1)
+        assert L.ar_symprec_setup(hp, 2, 2, 16, 16, 0.1, None, ctypes.byref(out)) == 4
+        assert out.value is None
+        L.ar_inject_alloc_failures(0, 2)
+        assert L.ar_restore(FAKE, hp, 16, 16, 2, 2, 0.1, 1.0, 3, 0, None, None, FAKE * 64,
+                            None, None, None) == 4
+        assert L.ar_restore(FAKE, hp, 16, 16, 2, 2, 0.1, 1.0, 3, 0, None, None, FAKE * 64,
+                            None, None, None) == 4
+    finally:
+        L.ar_inject_alloc_failures(0, 0)

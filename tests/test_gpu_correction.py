@@ -94,6 +94,57 @@ def test_training_steps_match_oracle(ar):
     M.close()
 
 
+def test_adam_steps_match_oracle_elementwise(ar):
+    """Every parameter after six Adam steps (three epochs of two batches, taken in
+    order) against the oracle's forward pass, backward pass and Adam update.
+
+    Adam normalises each update by the running gradient scale, so an entry whose
+    gradient is at the float32 rounding level of its tensor (or whose ReLU mask
+    flips on a pre-activation at rounding level) can move by up to lr per step in
+    either direction on either side.  Entries whose oracle gradient stays above
+    1e-3 of the tensor's largest at every step are determined by the arithmetic
+    and must agree to 2e-5 (float32 gradients carry relative errors of about 1e-3
+    there, on updates of size lr = 1e-3; a float32 emulation of the training
+    agrees to 4e-8 on them and to 1.1e-6 on all entries).  All but 0.1% of every
+    tensor must agree to 2e-5 as well (exactly-zero gradients of inactive units
+    are zero on both sides), and no entry may differ by more than the Adam step
+    bound, 2 lr per step.  A wrong gradient of any layer, a wrong bias
+    correction or a wrong moment update moves the determined entries by about
+    lr and fails."""
+    P = model_params(5)
+    H = psfs(6, 16)
+    lr, epochs, batch = 1e-3, 3, 8
+    M = ar.Corr(flat(P))
+    loss = M.train(H, epochs=epochs, batch=batch, lr=lr)
+    got = unflat(M.params())
+    M.close()
+    X = np.stack([O.corr_input(h) for h in H])
+    T = np.stack([O.corr_target(h).reshape(-1) for h in H])
+    Po = {k: v.copy() for k, v in P.items()}
+    st = {}
+    minrel = {k: np.full(v.shape, np.inf) for k, v in P.items()}
+    steps = 0
+    for _ in range(epochs):
+        for b0 in range(0, len(H), batch):
+            Y, cache = O.mlp_forward(Po, X[b0:b0 + batch])
+            _, dY = O.mse_loss(Y, T[b0:b0 + batch])
+            G = O.mlp_backward(Po, cache, dY)
+            for k in O.PARAM_ORDER:
+                minrel[k] = np.minimum(minrel[k], np.abs(G[k]) / np.max(np.abs(G[k])))
+            O.adam_step(Po, G, st, lr=lr)
+            steps += 1
+    assert steps == 6 and len(loss) == epochs
+    for k in O.PARAM_ORDER:
+        d = np.abs(got[k] - Po[k])
+        det = minrel[k] >= 1e-3
+        assert det.mean() >= 0.1, (k, det.mean())
+        assert np.max(d[det]) <= 2e-5, (k, np.max(d[det]))
+        assert np.mean(d > 2e-5) <= 1e-3, (k, np.mean(d > 2e-5))
+        assert np.max(d) <= 2 * lr * steps, (k, np.max(d))
+        # the parameters really moved: the comparison is not of two initial states
+        assert np.median(np.abs(Po[k] - P[k])[det]) > 0.5 * lr
+
+
 @pytest.mark.parametrize("n1,n2", [(64, 64), (33, 33), (130, 97)])
 def test_exact_corrected_setup_matches_oracle(ar, n1, n2):
     h = W.psf_config2()

@@ -1,6 +1,6 @@
 """Precision modes on the 2048^2 workload (ellipses, 21x21 asymmetric Gaussian
 PSF, 1% noise; alpha 0.1, the smallest half-decade value for which tau = 1 is
-stable with this PSF): the error of each of the first iterates against the
+stable with this PSF): the error of each of the first ten iterates against the
 FP64 oracle, for the float32-grade contractions (bf16x3, six products) and the
 fast mode (bf16x2, three products).  Bounds as in test_gpu_parity:
 tol(alpha) = max(1e-5, 3 * 2^-24 / alpha), tol_fast(alpha) = max(1e-4, 3 * 2^-16 / alpha)."""
@@ -17,7 +17,7 @@ from paper_1211_0393_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 ALPHA = 0.1
-STEPS = 3
+STEPS = 10
 
 
 @pytest.fixture(scope="module")
