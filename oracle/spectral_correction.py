@@ -32,7 +32,7 @@ from __future__ import annotations
 import numpy as np
 
 from .ar_oracle import (ar_analysis, ar_blur, ar_grid, ar_reblur, ar_synthesis, eigenvalues,
-                        psf_support, rre, symmetrize)
+                        psf_support, rre, symmetrize, symprec_setup)
 
 CORR_GRID = 33                 # points per axis of the predicted table on [0, pi]
 CORR_Q = 7                     # the model takes 15 x 15 PSFs
@@ -169,19 +169,24 @@ def adam_step(P: dict, G: dict, state: dict, lr: float, beta1=0.9, beta2=0.999, 
 
 
 def mlp_predict_table(P: dict, h: np.ndarray) -> np.ndarray:
-    """The model's ``delta`` table for one PSF (negative predictions clipped to 0)."""
+    """The model's ``delta`` table for one PSF (entries may be negative where the
+    symmetrized eigenvalue overstates the response; the filter clamps)."""
     Y, _ = mlp_forward(P, corr_input(h)[None, :])
-    return np.maximum(Y[0].reshape(CORR_GRID, CORR_GRID), 0.0)
+    return Y[0].reshape(CORR_GRID, CORR_GRID)
 
 
 # ------------------------------------------------------ corrected filter --
 
 def symprec_setup_corrected(h: np.ndarray, n1: int, n2: int, alpha: float,
                             table: np.ndarray | None = None) -> dict:
-    """AR preconditioner with the refined eigenvalues: ``d = 1/(lambda_s^2 + delta + alpha)``.
+    """AR preconditioner with the refined eigenvalues:
+    ``d = 1/(max(lambda_s^2 + delta, 0) + alpha)``.
 
     ``delta`` is the exact spectral energy of ``h - s`` on the AR grid when
-    ``table`` is None, else the bilinear reading of a ``G x G`` table."""
+    ``table`` is None, else the bilinear reading of a ``G x G`` table.  A
+    refined eigenvalue of A'A is a response energy, never negative: a table
+    entry below ``-lambda_s^2`` (a restoration-fitted departure, or a model's
+    prediction of one) is clamped there."""
     s = symmetrize(h)
     lam = eigenvalues(s, n1, n2)
     x1, x2 = ar_grid(n1), ar_grid(n2)
@@ -189,8 +194,8 @@ def symprec_setup_corrected(h: np.ndarray, n1: int, n2: int, alpha: float,
         delta = spectral_energy(antisymmetric_part(h), x1, x2)
     else:
         delta = bilinear(np.asarray(table, dtype=np.float64), x1, x2)
-    return {"s": s, "lam": lam, "delta": delta, "d": 1.0 / (lam ** 2 + delta + alpha),
-            "n1": n1, "n2": n2}
+    return {"s": s, "lam": lam, "delta": delta,
+            "d": 1.0 / (np.maximum(lam ** 2 + delta, 0.0) + alpha), "n1": n1, "n2": n2}
 
 
 def restore_corrected(g, h, alpha, tau=1.0, iters=20, table=None, f_true=None):
@@ -207,3 +212,95 @@ def restore_corrected(g, h, alpha, tau=1.0, iters=20, table=None, f_true=None):
             trace.append(rre(x, f_true))
     best = int(np.argmin(trace)) + 1 if trace else None
     return x, (np.asarray(trace) if trace is not None else None), best
+
+
+# ------------------------------------- targets from the method's restorations --
+#
+# The learned form's training targets come from restorations the plain method
+# itself produces.  Section 4's iteration x_{k+1} = x_k + tau D z_k, with
+# z_k = A'(g - A x_k), updates the reblurred residual as
+#     z_{k+1} = z_k - tau A'A D z_k,
+# so in the AR spectral basis of Theorem 1 (z^ = T~ z, D = T diag(d) T~)
+#     z^_{k+1} = z^_k - tau (T~ A'A T) (d o z^_k).
+# Were T~ A'A T diagonal with entries mu, every frequency would obey
+# z^_{k+1} = (1 - tau mu d) z^_k.  The per-frequency mu the iterates of the
+# symmetrized D-Landweber actually show is the least-squares fit over the pairs
+# of consecutive iterates,
+#     mu^ = sum_k w_k v_k / sum_k w_k^2,   w_k = tau d z^_k,   v_k = z^_k - z^_{k+1},
+# and the target is its departure from the symmetrized eigenvalue,
+#     delta^ = mu^ - lambda_s^2,
+# pooled onto the model's G x G grid: each interior AR frequency adds its
+# delta^ with weight (bilinear weight of the node) x (sum_k w_k^2 / tau^2) to the
+# four nodes around it, and a node takes the weighted mean (0 where no weight
+# falls).  Frequencies on the boundary lines of the AR basis (index 0 or m - 1
+# on either axis, the unit columns of T_m) are left out.  For a strongly
+# symmetric PSF T~ A'A T = diag(lambda^2) (Theorem 2, and A' = A), so mu^ =
+# lambda^2 and the target is zero.
+
+def fit_spectral_response(zhat, d: np.ndarray, tau: float):
+    """``(mu^, weight)`` per frequency from the spectra ``z^_0 .. z^_K`` of the
+    reblurred residuals: ``mu^ = sum_k w_k v_k / sum_k w_k^2`` over k = 0..K-1,
+    ``w_k = tau d z^_k``, ``v_k = z^_k - z^_{k+1}``; weight ``sum_k (d z^_k)^2``
+    (mu^ = 0 where the weight is 0)."""
+    num = np.zeros_like(d)
+    den = np.zeros_like(d)
+    for k in range(len(zhat) - 1):
+        w = tau * d * zhat[k]
+        v = zhat[k] - zhat[k + 1]
+        num += w * v
+        den += w * w
+    mu = np.where(den > 0, num / np.where(den > 0, den, 1.0), 0.0)
+    return mu, den / (tau * tau)
+
+
+def pool_to_grid(field: np.ndarray, weight: np.ndarray, x1: np.ndarray, x2: np.ndarray,
+                 G: int = CORR_GRID) -> np.ndarray:
+    """Weighted bilinear pooling of a field sampled at ``x1 x x2`` onto the ``G x G``
+    grid ``j pi / (G - 1)``: node value = sum(b w f) / sum(b w) over the samples
+    of its four cells, b the bilinear weight of the node at the sample."""
+    num = np.zeros((G, G))
+    wsum = np.zeros((G, G))
+    u1 = np.asarray(x1, dtype=np.float64) / np.pi * (G - 1)
+    u2 = np.asarray(x2, dtype=np.float64) / np.pi * (G - 1)
+    for r in range(len(u1)):
+        i = min(int(np.floor(u1[r])), G - 2)
+        t = u1[r] - i
+        for c in range(len(u2)):
+            if weight[r, c] <= 0:
+                continue
+            j = min(int(np.floor(u2[c])), G - 2)
+            w = u2[c] - j
+            for (a, b, bw) in ((i, j, (1 - t) * (1 - w)), (i, j + 1, (1 - t) * w),
+                               (i + 1, j, t * (1 - w)), (i + 1, j + 1, t * w)):
+                num[a, b] += bw * weight[r, c] * field[r, c]
+                wsum[a, b] += bw * weight[r, c]
+    return np.where(wsum > 0, num / np.where(wsum > 0, wsum, 1.0), 0.0)
+
+
+def restoration_target(h: np.ndarray, f: np.ndarray, e: np.ndarray, nu: float, alpha: float,
+                       tau: float = 1.0, iters: int = 8) -> np.ndarray:
+    """The learned form's training target for PSF ``h`` from a restoration of the
+    scene ``f`` by the symmetrized D-Landweber (eq. DLandweberMeth, x_0 = 0):
+    g = A f + nu ||A f|| e / ||e||, ``iters`` iterations, the spectra
+    ``z^_k = T~ z_k`` (k = 0 .. iters - 1) fitted per frequency as above,
+    ``delta^ = mu^ - lambda_s^2`` on the interior AR frequencies pooled onto the
+    model grid."""
+    f = np.asarray(f, dtype=np.float64)
+    e = np.asarray(e, dtype=np.float64)
+    n1, n2 = f.shape
+    gc = ar_blur(f, h)
+    g = gc + nu * np.linalg.norm(gc) / np.linalg.norm(e) * e
+    prec = symprec_setup(h, n1, n2, alpha)
+    d = prec["d"]
+    x = np.zeros((n1, n2))
+    zhat = []
+    for _ in range(iters):
+        z = ar_reblur(g - ar_blur(x, h), h)
+        zh = ar_analysis(z)
+        zhat.append(zh)
+        x = x + tau * ar_synthesis(d * zh)
+    mu, wgt = fit_spectral_response(zhat, d, tau)
+    inner = (slice(1, n1 - 1), slice(1, n2 - 1))
+    x1, x2 = ar_grid(n1)[1:n1 - 1], ar_grid(n2)[1:n2 - 1]
+    delta = mu[inner] - prec["lam"][inner] ** 2
+    return pool_to_grid(delta, wgt[inner], x1, x2)

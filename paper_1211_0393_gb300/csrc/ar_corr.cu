@@ -159,7 +159,8 @@ __global__ void delta_grid_kernel(const double2* __restrict__ R, int q1, int n1,
     delta[idx] = 0.5 * (pr * pr + pi * pi + mr * mr + mi * mi);
 }
 
-// Bilinear reading of a 33 x 33 table (negative entries clipped to 0) on the AR grid.
+// Bilinear reading of a 33 x 33 table on the AR grid (entries may be negative:
+// the filter clamps lambda^2 + delta at 0).
 __global__ void delta_table_kernel(const float* __restrict__ table, int n1, int n2,
                                    double* __restrict__ delta) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -172,7 +173,7 @@ __global__ void delta_table_kernel(const float* __restrict__ table, int n1, int 
     i = i > CG - 2 ? CG - 2 : i;
     j = j > CG - 2 ? CG - 2 : j;
     const double t = u1 - i, w = u2 - j;
-    auto T = [&](int r, int c) { return fmax((double)table[r * CG + c], 0.0); };
+    auto T = [&](int r, int c) { return (double)table[r * CG + c]; };
     delta[idx] = (1 - t) * (1 - w) * T(i, j) + (1 - t) * w * T(i, j + 1) + t * (1 - w) * T(i + 1, j) +
                  t * w * T(i + 1, j + 1);
 }

@@ -12,7 +12,7 @@
 //      t_a(x2) = w_a (s_{a,0} + 2 sum_{b>=1} s_{a,b} cos(b x2)), w_0 = 1, w_a = 2,
 //      which regroups the four sums of the equation.
 //  S2  d = 1/(lambda^2 + alpha), eq. TikFilter (with a spectral correction
-//      delta when one is given: d = 1/(lambda^2 + delta + alpha)).
+//      delta when one is given: d = 1/(max(lambda^2 + delta, 0) + alpha)).
 //
 // Periodic (comparison BC): lambda = |sum_s h_s exp(-i s . w)| at
 // w = 2 pi k / m, the eigenvalue magnitudes of the circulant of the PSF itself,
@@ -89,7 +89,7 @@ __global__ void eigen_kernel(const double* __restrict__ t, const double* __restr
     const int i = (int)(idx / n2), j = (int)(idx % n2);
     double lam = 0.0;
     for (int a = q1; a >= 0; --a) lam += c1[(size_t)a * n1 + i] * t[(size_t)a * n2 + j];
-    const double d = 1.0 / (lam * lam + (delta ? delta[idx] : 0.0) + alpha);
+    const double d = 1.0 / (fmax(lam * lam + (delta ? delta[idx] : 0.0), 0.0) + alpha);
     if (lam64) lam64[idx] = lam;
     if (d64) d64[idx] = d;
     d32[idx] = (float)d;

@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from paper_1211_0393_gb300 import workloads as W
 
 
 def rand_psf(rng, q1, q2):
@@ -142,3 +143,79 @@ def test_restore_corrected_reduces_to_restore_for_symmetric_psf_and_matches_dens
         x = x + D @ (Ap @ (g.reshape(-1) - A @ x))
     x3, _, _ = O.restore_corrected(g, h, 0.05, 1.0, 5)
     np.testing.assert_allclose(x3.reshape(-1), x, rtol=0, atol=1e-11)
+
+
+# ---------------------------------------- targets from the method's restorations
+
+def test_fit_recovers_a_known_spectral_response():
+    """A sequence that obeys z^_{k+1} = (1 - tau mu d) z^_k exactly at every
+    frequency: the least-squares fit returns mu, and the weight sum_k (d z^_k)^2."""
+    rng = np.random.default_rng(3)
+    shape = (9, 7)
+    mu = rng.uniform(0.0, 1.5, shape)
+    d = rng.uniform(0.5, 3.0, shape)
+    z = [rng.standard_normal(shape)]
+    tau = 0.7
+    for _ in range(5):
+        z.append((1.0 - tau * mu * d) * z[-1])
+    got, wgt = O.fit_spectral_response(z, d, tau)
+    np.testing.assert_allclose(got, mu, rtol=1e-12, atol=1e-12)
+    want_w = sum((d * zk) ** 2 for zk in z[:-1])
+    np.testing.assert_allclose(wgt, want_w, rtol=1e-13)
+
+
+def test_pool_of_a_constant_field_is_that_constant():
+    rng = np.random.default_rng(4)
+    x1 = np.sort(rng.uniform(0, np.pi, 40))
+    x2 = np.sort(rng.uniform(0, np.pi, 50))
+    w = rng.uniform(0.1, 2.0, (40, 50))
+    T = O.pool_to_grid(np.full((40, 50), -0.375), w, x1, x2)
+    covered = np.zeros_like(T, dtype=bool)
+    G = T.shape[0]
+    for a in x1:
+        for b in x2:
+            i = min(int(a / np.pi * (G - 1)), G - 2)
+            j = min(int(b / np.pi * (G - 1)), G - 2)
+            covered[i:i + 2, j:j + 2] = True
+    np.testing.assert_allclose(T[covered], -0.375, rtol=1e-13)
+    assert np.all(T[~covered] == 0.0)
+
+
+def test_pool_is_a_weighted_mean_of_the_samples_around_a_node():
+    """One sample per cell at known places: every node equals the bilinear-and-weight
+    weighted mean of the field values of the samples in its (up to) four cells."""
+    G = 5
+    x = (np.arange(G - 1) + 0.3) * np.pi / (G - 1)       # one sample per cell, t = 0.3
+    f = np.arange(16.0).reshape(4, 4)
+    w = np.ones((4, 4))
+    T = O.pool_to_grid(f, w, x, x, G)
+    # node (1, 1): samples (0,0) b = .3*.3, (0,1) b = .3*.7, (1,0) .7*.3, (1,1) .7*.7
+    b = np.array([[0.09, 0.21], [0.21, 0.49]])
+    assert T[1, 1] == pytest.approx(np.sum(b * f[0:2, 0:2]) / np.sum(b), rel=1e-13)
+    assert T[0, 0] == pytest.approx(f[0, 0], rel=1e-13)
+
+
+def test_restoration_target_vanishes_for_a_strongly_symmetric_psf():
+    """For h = s, T~ A'A T = diag(lambda^2) (Theorem 2 with A' = A), so the
+    iterates decay frequency by frequency exactly and the fitted response equals
+    lambda^2: the target is zero up to rounding."""
+    rng = np.random.default_rng(5)
+    n = 24
+    a = np.arange(-3, 4)
+    h = np.exp(-0.5 * (a[:, None] ** 2 / 1.3 + a[None, :] ** 2 / 2.1))
+    h /= h.sum()
+    f = rng.uniform(0, 1, (n, n))
+    e = rng.standard_normal((n, n))
+    T = O.restoration_target(h, f, e, 0.01, 0.1, 1.0, 6)
+    assert np.max(np.abs(T)) <= 1e-9
+
+
+def test_restoration_target_is_not_zero_and_tracks_the_closed_form():
+    """For the bench's strongly non-symmetric PSF the fitted departure is clearly
+    nonzero and follows the closed-form flip-averaged energy of h - s in shape."""
+    h = W.psf_config2()
+    ext, f, e = W.make_inputs(128, 128, h, "ellipses", 5)
+    T = O.restoration_target(h, f, e, 0.005, 0.3, 1.0, 8)
+    c = O.corr_target(h)
+    assert np.max(np.abs(T)) > 0.1
+    assert np.corrcoef(T.ravel(), c.ravel())[0, 1] > 0.9
