@@ -82,12 +82,11 @@ def replica_throughput(pixels, iters, steps, world, total_ms):
     return pixels * iters * steps * world / 1e6 / (total_ms / 1e3)
 
 
-def config_dict(extra=None):
+def config_dict(world=1):
     c = {"workload": WORKLOAD, "n1": N1, "n2": N2, "psf": "15x15 motion(len 11, 30 deg)+0.2 gauss",
          "iters_per_step": ITERS, "alpha": ALPHA, "tau": TAU, "precondition": True, "noise": NU,
-         "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MiB write)"}
-    if extra:
-        c.update(extra)
+         "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MiB write)",
+         "parallelism": f"replicas{world}" if world > 1 else "single"}
     return c
 
 
@@ -240,7 +239,7 @@ def run_own(args):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": config_dict({"parallelism": f"replicas{world}" if world > 1 else "single"}),
+            "config": config_dict(world),
             "e2e": {"value": round(e2e_value, 2), "unit": UNIT,
                     "h2d_bytes_per_step": int(g.nbytes + f.nbytes),
                     "d2h_bytes_per_step": int(g.nbytes + 8 * ITERS + 8 * (ITERS + 1))},
@@ -252,8 +251,12 @@ def run_own(args):
             "rre_last_step": {"best_iter": best, "rre_best": float(np.min(trace)),
                               "rre_final": float(trace[-1])},
         }
+        oracle_best = None
+        if not args.no_cpu_baseline:
+            out["parity_vs_oracle"] = oracle_parity(ar, torch, g_d, h, g, f, trace)
+            oracle_best = out["parity_vs_oracle"]["oracle_best_rre"]
         if not args.no_quality:
-            out["quality"] = quality_vs_plain(ar, torch, g_d, f_d, h)
+            out["quality"] = quality_vs_plain(ar, torch, stream, g_d, f_d, h, flush, oracle_best)
             x_ref = x_d.clone()
             out["forms"] = {"bf16x2": precision_form(ar, torch, stream, g_d, f_d, h, flush,
                                                      max(args.steps // 2, 3), x_ref)}
@@ -290,6 +293,14 @@ def kernel_rooflines(ar, torch, dev, step):
     The library brackets every kernel it launches with CUDA events on its launch
     stream (profiled kernels run serialized, without dependent-launch overlap).
     The dominant class is the one with the largest share of the step.
+
+    Work counted for the contraction is the method's: one launch applies a
+    one-dimensional AR transform (a dense DST-I plus its boundary columns) to
+    every row of a 1024 x 1024 operand, 2 n^3 flops dense, halved by the even/odd
+    fold (Theorem 1's reflection symmetry): n^3 = 1.07 GFLOP per launch at
+    float32-grade accuracy.  The tensor core executes it as six bf16 products
+    (the bf16x3 split); the rate of those products against the bf16 peak is
+    reported separately as tensor_pipe_frac.
     """
     peaks = PEAKS
     bf16 = peaks.get("bf16_tflops")
@@ -301,28 +312,32 @@ def kernel_rooflines(ar, torch, dev, step):
     prof = ar.ar_profile_end()
     k1, k2 = ar_psf_shape()
     stencil_flops = 2.0 * k1 * k2 * N1 * N2                 # per launch
-    # per iteration, six bf16 products (bf16x3 split) of G1..G4, all four block diagonal
-    # (the even/odd fold; G1's input arrives folded from the reblur, G4 pairs its parity
-    # tiles in clusters of four): half of n^3 each, i.e. 1/2 of 6 x 2 x n^3 per launch.
-    contraction_flops = 6 * 2.0 * N1 * N2 * N1 * 0.5
+    method_flops = 2.0 * N1 * N2 * N1 * 0.5                 # folded DST of every row
+    executed_flops = 6 * method_flops                       # six bf16 products
     kernels = {}
     for kind, (ms, cnt) in prof.items():
         if cnt:
-            kernels[kind] = {"launches": cnt, "ms_total": round(ms, 4), "us_per_launch": round(ms / cnt * 1e3, 3)}
+            kernels[kind] = {"launches": cnt, "ms_total": round(ms, 4),
+                             "us_per_launch": round(ms / cnt * 1e3, 3)}
     t_st = prof["stencil"][0] / max(prof["stencil"][1], 1) / 1e3
     t_ct = prof["contraction"][0] / max(prof["contraction"][1], 1) / 1e3
     if t_st > 0:
         kernels["stencil"]["tflops_fp32"] = round(stencil_flops / t_st / 1e12, 2)
+        kernels["stencil"]["alu_frac"] = round(stencil_flops / t_st / 1e12 / fp32_peak, 4)
     if t_ct > 0:
-        kernels["contraction"]["tflops_bf16"] = round(contraction_flops / t_ct / 1e12, 1)
+        kernels["contraction"]["method_tflops"] = round(method_flops / t_ct / 1e12, 2)
+        kernels["contraction"]["executed_bf16_tflops"] = round(executed_flops / t_ct / 1e12, 1)
     dom = max(("stencil", "contraction"), key=lambda k: prof[k][0])
     if dom == "contraction" and bf16:
-        ach = contraction_flops / t_ct / 1e12
-        roof = {"kernel": "tc_contract_kernel (AR transform contraction, bf16x3, 6 products)",
+        ach = method_flops / t_ct / 1e12
+        roof = {"kernel": "tc_contract_kernel (AR transform contraction, bf16x3 split)",
                 "bound": "tensor", "achieved": round(ach, 2), "peak": bf16, "unit": "TFLOP/s",
                 "frac": round(ach / bf16, 4), "traffic": measured_traffic("contraction"),
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; kernel timed alone)",
-                "work_per_launch": "6 x 2 x 1024^3 x 1/2 bf16 flops (G1-G4 block diagonal)"}
+                "work_per_launch": "method's work: folded 1D AR transform of 1024 rows of "
+                                   "1024, 1024^3 flops (float32-grade)",
+                "tensor_pipe_frac": round(executed_flops / t_ct / 1e12 / bf16, 4),
+                "executed_per_launch": "six bf16 products of the bf16x3 split, 6 x 1024^3 flops"}
     else:
         ach = stencil_flops / t_st / 1e12
         roof = {"kernel": "conv_tma_kernel<7, true, G54> (AR pad + 15x15 convolution, residual)",
@@ -616,16 +631,22 @@ MATVEC_SIDE = 8192      # 256 MiB per image: input and output are both far large
 
 
 def matvec_hbm_form(ar, torch, dev, stream, reps=10):
-    """The AR matvec y = A_n x alone where it is byte-bound: small PSFs on an
-    8192^2 image (in + out = 512 MiB per call, no L2 reuse across calls).
-    Achieved bytes = 8 B per pixel (one read of x, one write of y) over the
-    CUDA-event time of one call, against the measured copy bandwidth."""
+    """The AR matvec y = A_n x alone on an 8192^2 image (in + out = 512 MiB per
+    call, no L2 reuse across calls), from the byte-bound 3x3 PSF to the bench's
+    15 x 15.  Achieved bytes = 8 B per pixel (one read of x, one write of y) over
+    the CUDA-event time of one call, against the measured copy bandwidth; the
+    flops 2 (2q+1)^2 per pixel against the FP32 FMA peak (SMs x 128 lanes x 2 x
+    the maximum SM clock).  A (2q+1)^2 stencil is ALU-bound from 5 x 5 on: its
+    HBM fraction cannot exceed the ALU peak's pixel rate x 8 B / the copy
+    bandwidth (0.21 at 15 x 15)."""
     n = MATVEC_SIDE
     x = torch.rand(n, n, device=dev)
     y = torch.empty_like(x)
     peak = PEAKS.get("hbm_gbs")
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = nsm * 128 * 2 * PEAKS.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     out = {}
-    for q in (1, 2, 3):
+    for q in (1, 2, 3, 4, 7):
         a = np.arange(-q, q + 1)
         h = np.exp(-0.5 * (a[:, None] ** 2 + a[None, :] ** 2) / max(q, 1) ** 2)
         hd = torch.from_numpy((h / h.sum()).astype(np.float32)).to(dev)
@@ -641,12 +662,17 @@ def matvec_hbm_form(ar, torch, dev, stream, reps=10):
             tot += e0.elapsed_time(e1)
         ms = tot / reps
         gbs = 8.0 * n * n / (ms / 1e3) / 1e9
+        tf = 2 * (2 * q + 1) ** 2 * n * n / (ms / 1e3) / 1e12
         out[f"{2 * q + 1}x{2 * q + 1}"] = {
             "us_per_call": round(ms * 1e3, 2), "achieved_gbs": round(gbs, 1),
             "hbm_frac": round(gbs / peak, 4) if peak else None,
-            "fp32_tflops": round(2 * (2 * q + 1) ** 2 * n * n / (ms / 1e3) / 1e12, 2)}
+            "fp32_tflops": round(tf, 2), "alu_frac": round(tf / fp32_peak, 4),
+            "hbm_frac_ceiling_at_alu_peak": (round(min(1.0, fp32_peak * 1e12 /
+                                                       (2 * (2 * q + 1) ** 2) * 8 / 1e9 / peak), 4)
+                                             if peak else None)}
     out["workload"] = f"ar_blur_apply on {n}x{n} float32, Gaussian PSFs, 8 B/px algorithmic"
     out["peak"] = f"{peak} GB/s of measured" if peak else None
+    out["fp32_peak_tflops"] = round(fp32_peak, 1)
     return out
 
 
@@ -691,56 +717,165 @@ def bcs_form(ar, torch, stream, g_d, f_d, h, flush, steps):
     return out
 
 
-def quality_vs_plain(ar, torch, g_d, f_d, h):
-    """Iterations and GPU time for D-Landweber and plain Landweber to reach the
-    restoration error both attain (1% above the larger of their best RREs)."""
-    plain_iters = 200
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
+def _event_ms(torch, stream, fn, flush=None, reps=3):
+    """Median CUDA-event time of fn() on `stream` (L2 flushed before each rep)."""
+    ts = []
+    for i in range(reps):
+        if flush is not None:
+            flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def quality_vs_plain(ar, torch, stream, g_d, f_d, h, flush, oracle_best):
+    """Iterations and device time for D-Landweber and plain Landweber to reach
+    the restoration error the FP64 oracle's D-Landweber attains (its best RRE
+    within the bench's 50 iterations, Section 4's IT).  The iteration counts
+    come from the GPU RRE traces; the times are CUDA-event times of calls that
+    run exactly that many iterations (no RRE trace), with the preconditioner's
+    FP64 setup timed apart (ar_symprec_setup, then ar_restore_prec)."""
+    plain_iters = 400
     _, tr_p, best_p = ar.ar_restore(g_d, h, ALPHA, TAU, plain_iters, False, f_true=f_d)
-    t_plain = time.perf_counter() - t0
-    t0 = time.perf_counter()
     _, tr_d, best_d = ar.ar_restore(g_d, h, ALPHA, TAU, ITERS, True, f_true=f_d)
-    t_prec = time.perf_counter() - t0
-    target = max(float(np.min(tr_p)), float(np.min(tr_d))) * 1.01
+    target = oracle_best * (1 + 1e-5) if oracle_best else None
 
     def first(tr):
-        idx = np.nonzero(tr <= target)[0]
+        if target is None:
+            return None
+        idx = np.nonzero(np.asarray(tr) <= target)[0]
         return int(idx[0]) + 1 if len(idx) else None
 
     kp, kd = first(tr_p), first(tr_d)
-    return {"target_rre": round(target, 6), "plain_best_rre": round(float(np.min(tr_p)), 6),
-            "plain_best_iter": best_p, "precond_best_rre": round(float(np.min(tr_d)), 6),
-            "precond_best_iter": best_d, "plain_iters_to_target": kp,
-            "precond_iters_to_target": kd,
-            "plain_ms_to_target": round(t_plain * 1e3 * kp / plain_iters, 3) if kp else None,
-            "precond_ms_to_target": round(t_prec * 1e3 * kd / ITERS, 3) if kd else None,
-            "note": "ms = wall time of the whole call scaled by iterations used"}
+    out = {"target_rre": round(target, 6) if target else None,
+           "target": "best RRE of the FP64 oracle's D-Landweber run (x (1 + 1e-5))",
+           "plain_best_rre": round(float(np.min(tr_p)), 6), "plain_best_iter": best_p,
+           "precond_best_rre": round(float(np.min(tr_d)), 6), "precond_best_iter": best_d,
+           "plain_iters_to_target": kp, "precond_iters_to_target": kd}
+    x = torch.empty_like(g_d)
+    hold = {}
+
+    def setup():
+        hold["P"] = ar.ar_symprec_setup(h, N1, N2, ALPHA)
+
+    out["precond_setup_ms"] = round(_event_ms(torch, stream, setup, flush), 4)
+    P = hold["P"]
+    if kd:
+        t = _event_ms(torch, stream, lambda: ar.ar_restore_prec(P, g_d, h, TAU, kd, x_out=x,
+                                                                trace=False), flush)
+        out["precond_iterations_ms"] = round(t, 4)
+        out["precond_ms_to_target"] = round(t + out["precond_setup_ms"], 4)
+    P.close()
+    if kp:
+        t = _event_ms(torch, stream, lambda: ar.ar_restore(g_d, h, ALPHA, TAU, kp, False,
+                                                           x_out=x, trace=False), flush)
+        out["plain_ms_to_target"] = round(t, 4)
+    if kd and kp:
+        out["iteration_ratio_plain_over_precond"] = round(kp / kd, 3)
+        out["time_ratio_plain_over_precond"] = round(out["plain_ms_to_target"] /
+                                                     out["precond_ms_to_target"], 3)
+    return out
 
 
 # ------------------------------------------------------------ oracle arm ----
 
 ORACLE_SAMPLE_ITERS = 3          # per reference-arm step
-CPU_BASELINE_ITERS = 12          # about 10 s of oracle work on the host cores
+CPU_SAMPLE_ITERS = {"1": 2, "all": 4}   # per run; three runs each
+THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+               "BLIS_NUM_THREADS", "VECLIB_MAXIMUM_THREADS")
 
 
-def oracle_sample(h, g, f, iters):
+def oracle_sample(h, g, f, iters, each=None):
+    """Seconds of one oracle restoration of `iters` D-Landweber iterations (setup
+    included); returns (seconds, oracle result)."""
     import oracle as O
 
     t0 = time.perf_counter()
-    O.restore(g.astype(np.float64), h, ALPHA, TAU, iters, True, f_true=f.astype(np.float64))
-    return time.perf_counter() - t0
+    res = O.restore(g.astype(np.float64), h, ALPHA, TAU, iters, True,
+                    f_true=f.astype(np.float64), each=each)
+    return time.perf_counter() - t0, res
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def cpu_baseline(h, g, f):
-    iters = CPU_BASELINE_ITERS
-    oracle_sample(h, g, f, 1)
-    dt = oracle_sample(h, g, f, iters)
-    return {"value": round(N1 * N2 * iters / dt / 1e6, 4), "unit": UNIT,
-            "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"FP64 NumPy oracle, {iters} D-Landweber iterations (setup included) of the "
-                      f"{WORKLOAD} workload; numpy default threads",
-            "seconds": round(dt, 3)}
+    """The FP64 oracle on the host cores, per the baseline plan: one BLAS thread
+    and all cores, three runs each (median), the thread variables recorded.
+    Each run is a child process with the thread variables set before NumPy
+    loads, restoring the bench workload for a few iterations (setup included)."""
+    fd, path = tempfile.mkstemp(suffix=".npz")
+    os.close(fd)
+    np.savez(path, h=h, g=g, f=f)
+    legs = {}
+    try:
+        for key, threads in (("1", 1), ("all", os.cpu_count() or 1)):
+            env = dict(os.environ)
+            for v in THREAD_VARS:
+                env[v] = str(threads)
+            iters = CPU_SAMPLE_ITERS[key]
+            secs = []
+            for _ in range(3):
+                r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample",
+                                    path, str(iters)], env=env, capture_output=True, text=True,
+                                   timeout=600)
+                secs.append(float(r.stdout.strip().splitlines()[-1]))
+            med = statistics.median(secs)
+            legs[key] = {"value": round(N1 * N2 * iters / med / 1e6, 4), "unit": UNIT,
+                         "threads": threads, "iterations_per_run": iters,
+                         "seconds_runs": [round(x, 3) for x in secs],
+                         "thread_env": {v: env[v] for v in THREAD_VARS}}
+    finally:
+        os.unlink(path)
+    return {"value": legs["all"]["value"], "unit": UNIT, "cores": legs["all"]["threads"],
+            "kind": "oracle",
+            "sample": (f"FP64 NumPy oracle, D-Landweber on the {WORKLOAD} workload, "
+                       f"{CPU_SAMPLE_ITERS['all']} iterations per run with all cores and "
+                       f"{CPU_SAMPLE_ITERS['1']} with one thread (setup included), median of 3 "
+                       f"runs each, each run a fresh process"),
+            "single_thread": legs["1"], "all_cores": legs["all"],
+            "cpu": cpu_model(), "cpu_count": os.cpu_count()}
+
+
+def oracle_sample_main(path, iters):
+    d = np.load(path)
+    oracle_sample(d["h"], d["g"], d["f"], 1)                 # imports and caches warm
+    dt, _ = oracle_sample(d["h"], d["g"], d["f"], iters)
+    print(f"{dt:.6f}", flush=True)
+
+
+def oracle_parity(ar, torch, g_d, h, g, f, trace_gpu):
+    """Every iterate of the benchmarked call against the FP64 oracle: the GPU's
+    x_k from k-iteration calls (the iteration is deterministic), the oracle's
+    from one 50-iteration run; rel-L2 per iterate, the RRE traces and IT."""
+    xs = {}
+    for k in range(1, ITERS + 1):
+        xs[k] = ar.ar_restore(g_d, h, ALPHA, TAU, k, True)[0].cpu().numpy()
+    errs = {}
+
+    def each(k, xk):
+        errs[k] = float(np.linalg.norm(xs[k].astype(np.float64) - xk) / np.linalg.norm(xk))
+
+    dt, (_, to, bo) = oracle_sample(h, g, f, ITERS, each=each)
+    worst = max(errs, key=errs.get)
+    return {"max_rel_l2_vs_oracle": errs[worst], "at_iterate": worst,
+            "rel_l2_per_iterate": [round(errs[k], 10) for k in range(1, ITERS + 1)],
+            "max_abs_rre_diff": float(np.max(np.abs(np.asarray(trace_gpu) - to))),
+            "oracle_best_iter": bo, "oracle_best_rre": float(np.min(to)),
+            "tolerance": 1e-5, "oracle_seconds": round(dt, 2)}
 
 
 def run_reference(args):
@@ -760,7 +895,7 @@ def run_reference(args):
         oracle_sample(h, g, f, 1)
     tot = 0.0
     for _ in range(args.steps):
-        tot += oracle_sample(h, g, f, iters)
+        tot += oracle_sample(h, g, f, iters)[0]
     value = N1 * N2 * iters * args.steps / 1e6 / tot
     cb = {"value": round(value, 4), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
           "sample": f"FP64 NumPy oracle, {iters} D-Landweber iterations (setup included) per step of "
@@ -777,6 +912,9 @@ def run_reference(args):
 
 
 def main():
+    if len(sys.argv) == 4 and sys.argv[1] == "--oracle-sample":
+        oracle_sample_main(sys.argv[2], int(sys.argv[3]))
+        return
     args = parse()
     if args.impl == "reference":
         run_reference(args)
