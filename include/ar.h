@@ -282,23 +282,34 @@ AR_API ar_status ar_restore_residuals(const float* g, const double* psf_host,
 
 /*
  * Batched restoration of many independent images (each with its own size,
- * PSF and alpha).  ar_batch_create builds every image's preconditioner
- * (as ar_symprec_setup) and scratch, then captures the whole restoration of
- * every image -- x_0 = 0, `iters` iterations of eq. DLandweberMeth with the
- * reblurred A' (plain Landweber when precondition == 0), the RRE of every
- * iterate when f_true is given -- into one CUDA graph whose per-image kernel
- * chains run on `concurrency` (1..64) parallel branches.  The images' device
- * pointers are bound at creation and must stay valid for the life of the plan.
- * Creation synchronizes `stream`.  ar_batch_run launches the graph on
- * `stream` (asynchronous: every x_out is overwritten); ar_batch_results waits
- * for the last run and copies the RRE traces (count x iters doubles, may be
- * NULL), the best iterations (count ints, may be NULL) and the number of
- * kernels one run launches.  Results of a run equal those of ar_restore_ex
- * with the same arguments, image by image.
+ * PSF and alpha; AR BCs).  ar_batch_create builds every image's
+ * preconditioner (as ar_symprec_setup) and scratch, then captures the whole
+ * restoration of every image -- x_0 = 0, `iters` iterations of eq.
+ * DLandweberMeth with the reblurred A' (plain Landweber when precondition ==
+ * 0), the RRE of every iterate when f_true is given -- into one CUDA graph in
+ * which every iteration of the whole batch is five launches: one persistent
+ * stencil kernel (the blur and the reblur of every image, single tiles handed
+ * out by a device-side queue, largest images first, each reblur tile waiting
+ * with a bounded wait for its image's blur tiles) and four grouped
+ * contractions (every image's tiles of one product of the AR transform pair).
+ * `tuning` 0 lets an autotuner time the stencil launch's tile geometry (64- or
+ * 54-row tiles) and persistent CTAs per SM (1..3) on the batch itself and keep
+ * the fastest (ar_batch_tuning reports the candidates); 1..8 fixes the CTAs
+ * per SM with 64-row tiles.  Needs q_j <= 15, n2 % 4 == 0 and 16-byte aligned
+ * x_out (AR_ERR_UNSUPPORTED otherwise).  The images' device pointers are bound
+ * at creation and must stay valid for the life of the plan.  Creation
+ * synchronizes `stream`.  ar_batch_run launches the graph on `stream`
+ * (asynchronous: every x_out is overwritten); ar_batch_results waits for the
+ * last run and copies the RRE traces (count x iters doubles, may be NULL), the
+ * best iterations (count ints, may be NULL) and the number of kernels one run
+ * launches.  The stencils of a run equal those of ar_restore_ex bit for bit;
+ * the contractions read the unfolded reblur (the single-image loop folds it
+ * into the first product) and run the last product unpaired, so the iterates
+ * agree with ar_restore_ex within the restoration's float32 tolerance.
  * Errors: AR_ERR_INVALID_ARG (item index in the detail), AR_ERR_ALIAS (an
  * output overlapping any input or output of the batch),
- * AR_ERR_PSF_NOT_NORMALIZED, AR_ERR_ALLOC, AR_ERR_CUDA; ar_batch_results:
- * AR_ERR_NONFINITE, AR_ERR_TIMEOUT.
+ * AR_ERR_PSF_NOT_NORMALIZED, AR_ERR_UNSUPPORTED, AR_ERR_ALLOC, AR_ERR_CUDA;
+ * ar_batch_results: AR_ERR_NONFINITE, AR_ERR_TIMEOUT.
  */
 typedef struct ar_batch_item {
     const float* g;            /* device n1*n2 observed image */
@@ -310,12 +321,19 @@ typedef struct ar_batch_item {
 } ar_batch_item;
 typedef struct ar_batch ar_batch;
 AR_API ar_status ar_batch_create(const ar_batch_item* items, int count, double tau, int iters,
-                                 int precondition, int precision, int concurrency, void* stream,
+                                 int precondition, int precision, int tuning, void* stream,
                                  ar_batch** out);
 AR_API ar_status ar_batch_run(ar_batch* B, void* stream);
 AR_API ar_status ar_batch_results(ar_batch* B, double* rre_traces, int* best_iters,
                                   unsigned long long* kernels_per_run);
 AR_API void ar_batch_destroy(ar_batch* B);
+/* The stencil configuration the batch runs with (geometry 0: 64-row tiles, 1:
+ * 54-row tiles; persistent CTAs per SM) and, when autotuned, every timed
+ * candidate (up to max_candidates of them: geometry, CTAs per SM, device
+ * milliseconds of three batch iterations).  Any output may be NULL. */
+AR_API ar_status ar_batch_tuning(const ar_batch* B, int* geometry, int* ctas_per_sm,
+                                 int* candidates, int* cand_geometry, int* cand_ctas,
+                                 double* cand_ms, int max_candidates);
 
 /*
  * Spectral correction of the symmetrized preconditioner (learned form).
@@ -331,9 +349,16 @@ AR_API void ar_batch_destroy(ar_batch* B);
  * learns from the PSF's antisymmetric part: an MLP (ReLU, widths 225 -> 256
  * -> 256 -> 1089) mapping 16 (h - s) of a 15 x 15 PSF (row-major) to delta on
  * the 33 x 33 grid x_j = j pi / 32 of [0, pi]^2 (row-major), read on the AR
- * grid by bilinear interpolation (negative predictions count as 0).
+ * grid by bilinear interpolation.  A refined eigenvalue of A'A is a response
+ * energy: every corrected filter is d = 1/(max(lambda_s^2 + delta, 0) + alpha),
+ * so a table entry below -lambda_s^2 counts as -lambda_s^2.
  * Parameters are float32, row-major (inputs x outputs), in the order
  * W1 (225 x 256), b1, W2 (256 x 256), b2, W3 (256 x 1089), b3.
+ *
+ * Two kinds of training target exist: the closed form above
+ * (ar_corr_targets, ar_corr_train), and tables read off restorations the
+ * symmetrized method itself produces (ar_corr_restoration_targets,
+ * ar_corr_train_tables).
  */
 #define AR_CORR_Q 7
 #define AR_CORR_IN 225
@@ -370,12 +395,52 @@ AR_API ar_status ar_corr_targets(const double* psfs_host, int count, double* del
 AR_API ar_status ar_corr_train(ar_corr* M, const double* psfs_host, int count, int epochs,
                                int batch, double lr, float* loss_trace_host, void* stream);
 
+/* Train as ar_corr_train on given target tables: tables_host holds count x
+ * 1089 float64 values (row-major 33 x 33 per PSF, e.g. from
+ * ar_corr_restoration_targets), used as float32 targets.  Errors as
+ * ar_corr_train, plus AR_ERR_INVALID_ARG for a null or non-finite table. */
+AR_API ar_status ar_corr_train_tables(ar_corr* M, const double* psfs_host,
+                                      const double* tables_host, int count, int epochs,
+                                      int batch, double lr, float* loss_trace_host, void* stream);
+
+/*
+ * Training targets from restorations the symmetrized method produces (Section
+ * 4's D-Landweber, eq. DLandweberMeth with the reblurred A', x_0 = 0).  For
+ * each of `count` 15 x 15 PSFs h (host float64, 225 each, unit sum):
+ *   g = A f + nu ||A f||_F e / ||e||_F  (A the AR blur of h; f and e device
+ *       float32 n1 x n2, the scene and a noise field, read only);
+ *   `iters` iterations with the symmetrized preconditioner of parameter alpha
+ *   and step tau, keeping each iteration's spectral operand W_k = d o (T~ z_k),
+ *   z_k = A'(g - A x_k) (Theorem 1's basis);
+ *   per interior AR frequency, the least-squares effective eigenvalue of A'A
+ *   over consecutive iterates, mu = sum_k W_k (W_k - W_{k+1}) / (tau d sum_k W_k^2),
+ *   which obeys z^_{k+1} = (1 - tau mu d) z^_k when T~ A'A T is diagonal there;
+ *   the target delta = (mu - lambda_s^2) w / (w + 5 w_mean), w = sum_k W_k^2
+ *   and w_mean its mean over the interior frequencies (frequencies where the
+ *   image has no content, and the fit only rounding, stay near 0), pooled
+ *   onto the 33 x 33 grid (each
+ *   frequency adds to the four nodes around it with weight w times the node's
+ *   bilinear weight; a node is the weighted mean, 0 if no weight falls).
+ * tables_host receives count x 1089 float64.  The paper has no such
+ * procedure: it generates the learned correction's training data from the
+ * method's own iterations.  Requires n_j >= 17 (the support condition of the
+ * preconditioner), iters >= 2, nu >= 0, alpha > 0, tau > 0.  Allocates stream-
+ * ordered scratch; synchronizes `stream`.  Errors: AR_ERR_INVALID_ARG,
+ * AR_ERR_PSF_NOT_NORMALIZED, AR_ERR_ALIAS (f partially overlaps e),
+ * AR_ERR_ALLOC, AR_ERR_CUDA, AR_ERR_TIMEOUT, AR_ERR_NONFINITE (a table entry;
+ * e.g. a diverging restoration).
+ */
+AR_API ar_status ar_corr_restoration_targets(const float* f, const float* e, int n1, int n2,
+                                             const double* psfs_host, int count, double nu,
+                                             double alpha, double tau, int iters,
+                                             double* tables_host, void* stream);
+
 /* The model's 33 x 33 delta table for one 15 x 15 PSF (host float64) into
- * table_host (1089 floats, before clipping at 0).  Synchronous. */
+ * table_host (1089 floats).  Synchronous. */
 AR_API ar_status ar_corr_predict(const ar_corr* M, const double* psf_host, float* table_host);
 
 /* ar_symprec_setup_ex (AR BCs) with the corrected filter
- * d = 1/(lambda_s^2 + delta + alpha): delta exact on the AR grid (float64)
+ * d = 1/(max(lambda_s^2 + delta, 0) + alpha): delta exact on the AR grid (float64)
  * when M is NULL, else read from M's prediction for the PSF (which must then
  * be 15 x 15).  Errors as ar_symprec_setup_ex. */
 AR_API ar_status ar_symprec_setup_corrected(const double* psf_host, int q1, int q2, int n1, int n2,

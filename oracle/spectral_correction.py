@@ -231,11 +231,23 @@ def restore_corrected(g, h, alpha, tau=1.0, iters=20, table=None, f_true=None):
 #     delta^ = mu^ - lambda_s^2,
 # pooled onto the model's G x G grid: each interior AR frequency adds its
 # delta^ with weight (bilinear weight of the node) x (sum_k w_k^2 / tau^2) to the
-# four nodes around it, and a node takes the weighted mean (0 where no weight
-# falls).  Frequencies on the boundary lines of the AR basis (index 0 or m - 1
-# on either axis, the unit columns of T_m) are left out.  For a strongly
-# symmetric PSF T~ A'A T = diag(lambda^2) (Theorem 2, and A' = A), so mu^ =
-# lambda^2 and the target is zero.
+# four nodes around it, and a node takes the weighted mean.  Where the image
+# has almost no content the fit divides two differences of tiny spectral values
+# and is set by rounding, so each frequency's departure is shrunk towards 0 by
+# a prior weight rho = theta x (the mean weight of the interior frequencies),
+# theta = CORR_FIT_PRIOR: delta^ = (mu^ - lambda_s^2) w / (w + rho) (a Tikhonov
+# fit of mu towards lambda_s^2).  A perturbation e of the spectral values then
+# moves delta^ by at most about e sqrt(K) / (tau d sqrt(rho)): frequencies with
+# real weight keep their fit, the others stay near 0.  (The mean, not the
+# largest weight, keeps the rule independent of the image size: a natural
+# scene's largest weight grows faster with the size than its typical one.)
+# Frequencies on the
+# boundary lines of the AR basis (index 0 or m - 1 on either axis, the unit
+# columns of T_m) are left out.  For a strongly symmetric PSF T~ A'A T =
+# diag(lambda^2) (Theorem 2, and A' = A), so mu^ = lambda^2 and the target is
+# zero.
+
+CORR_FIT_PRIOR = 5.0
 
 def fit_spectral_response(zhat, d: np.ndarray, tau: float):
     """``(mu^, weight)`` per frequency from the spectra ``z^_0 .. z^_K`` of the
@@ -254,10 +266,11 @@ def fit_spectral_response(zhat, d: np.ndarray, tau: float):
 
 
 def pool_to_grid(field: np.ndarray, weight: np.ndarray, x1: np.ndarray, x2: np.ndarray,
-                 G: int = CORR_GRID) -> np.ndarray:
+                 G: int = CORR_GRID, prior: float = 0.0) -> np.ndarray:
     """Weighted bilinear pooling of a field sampled at ``x1 x x2`` onto the ``G x G``
-    grid ``j pi / (G - 1)``: node value = sum(b w f) / sum(b w) over the samples
-    of its four cells, b the bilinear weight of the node at the sample."""
+    grid ``j pi / (G - 1)``: node value = sum(b w f) / (sum(b w) + prior) over the
+    samples of its four cells, b the bilinear weight of the node at the sample
+    (0 where no weight falls)."""
     num = np.zeros((G, G))
     wsum = np.zeros((G, G))
     u1 = np.asarray(x1, dtype=np.float64) / np.pi * (G - 1)
@@ -274,7 +287,7 @@ def pool_to_grid(field: np.ndarray, weight: np.ndarray, x1: np.ndarray, x2: np.n
                                (i + 1, j, t * (1 - w)), (i + 1, j + 1, t * w)):
                 num[a, b] += bw * weight[r, c] * field[r, c]
                 wsum[a, b] += bw * weight[r, c]
-    return np.where(wsum > 0, num / np.where(wsum > 0, wsum, 1.0), 0.0)
+    return np.where(wsum > 0, num / np.where(wsum > 0, wsum + prior, 1.0), 0.0)
 
 
 def restoration_target(h: np.ndarray, f: np.ndarray, e: np.ndarray, nu: float, alpha: float,
@@ -284,7 +297,7 @@ def restoration_target(h: np.ndarray, f: np.ndarray, e: np.ndarray, nu: float, a
     g = A f + nu ||A f|| e / ||e||, ``iters`` iterations, the spectra
     ``z^_k = T~ z_k`` (k = 0 .. iters - 1) fitted per frequency as above,
     ``delta^ = mu^ - lambda_s^2`` on the interior AR frequencies pooled onto the
-    model grid."""
+    model grid, each shrunk by the prior weight CORR_FIT_PRIOR x the mean weight."""
     f = np.asarray(f, dtype=np.float64)
     e = np.asarray(e, dtype=np.float64)
     n1, n2 = f.shape
@@ -302,5 +315,7 @@ def restoration_target(h: np.ndarray, f: np.ndarray, e: np.ndarray, nu: float, a
     mu, wgt = fit_spectral_response(zhat, d, tau)
     inner = (slice(1, n1 - 1), slice(1, n2 - 1))
     x1, x2 = ar_grid(n1)[1:n1 - 1], ar_grid(n2)[1:n2 - 1]
-    delta = mu[inner] - prec["lam"][inner] ** 2
-    return pool_to_grid(delta, wgt[inner], x1, x2)
+    w = wgt[inner]
+    rho = CORR_FIT_PRIOR * float(np.mean(w))
+    delta = (mu[inner] - prec["lam"][inner] ** 2) * w / (w + rho)
+    return pool_to_grid(delta, w, x1, x2)

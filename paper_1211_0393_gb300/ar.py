@@ -34,7 +34,8 @@ EXPORTS = [
     "ar_corr_param_count", "ar_corr_create", "ar_corr_params", "ar_corr_destroy",
     "ar_corr_targets", "ar_corr_train", "ar_corr_predict", "ar_symprec_setup_corrected",
     "ar_restore_prec", "ar_restore_residuals", "ar_set_stencil_wait_polls",
-    "ar_inject_alloc_failures",
+    "ar_inject_alloc_failures", "ar_corr_train_tables", "ar_corr_restoration_targets",
+    "ar_batch_tuning",
 ]
 
 DEFAULT_WAIT_POLLS = 1 << 24
@@ -115,6 +116,9 @@ def lib() -> ctypes.CDLL:
         L.ar_batch_run.restype = _i
         L.ar_batch_results.argtypes = [_vp, _vp, _vp, _vp]
         L.ar_batch_results.restype = _i
+        L.ar_batch_tuning.argtypes = [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i),
+                                      ctypes.POINTER(_i), _vp, _vp, _vp, _i]
+        L.ar_batch_tuning.restype = _i
         L.ar_batch_destroy.argtypes = [_vp]
         L.ar_batch_destroy.restype = None
         L.ar_set_stencil_wait_polls.argtypes = [ctypes.c_uint]
@@ -134,6 +138,8 @@ def lib() -> ctypes.CDLL:
             "ar_corr_params": [_vp, _vp],
             "ar_corr_targets": [_vp, _i, _vp],
             "ar_corr_train": [_vp, _vp, _i, _i, _i, _d, _vp, _vp],
+            "ar_corr_train_tables": [_vp, _vp, _vp, _i, _i, _i, _d, _vp, _vp],
+            "ar_corr_restoration_targets": [_vp, _vp, _i, _i, _vp, _i, _d, _d, _d, _i, _vp, _vp],
             "ar_corr_predict": [_vp, _vp, _vp],
             "ar_symprec_setup_corrected": [_vp, _i, _i, _i, _i, _d, _vp, _i, _vp,
                                            ctypes.POINTER(_vp)],
@@ -392,7 +398,7 @@ class Batch:
     alive while the batch exists."""
 
     def __init__(self, images, tau=1.0, iters=50, precondition=True, precision="fp32",
-                 concurrency=8, stream=None):
+                 tuning=0, stream=None):
         self.count = len(images)
         self.iters = int(iters)
         self._keep = []
@@ -412,7 +418,7 @@ class Batch:
         out = _vp()
         _check(lib().ar_batch_create(arr, self.count, float(tau), self.iters,
                                      1 if precondition else 0, PRECISION[precision],
-                                     int(concurrency), _stream(stream), ctypes.byref(out)),
+                                     int(tuning), _stream(stream), ctypes.byref(out)),
                "ar_batch_create")
         self.handle = out.value
 
@@ -427,6 +433,21 @@ class Batch:
         _check(lib().ar_batch_results(self.handle, tr.ctypes.data, best.ctypes.data,
                                       ctypes.byref(kpr)), "ar_batch_results")
         return tr[:, :self.iters], best, int(kpr.value)
+
+    def tuning(self) -> dict:
+        """The stencil configuration in use and the autotuner's timed candidates."""
+        geo, ctas, n = _i(), _i(), _i()
+        cg = np.zeros(16, dtype=np.int32)
+        cc = np.zeros(16, dtype=np.int32)
+        cm = np.zeros(16, dtype=np.float64)
+        _check(lib().ar_batch_tuning(self.handle, ctypes.byref(geo), ctypes.byref(ctas),
+                                     ctypes.byref(n), cg.ctypes.data, cc.ctypes.data,
+                                     cm.ctypes.data, 16), "ar_batch_tuning")
+        k = min(n.value, 16)
+        return {"geometry": ("64-row", "54-row")[geo.value], "ctas_per_sm": ctas.value,
+                "candidates": [{"geometry": ("64-row", "54-row")[int(cg[i])],
+                                "ctas_per_sm": int(cc[i]), "ms_3_iters": float(cm[i])}
+                               for i in range(k)]}
 
     def close(self) -> None:
         if self.handle:
@@ -457,12 +478,26 @@ class Corr:
         _check(lib().ar_corr_params(self.handle, p.ctypes.data), "ar_corr_params")
         return p
 
-    def train(self, psfs, epochs: int, batch: int, lr: float, stream=None) -> np.ndarray:
-        """Adam on the mean squared error of the delta tables; returns the loss per epoch."""
+    def train(self, psfs, epochs: int, batch: int, lr: float, stream=None,
+              tables=None) -> np.ndarray:
+        """Adam on the mean squared error of the delta tables; returns the loss per epoch.
+
+        ``tables`` (count x 33 x 33) replaces the closed-form targets, e.g. with
+        those of :func:`corr_restoration_targets`."""
         h = np.ascontiguousarray(psfs, dtype=np.float64).reshape(-1, 225)
         tr = np.zeros(max(int(epochs), 1), dtype=np.float32)
-        _check(lib().ar_corr_train(self.handle, h.ctypes.data, h.shape[0], int(epochs), int(batch),
-                                   float(lr), tr.ctypes.data, _stream(stream)), "ar_corr_train")
+        if tables is None:
+            _check(lib().ar_corr_train(self.handle, h.ctypes.data, h.shape[0], int(epochs),
+                                       int(batch), float(lr), tr.ctypes.data, _stream(stream)),
+                   "ar_corr_train")
+        else:
+            t = np.ascontiguousarray(tables, dtype=np.float64).reshape(h.shape[0], -1)
+            if t.shape[1] != CORR_GRID * CORR_GRID:
+                raise ValueError("tables must be count x 33 x 33")
+            _check(lib().ar_corr_train_tables(self.handle, h.ctypes.data, t.ctypes.data,
+                                              h.shape[0], int(epochs), int(batch), float(lr),
+                                              tr.ctypes.data, _stream(stream)),
+                   "ar_corr_train_tables")
         return tr[:int(epochs)]
 
     def predict(self, psf) -> np.ndarray:
@@ -492,6 +527,24 @@ def corr_targets(psfs) -> np.ndarray:
     h = np.ascontiguousarray(psfs, dtype=np.float64).reshape(-1, 225)
     out = np.empty((h.shape[0], CORR_GRID * CORR_GRID), dtype=np.float64)
     _check(lib().ar_corr_targets(h.ctypes.data, h.shape[0], out.ctypes.data), "ar_corr_targets")
+    return out.reshape(-1, CORR_GRID, CORR_GRID)
+
+
+def corr_restoration_targets(f: torch.Tensor, e: torch.Tensor, psfs, nu: float, alpha: float,
+                             tau: float = 1.0, iters: int = 8, stream=None) -> np.ndarray:
+    """Training tables (count x 33 x 33, float64) read off restorations of the scene
+    ``f`` (noise field ``e``, relative level ``nu``) by the symmetrized D-Landweber,
+    one per 15 x 15 PSF (see ``include/ar.h``)."""
+    _image(f, "f")
+    _image(e, "e")
+    if f.shape != e.shape:
+        raise ValueError("f and e must have the same shape")
+    h = np.ascontiguousarray(psfs, dtype=np.float64).reshape(-1, 225)
+    out = np.empty((h.shape[0], CORR_GRID * CORR_GRID), dtype=np.float64)
+    n1, n2 = f.shape
+    _check(lib().ar_corr_restoration_targets(
+        f.data_ptr(), e.data_ptr(), n1, n2, h.ctypes.data, h.shape[0], float(nu), float(alpha),
+        float(tau), int(iters), out.ctypes.data, _stream(stream)), "ar_corr_restoration_targets")
     return out.reshape(-1, CORR_GRID, CORR_GRID)
 
 

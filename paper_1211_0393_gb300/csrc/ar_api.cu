@@ -178,7 +178,7 @@ void prec_release(ar_prec* P, cudaStream_t s) {
 
 ar_status prec_build(const double* psf_host, int q1, int q2, int n1, int n2, double alpha,
                      int bc, int precision, cudaStream_t s, bool keep64, ar_prec** out,
-                     int correction, const ar_corr* model) {
+                     int correction, const ar_corr* model, bool grouped) {
     set_pool_threshold_once();
     ar_prec* P = new (std::nothrow) ar_prec();
     if (!P) return fail(AR_ERR_ALLOC, "host allocation of ar_prec");
@@ -230,7 +230,7 @@ ar_status prec_build(const double* psf_host, int q1, int q2, int n1, int n2, dou
         // the reblur stencil writes the transform input folded (q <= 15, TMA path)
         if (st == AR_OK)
             st = transform_plan_create(n1, n2, bc, precision, s, &P->plan,
-                                       (q1 > q2 ? q1 : q2) <= 15);
+                                       !grouped && (q1 > q2 ? q1 : q2) <= 15, !grouped);
         if (st == AR_OK) st = transform_set_filter(P->plan, P->d32, s);
     }
     if (st != AR_OK) {

@@ -28,8 +28,12 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <cstring>
 #include <mutex>
+#include <new>
+#include <vector>
 
 namespace ar {
 namespace {
@@ -751,6 +755,180 @@ cudaError_t launch_tiles(const ConvArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// ------------------------------------------------ batched stencils -------
+// Both stencils of one restoration iteration for many images in one persistent
+// launch: the residual blur r_j = g_j - A_j x_j of every image, then its
+// reblur z_j = A'_j r_j (written as the transform operand, or x_j += tau z_j in
+// plain mode).  Work items are single tiles, listed blur tiles first (largest
+// images first), then the reblur tiles in the same order; a device counter
+// hands them out.  A reblur tile of image j reads r_j around its tile, so it
+// waits (bounded) until every blur tile of image j is done: each finished blur
+// tile is published with a release increment of its image's counter, which the
+// reblur's loader acquires before it issues the TMA copy.  Items are taken in
+// list order, so every blur tile a waiting CTA depends on was taken earlier by
+// a running CTA that needs nothing to finish it: the waits cannot deadlock.
+// Each image has its own PSF support q (the tile code is instantiated for
+// q = 0..15 and chosen per item) and its own TMA maps with a halo box for its q.
+struct ConvJob {
+    CUtensorMap mx;          // blur input x_j, halo box of (q, G)
+    CUtensorMap mr;          // reblur input r_j
+    ConvArgs blur, reblur;
+    int q, ntx, ntiles;
+};
+
+template <int Q, class G>
+__device__ __forceinline__ void group_tile(const ConvArgs& a, float* box, float* coef, int r0,
+                                           int c0, int tid) {
+    constexpr int PADL = (Q + 3) & ~3;
+    constexpr int WB = TX + 2 * PADL;
+    load_coefs<Q>(a, coef, tid, TX * G::TY);
+    __syncthreads();
+    float* tile = box + (PADL - Q);
+    if (r0 - Q < 0 || r0 + G::TH + Q > a.n1 || c0 - Q < 0 || c0 + TX + Q > a.n2)
+        fixup_tile<Q, G>(a, tile, WB, r0, c0, tid, TX * G::TY);
+    if (a.mode == CONV_RESIDUAL || a.mode == CONV_AXPY)
+        compute_tile<Q, true, G>(a, tile, WB, coef, r0, c0);
+    else
+        compute_tile<Q, false, G>(a, tile, WB, coef, r0, c0);
+}
+
+template <class G>
+__device__ __forceinline__ void group_dispatch(int q, const ConvArgs& a, float* box, float* coef,
+                                               int r0, int c0, int tid) {
+    switch (q) {
+        case 0: group_tile<0, G>(a, box, coef, r0, c0, tid); break;
+        case 1: group_tile<1, G>(a, box, coef, r0, c0, tid); break;
+        case 2: group_tile<2, G>(a, box, coef, r0, c0, tid); break;
+        case 3: group_tile<3, G>(a, box, coef, r0, c0, tid); break;
+        case 4: group_tile<4, G>(a, box, coef, r0, c0, tid); break;
+        case 5: group_tile<5, G>(a, box, coef, r0, c0, tid); break;
+        case 6: group_tile<6, G>(a, box, coef, r0, c0, tid); break;
+        case 7: group_tile<7, G>(a, box, coef, r0, c0, tid); break;
+        case 8: group_tile<8, G>(a, box, coef, r0, c0, tid); break;
+        case 9: group_tile<9, G>(a, box, coef, r0, c0, tid); break;
+        case 10: group_tile<10, G>(a, box, coef, r0, c0, tid); break;
+        case 11: group_tile<11, G>(a, box, coef, r0, c0, tid); break;
+        case 12: group_tile<12, G>(a, box, coef, r0, c0, tid); break;
+        case 13: group_tile<13, G>(a, box, coef, r0, c0, tid); break;
+        case 14: group_tile<14, G>(a, box, coef, r0, c0, tid); break;
+        default: group_tile<15, G>(a, box, coef, r0, c0, tid); break;
+    }
+}
+
+// Polls of a reblur tile's wait for its image's blur tiles (each poll sleeps
+// about 0.1 us: about 0.4 s in all).
+constexpr uint32_t kDepPolls = 1u << 22;
+
+// ctr[0]: the queue's next item; ctr[1 + j]: finished blur tiles of image j
+// (zero at launch); buf: bytes of one halo buffer (the largest q's box).
+template <class G>
+__global__ void __launch_bounds__(TX * G::TY)
+conv_group_kernel(const ConvJob* __restrict__ jobs, const int2* __restrict__ items, int nblur,
+                  int nitems, int* __restrict__ ctr, int iter, uint32_t buf) {
+    using namespace tc;
+    extern __shared__ __align__(128) uint8_t smem_raw_c[];
+    uint8_t* sbase = smem_raw_c + ((128u - (smem_u32(smem_raw_c) & 127u)) & 127u);
+    float* coef = reinterpret_cast<float*>(sbase + 2 * buf);
+    const uint32_t bar0 = smem_u32(coef + Coefs<QMAX_FAST>::COUNT);   // two mbarriers
+    volatile int* slot = reinterpret_cast<volatile int*>(coef + Coefs<QMAX_FAST>::COUNT + 4);
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    auto box = [&](int b) { return reinterpret_cast<float*>(sbase + b * buf); };
+    if (tid == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar0 + 8u, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    pdl_wait();                          // x_j and the planes come from the previous kernels
+    const uint32_t polls = g_conv_wait_polls;
+    bool req[2] = {false, false};        // thread 0: a copy into buffer b is in flight / landed
+    auto request = [&](int item, int b) {
+        const int2 w = items[item];
+        const ConvJob& J = jobs[w.x];
+        const int r0 = (w.y / J.ntx) * G::TH, c0 = (w.y % J.ntx) * TX;
+        const int padl = (J.q + 3) & ~3;
+        const uint32_t bytes = (uint32_t)(TX + 2 * padl) * (uint32_t)(G::TH + 2 * J.q) * 4u;
+        fence_proxy_async_smem();        // generic writes to the buffer (fix-up) before the copy
+        mbar_arrive_expect_tx(bar0 + 8u * b, bytes);
+        tma_load_2d(smem_u32(box(b)), item >= nblur ? &J.mr : &J.mx, c0 - padl, r0 - J.q,
+                    bar0 + 8u * b);
+        req[b] = true;
+    };
+    auto ready = [&](int item) {         // a reblur tile's image has all its blur tiles done
+        if (item < nblur) return true;
+        const int j = items[item].x;
+        return ld_acquire_gpu(ctr + 1 + j) >= jobs[j].ntiles;
+    };
+    if (tid == 0) {
+        const int it = atomicAdd(ctr, 1);
+        slot[0] = it;
+        if (it < nitems && ready(it)) {
+            fence_proxy_async_global();
+            request(it, 0);
+        }
+        slot[2] = 0;
+    }
+    int li = 0;
+    bool failed = false;
+    for (;; ++li) {
+        const int b = li & 1;
+        __syncthreads();                 // slot[b] is set; buffer b ^ 1 and coef are free
+        const int item = slot[b];
+        if (item >= nitems) break;
+        if (tid == 0) {
+            if (!req[b]) {               // the image's blur tiles were not done at dequeue
+                uint32_t i = 0;
+                for (; i < kDepPolls && !ready(item); ++i) __nanosleep(100);
+                if (i == kDepPolls) {
+                    slot[2] = 1;
+                } else {
+                    fence_proxy_async_global();
+                    request(item, b);
+                }
+            }
+            if (!slot[2]) {              // the next item, prefetched when it can start
+                const int nx = atomicAdd(ctr, 1);
+                slot[b ^ 1] = nx;
+                if (nx < nitems && ready(nx)) {
+                    fence_proxy_async_global();
+                    request(nx, b ^ 1);
+                }
+            }
+        }
+        __syncthreads();
+        if (slot[2]) {
+            failed = true;
+            break;
+        }
+        const bool ok = mbar_wait(bar0 + 8u * b, (li >> 1) & 1, polls);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        if (tid == 0) req[b] = false;
+        const int2 w = items[item];
+        const ConvJob& J = jobs[w.x];
+        const bool re = item >= nblur;
+        ConvArgs a = re ? J.reblur : J.blur;
+        if (a.sumsq) a.sumsq += iter;
+        const int r0 = (w.y / J.ntx) * G::TH, c0 = (w.y % J.ntx) * TX;
+        group_dispatch<G>(J.q, a, box(b), coef, r0, c0, tid);
+        if (!re) {
+            __syncthreads();             // the tile's r is written
+            if (tid == 0) {
+                __threadfence();
+                red_release_add_gpu(ctr + 1 + w.x, 1);
+            }
+        }
+    }
+    pdl_trigger();
+    if (failed && tid == 0) {
+        atomicExch(&g_conv_timeout, 1);
+        for (int k = 0; k < 2; ++k)      // copies still in flight (bounded)
+            if (req[k]) mbar_wait(bar0 + 8u * k, ((li + ((k - li) & 1)) >> 1) & 1);
+    }
+}
+
 }  // namespace
 
 int* conv_error_flag() {
@@ -762,6 +940,161 @@ int* conv_error_flag() {
         if (cudaGetSymbolAddress(&q, g_conv_timeout) == cudaSuccess) p[dev] = static_cast<int*>(q);
     }
     return p[dev];
+}
+
+// ------------------------------------------------ batched stencils (host) --
+namespace {
+
+// TMA map of a float32 n1 x n2 image with the halo box of support q, geometry G.
+bool make_box_map(const float* img, int n1, int n2, int q, int th, CUtensorMap* map) {
+    auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder());
+    if (!enc) return false;
+    const int padl = (q + 3) & ~3;
+    cuuint64_t dims[2] = {(cuuint64_t)n2, (cuuint64_t)n1};
+    cuuint64_t strides[1] = {(cuuint64_t)n2 * 4};
+    cuuint32_t box[2] = {(cuuint32_t)(TX + 2 * padl), (cuuint32_t)(th + 2 * q)};
+    cuuint32_t es[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(img), dims, strides, box,
+               es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+uint32_t box_bytes(int q, int th) {
+    const int padl = (q + 3) & ~3;
+    return ((uint32_t)(TX + 2 * padl) * (uint32_t)(th + 2 * q) * 4u + 127u) & ~127u;
+}
+
+template <class G>
+cudaError_t group_attr(size_t smem, int* per_sm) {
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(conv_group_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    96 * 1024);
+    });
+    if (attr != cudaSuccess) return attr;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, conv_group_kernel<G>,
+                                                         TX * G::TY, smem);
+}
+
+}  // namespace
+
+struct ConvGroup {
+    int geometry = 0, count = 0, nblur = 0, nitems = 0, grid = 0, iters = 0, stride = 0;
+    int ctas_per_sm = 0;
+    uint32_t buf = 0;
+    size_t smem = 0;
+    ConvJob* jobs = nullptr;
+    int2* items = nullptr;
+    int* ctr = nullptr;
+};
+
+void conv_group_destroy(ConvGroup* g) {
+    if (!g) return;
+    cudaFree(g->jobs);
+    cudaFree(g->items);
+    cudaFree(g->ctr);
+    delete g;
+}
+
+int conv_group_ctas_per_sm(const ConvGroup* g) { return g->ctas_per_sm; }
+
+ar_status conv_group_create(const ConvArgs* blurs, const ConvArgs* reblurs, int count, int geometry,
+                            int ctas_per_sm, int iters, ConvGroup** out) {
+    if (count < 1 || iters < 1 || (geometry != 0 && geometry != 1) || ctas_per_sm < 1)
+        return fail(AR_ERR_INVALID_ARG, "batched stencil: count %d, iters %d, geometry %d", count,
+                    iters, geometry);
+    const int th = geometry == 0 ? G64::TH : G54::TH;
+    std::vector<ConvJob> jobs((size_t)count);
+    std::vector<double> cost((size_t)count);
+    int qmax = 0;
+    for (int j = 0; j < count; ++j) {
+        const ConvArgs& b = blurs[j];
+        const ConvArgs& r = reblurs[j];
+        const int q = b.q1 > b.q2 ? b.q1 : b.q2;
+        if (q > QMAX_FAST || b.bc == AR_BC_PERIODIC || (b.n2 & 3) != 0 ||
+            (reinterpret_cast<uintptr_t>(b.x) & 15) != 0 || (reinterpret_cast<uintptr_t>(r.x) & 15) != 0 ||
+            b.mode != CONV_RESIDUAL || r.fold)
+            return fail(AR_ERR_UNSUPPORTED,
+                        "batched stencil: image %d needs q <= 15, n2 %% 4 == 0, aligned rows, "
+                        "an unfolded reblur and a non-periodic BC", j);
+        ConvJob& J = jobs[(size_t)j];
+        std::memset(&J, 0, sizeof(J));
+        J.blur = b;
+        J.reblur = r;
+        J.q = q;
+        J.ntx = (b.n2 + TX - 1) / TX;
+        J.ntiles = J.ntx * ((b.n1 + th - 1) / th);
+        if (!make_box_map(b.x, b.n1, b.n2, q, th, &J.mx) || !make_box_map(r.x, r.n1, r.n2, q, th, &J.mr))
+            return fail(AR_ERR_CUDA, "batched stencil: tensor map of image %d", j);
+        cost[(size_t)j] = (double)b.n1 * b.n2 * (2 * q + 1) * (2 * q + 1);
+        qmax = q > qmax ? q : qmax;
+    }
+    // largest images first (the longest work first balances the tail), blur then reblur
+    std::vector<int> order((size_t)count);
+    for (int j = 0; j < count; ++j) order[(size_t)j] = j;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[(size_t)a] > cost[(size_t)b]; });
+    std::vector<int2> items;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int j : order)
+            for (int t = 0; t < jobs[(size_t)j].ntiles; ++t) items.push_back(make_int2(j, t));
+    ConvGroup* g = new (std::nothrow) ConvGroup();
+    if (!g) return fail(AR_ERR_ALLOC, "host allocation of the batched stencil");
+    g->geometry = geometry;
+    g->count = count;
+    g->nitems = (int)items.size();
+    g->nblur = g->nitems / 2;
+    g->iters = iters;
+    g->stride = 1 + count;
+    g->buf = box_bytes(qmax, th);
+    g->smem = 2 * (size_t)g->buf + (size_t)Coefs<QMAX_FAST>::COUNT * 4 + 64 + 128;
+    int per_sm = 0;
+    cudaError_t e = geometry == 0 ? group_attr<G64>(g->smem, &per_sm) : group_attr<G54>(g->smem, &per_sm);
+    if (e != cudaSuccess || per_sm < 1) {
+        conv_group_destroy(g);
+        return e != cudaSuccess ? cuda_fail(e, "batched stencil occupancy")
+                                : fail(AR_ERR_UNSUPPORTED, "batched stencil does not fit an SM");
+    }
+    g->ctas_per_sm = ctas_per_sm < per_sm ? ctas_per_sm : per_sm;
+    const int cap = g->ctas_per_sm * sm_count();
+    g->grid = g->nitems < cap ? g->nitems : cap;
+    e = cudaMalloc((void**)&g->jobs, jobs.size() * sizeof(ConvJob));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&g->items, items.size() * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&g->ctr, (size_t)iters * g->stride * sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(g->jobs, jobs.data(), jobs.size() * sizeof(ConvJob), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(g->items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(g->ctr, 0, (size_t)iters * g->stride * sizeof(int));
+    if (e != cudaSuccess) {
+        conv_group_destroy(g);
+        return cuda_fail(e, "batched stencil buffers");
+    }
+    *out = g;
+    return AR_OK;
+}
+
+ar_status conv_group_reset(ConvGroup* g, cudaStream_t s) {
+    AR_CUDA(cudaMemsetAsync(g->ctr, 0, (size_t)g->iters * g->stride * sizeof(int), s));
+    return AR_OK;
+}
+
+ar_status conv_group_apply(ConvGroup* g, int iter, cudaStream_t s) {
+    if (iter < 0 || iter >= g->iters) return fail(AR_ERR_INVALID_ARG, "iteration %d of %d", iter, g->iters);
+    ProfScope prof(AR_PROF_STENCIL, s);
+    count_launch();
+    int* ctr = g->ctr + (size_t)iter * g->stride;
+    cudaError_t e;
+    if (g->geometry == 0)
+        e = launch_pdl(conv_group_kernel<G64>, dim3(g->grid), dim3(TX, G64::TY), g->smem, s,
+                       (const ConvJob*)g->jobs, (const int2*)g->items, g->nblur, g->nitems, ctr,
+                       iter, g->buf);
+    else
+        e = launch_pdl(conv_group_kernel<G54>, dim3(g->grid), dim3(TX, G54::TY), g->smem, s,
+                       (const ConvJob*)g->jobs, (const int2*)g->items, g->nblur, g->nitems, ctr,
+                       iter, g->buf);
+    if (e != cudaSuccess) return cuda_fail(e, "batched stencil launch");
+    return AR_OK;
 }
 
 ar_status conv_set_wait_polls(unsigned polls) {

@@ -474,8 +474,13 @@ ar_status ar_corr_predict(const ar_corr* M, const double* psf_host, float* table
     return st;
 }
 
-ar_status ar_corr_train(ar_corr* M, const double* psfs_host, int count, int epochs, int batch,
-                        double lr, float* loss_trace_host, void* stream) {
+}  // extern "C"
+
+// Adam on the model's mean squared error against the closed-form targets
+// (tables_host null) or given target tables (count x 33 x 33 float64).
+static ar_status corr_train(ar_corr* M, const double* psfs_host, const double* tables_host,
+                            int count, int epochs, int batch, double lr, float* loss_trace_host,
+                            void* stream) {
     if (!M || !psfs_host) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
     if (!corr_on_current_device(M)) return fail(AR_ERR_INVALID_ARG, "model belongs to another device");
     if (count < 1 || epochs < 0 || batch < 1)
@@ -483,6 +488,10 @@ ar_status ar_corr_train(ar_corr* M, const double* psfs_host, int count, int epoc
     if (!(lr > 0.0) || !std::isfinite(lr))
         return fail(AR_ERR_INVALID_ARG, "learning rate must be finite and > 0");
     AR_TRY(check_psfs15(psfs_host, count));
+    if (tables_host)
+        for (size_t i = 0; i < (size_t)count * COUT; ++i)
+            if (!std::isfinite(tables_host[i]))
+                return fail(AR_ERR_INVALID_ARG, "target table entry %zu is not finite", i);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int B = batch < count ? batch : count;
     std::vector<void*> bufs;
@@ -509,10 +518,20 @@ ar_status ar_corr_train(ar_corr* M, const double* psfs_host, int count, int epoc
     if (e == cudaSuccess)
         e = cudaMemsetAsync(loss, 0, (size_t)(epochs > 0 ? epochs : 1) * sizeof(double), s);
     ar_status st = e == cudaSuccess ? AR_OK : cuda_fail(e, "training buffers");
+    std::vector<float> t32;
+    if (st == AR_OK && tables_host) {
+        t32.resize((size_t)count * COUT);
+        for (size_t i = 0; i < t32.size(); ++i) t32[i] = (float)tables_host[i];
+        e = cudaMemcpyAsync(T, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) st = cuda_fail(e, "target upload");
+    }
     if (st == AR_OK) {
         corr_input_kernel<<<count, 256, 0, s>>>(h, X);
-        corr_target_kernel<<<count, 256, 0, s>>>(h, nullptr, T);
-        count_launch(2);
+        count_launch();
+        if (!tables_host) {
+            corr_target_kernel<<<count, 256, 0, s>>>(h, nullptr, T);
+            count_launch();
+        }
         if (cudaGetLastError() != cudaSuccess) st = fail(AR_ERR_CUDA, "target kernels");
     }
     const int nb = (count + B - 1) / B;
@@ -586,6 +605,21 @@ ar_status ar_corr_train(ar_corr* M, const double* psfs_host, int count, int epoc
     if (loss_trace_host)
         for (int ep = 0; ep < epochs; ++ep) loss_trace_host[ep] = (float)(lh[ep] / nb);
     return AR_OK;
+}
+
+extern "C" {
+
+ar_status ar_corr_train(ar_corr* M, const double* psfs_host, int count, int epochs, int batch,
+                        double lr, float* loss_trace_host, void* stream) {
+    return corr_train(M, psfs_host, nullptr, count, epochs, batch, lr, loss_trace_host, stream);
+}
+
+ar_status ar_corr_train_tables(ar_corr* M, const double* psfs_host, const double* tables_host,
+                               int count, int epochs, int batch, double lr,
+                               float* loss_trace_host, void* stream) {
+    if (!tables_host) return fail(AR_ERR_INVALID_ARG, "null pointer argument (tables)");
+    return corr_train(M, psfs_host, tables_host, count, epochs, batch, lr, loss_trace_host,
+                      stream);
 }
 
 }  // extern "C"

@@ -101,10 +101,57 @@ int* conv_error_flag();
 // Sets the polls of the stencils' halo-tile waits on the current device.
 ar_status conv_set_wait_polls(unsigned polls);
 
+// Both stencils of a restoration iteration for many images in one persistent
+// launch (ar_conv.cu): blurs[j] (CONV_RESIDUAL, x_j -> r_j) then reblurs[j]
+// (CONV_SPLIT3 unfolded, or CONV_AXPY; input r_j; sumsq, if set, is the base of
+// one float64 per iteration).  geometry 0: 64-row tiles, 1: 54-row tiles;
+// ctas_per_sm: persistent CTAs per SM (capped by occupancy); iters: iterations
+// per run (each uses its own queue counters, zeroed by conv_group_reset).
+struct ConvGroup;
+ar_status conv_group_create(const ConvArgs* blurs, const ConvArgs* reblurs, int count, int geometry,
+                            int ctas_per_sm, int iters, ConvGroup** out);
+ar_status conv_group_reset(ConvGroup* g, cudaStream_t s);
+ar_status conv_group_apply(ConvGroup* g, int iter, cudaStream_t s);
+int conv_group_ctas_per_sm(const ConvGroup* g);
+void conv_group_destroy(ConvGroup* g);
+
 // cuTensorMapEncodeTiled from the driver (null if unavailable), as void*.
 void* tensor_map_encoder();
 
 // ------------------------------------------------------------ transform ---
+// Even/odd folds of one axis of length m (the AR transform's reflection
+// symmetry): h = ceil(m/2) sums, ha = floor(m/2) differences; spectral halves
+// padded to Hs (a multiple of 128), folded spatial halves to Kh (of 64).
+struct FoldDims {
+    int m, h, ha, Hs, Kh;
+};
+
+__host__ __device__ inline FoldDims fold_dims(int m) {
+    FoldDims f;
+    f.m = m;
+    f.h = (m + 1) / 2;
+    f.ha = m / 2;
+    f.Hs = (f.h + 127) / 128 * 128;
+    f.Kh = (f.h + 63) / 64 * 64;
+    return f;
+}
+
+// Folded spectral index kf -> kind (0 u+, 1 odd interior, 2 u-, 3 even interior,
+// -1 padding) and the natural spectral index s: the first half holds u+ (the
+// sum of the two boundary coefficients) and s = 1, 3, 5, ..; the second u- and
+// s = 2, 4, ...
+__device__ __forceinline__ int spec_of(int kf, const FoldDims& f, int& s) {
+    const bool anti = kf >= f.Hs;
+    const int u = anti ? kf - f.Hs : kf;
+    if (u == 0) {
+        s = 0;
+        return anti ? 2 : 0;
+    }
+    s = anti ? 2 * u : 2 * u - 1;
+    if (s > f.m - 2) return -1;
+    return anti ? 3 : 1;
+}
+
 // The transform pair of a boundary condition for one image size, applied as
 // dense contractions (four for AR and Reflective, seven for Periodic).
 // Implemented in ar_transform.cu.
@@ -114,8 +161,12 @@ struct TransformPlan;
 // AR_PRECISION_BF16X2 (two planes, three products); bc: an ar_bc value.
 // fold_input: the stencil producing the DIN_SPLIT input can write it folded
 // along the columns (AR plans then take it so when n2 is a multiple of 4).
+// pair_out: AR plans may run their last contraction in parity-paired clusters
+// of four when that fits (false: always the unpaired kernel, as grouped
+// launches need).
 ar_status transform_plan_create(int n1, int n2, int bc, int precision, cudaStream_t stream,
-                                TransformPlan** out, bool fold_input = false);
+                                TransformPlan** out, bool fold_input = false,
+                                bool pair_out = true);
 void transform_plan_destroy(TransformPlan* p);
 // Frees the plan's buffers in the order of stream s (after its pending work).
 void transform_plan_release(TransformPlan* p, cudaStream_t s);
@@ -154,8 +205,26 @@ ar_status transform_apply(TransformPlan* p, const float* d32, const float* d32_o
 // Number of kernels one transform_apply launches (for launch accounting).
 int transform_launches(const TransformPlan* p, DInput din);
 
+// The four contractions of x_j += tau D_j z_j for many AR plans in four grouped
+// launches (one per contraction, every plan's tiles as work items, largest K
+// first).  Each plan must be unpaired (transform_plan_create with pair_out
+// false) and read its input as written by its reblur (DIN_SPLIT); fs[j] (may be
+// null) and sumsq[j] give the RRE accumulation, sumsq[j] + iter per iteration.
+struct TransformGroup;
+ar_status transform_group_create(TransformPlan* const* plans, int count, float* const* outs,
+                                 const float* const* fs, double* const* sumsq, float tau,
+                                 TransformGroup** out);
+ar_status transform_group_apply(TransformGroup* g, int iter, cudaStream_t s);
+void transform_group_destroy(TransformGroup* g);
+
 // Device int set to 1 by a contraction kernel whose bounded wait gave up.
 int* transform_error_flag(TransformPlan* p);
+
+// The spectral operand W = d o (T~ y) of the last transform_apply of an AR
+// plan in the folded order of both axes: bf16 planes [nplanes][N1][ld],
+// N1 = 2 Hs(n1) rows, N2 = 2 Hs(n2) columns, and the folded filter (N1 x N2).
+ar_status transform_spectral_view(const TransformPlan* p, const uint16_t** planes,
+                                  size_t* pstride, int* ld, int* nplanes, const float** dfold);
 
 // ---------------------------------------------------------------- setup ---
 // FP64 eigenvalue setup on the GPU.  AR and Reflective: symmetrize (eq.
@@ -198,9 +267,10 @@ void set_pool_threshold_once();
 void prec_release(ar_prec* P, cudaStream_t s);
 
 // correction: 0 none, 1 exact spectral correction, 2 the model's (AR only).
+// grouped: the plan serves grouped launches (unfolded input, unpaired G4).
 ar_status prec_build(const double* psf_host, int q1, int q2, int n1, int n2, double alpha,
                      int bc, int precision, cudaStream_t s, bool keep64, ar_prec** out,
-                     int correction = 0, const ar_corr* model = nullptr);
+                     int correction = 0, const ar_corr* model = nullptr, bool grouped = false);
 
 // ----------------------------------------------------- spectral correction
 // delta of the PSF (device float64) on the AR grid of an n1 x n2 image into

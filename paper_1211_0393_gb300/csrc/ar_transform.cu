@@ -54,7 +54,10 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdlib>
+#include <cstring>
+#include <vector>
 #include <map>
 #include <tuple>
 #include <mutex>
@@ -174,10 +177,13 @@ constexpr int WCOLS = HALF / 2;         // columns of the CTA's half handled by 
 
 // The body of both contraction kernels: clusters of (1, 1, SPLITK) CTAs, or
 // (1, 2, SPLITK) with the parity pairs of N (NPAR, ep.npar set).
+// (bx, by) is the tile of the launch grid this cluster computes (blockIdx.x,
+// blockIdx.y in a plain launch; a work item's tile in a grouped one).
 template <int NP, bool NPAR>
 __device__ __forceinline__ void tc_contract_body(const CUtensorMap& tmA, const CUtensorMap& tmA64,
                                                  const CUtensorMap& tmB, const CUtensorMap& tmO,
-                                                 int M, int N, int K, const TcEpiArgs& ep, int* err) {
+                                                 int M, int N, int K, const TcEpiArgs& ep, int* err,
+                                                 int bx, int by) {
     using namespace tc;
     using Mode = TcMode<NP>;
     constexpr int STAGES = Mode::STAGES;
@@ -205,8 +211,8 @@ __device__ __forceinline__ void tc_contract_body(const CUtensorMap& tmA, const C
     const uint32_t ks = NPAR ? crank >> 1 : crank;                // split-K half
     const uint32_t kpeer = NPAR ? crank ^ 2u : crank ^ 1u;        // the other split-K half
     const int parity = NPAR ? (int)(crank & 1u) : 0;
-    const int m0 = blockIdx.x * (ep.pair ? BM / 2 : BM);
-    const int n0 = NPAR ? (int)(blockIdx.y >> 1) * BN + parity * ep.nhalf : (int)blockIdx.y * BN;
+    const int m0 = bx * (ep.pair ? BM / 2 : BM);
+    const int n0 = NPAR ? (by >> 1) * BN + parity * ep.nhalf : by * BN;
     // with NPAR the cluster is (1, 2, SPLITK): checked, not assumed
     const bool rank_ok = !NPAR || (cluster_ctaid_y() == (blockIdx.y & 1u) &&
                                    cluster_ctaid_z() == blockIdx.z &&
@@ -542,7 +548,7 @@ __global__ void __cluster_dims__(1, 1, SPLITK) __launch_bounds__(NTHREADS, 1)
 tc_contract_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA64,
                    const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmO,
                    int M, int N, int K, const TcEpiArgs ep, int* err) {
-    tc_contract_body<NP, false>(tmA, tmA64, tmB, tmO, M, N, K, ep, err);
+    tc_contract_body<NP, false>(tmA, tmA64, tmB, tmO, M, N, K, ep, err, blockIdx.x, blockIdx.y);
 }
 
 // npar: the parity pairs of N in the same cluster
@@ -551,7 +557,31 @@ __global__ void __cluster_dims__(1, 2, SPLITK) __launch_bounds__(NTHREADS, 1)
 tc_contract_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA64,
                         const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmO,
                         int M, int N, int K, const TcEpiArgs ep, int* err) {
-    tc_contract_body<NP, true>(tmA, tmA64, tmB, tmO, M, N, K, ep, err);
+    tc_contract_body<NP, true>(tmA, tmA64, tmB, tmO, M, N, K, ep, err, blockIdx.x, blockIdx.y);
+}
+
+// One contraction of many independent problems (the images of a batch) in one
+// launch.  Every work item is one output tile of one problem; items are listed
+// largest K first, and each cluster takes the item of its blockIdx.x, so the
+// block scheduler hands the remaining items to clusters as SMs free up.  The
+// problems' tensor maps and epilogues live in device memory (64-byte aligned
+// maps, written before the launch).  `iter` offsets each problem's RRE
+// accumulator (one float64 per iteration).
+struct GroupJob {
+    CUtensorMap tmA, tmA64, tmB, tmO;
+    int M, N, K;
+    TcEpiArgs ep;
+    int* err;
+};
+
+template <int NP>
+__global__ void __cluster_dims__(1, 1, SPLITK) __launch_bounds__(NTHREADS, 1)
+tc_contract_group_kernel(const GroupJob* __restrict__ jobs, const int4* __restrict__ items, int iter) {
+    const int4 it = items[blockIdx.x];                    // (job, m tile, n tile, -)
+    const GroupJob& J = jobs[it.x];
+    TcEpiArgs ep = J.ep;
+    if (ep.sumsq) ep.sumsq += iter;
+    tc_contract_body<NP, false>(J.tmA, J.tmA64, J.tmB, J.tmO, J.M, J.N, J.K, ep, J.err, it.y, it.z);
 }
 
 // ---------------------------------------------------------------- matrices --
@@ -660,32 +690,6 @@ __global__ void fill_bc_transforms_kernel(int m, int ld, int bc, uint16_t* Tt, u
 // padded: spectral and folded-output to a multiple of 128 rows (Hs), folded
 // spatial K to a multiple of 64 (Kh).  The filter d is equal at spectral
 // indices 0 and m-1, so it applies to u+ and u- alike.
-struct FoldDims {
-    int m, h, ha, Hs, Kh;               // h = ceil(m/2), ha = floor(m/2)
-};
-
-__host__ __device__ inline FoldDims fold_dims(int m) {
-    FoldDims f;
-    f.m = m;
-    f.h = (m + 1) / 2;
-    f.ha = m / 2;
-    f.Hs = (f.h + 127) / 128 * 128;
-    f.Kh = (f.h + 63) / 64 * 64;
-    return f;
-}
-
-// spectral folded index kf -> kind (0 u+, 1 odd interior, 2 u-, 3 even interior, -1 padding), s
-__device__ __forceinline__ int spec_of(int kf, const FoldDims& f, int& s) {
-    const bool anti = kf >= f.Hs;
-    const int u = anti ? kf - f.Hs : kf;
-    if (u == 0) {
-        s = 0;
-        return anti ? 2 : 0;
-    }
-    s = anti ? 2 * u : 2 * u - 1;
-    if (s > f.m - 2) return -1;
-    return anti ? 3 : 1;
-}
 
 // T~'_m[s][t] (normalisation dropped), T'_m[s][t] interior columns only
 __device__ __forceinline__ double ar_tt(int s, int t, int m, const double* tab, const double* qp,
@@ -1051,7 +1055,7 @@ struct TransformPlan {
 };
 
 ar_status transform_plan_create(int n1, int n2, int bc, int precision, cudaStream_t s,
-                                TransformPlan** out, bool fold_input) {
+                                TransformPlan** out, bool fold_input, bool pair_out) {
     TransformPlan* p = new (std::nothrow) TransformPlan();
     if (!p) return fail(AR_ERR_ALLOC, "host allocation of the transform plan");
     p->n1 = n1;
@@ -1066,7 +1070,7 @@ ar_status transform_plan_create(int n1, int n2, int bc, int precision, cudaStrea
         const FoldDims f1 = fold_dims(n1), f2 = fold_dims(n2);
         const int need = ((f2.h + BM / 2 - 1) / (BM / 2)) * (f1.Hs / BN);
         const int fit = p->np == 2 ? max_quad_clusters<2>() : max_quad_clusters<3>();
-        p->fold_out = fit > 0 && (need <= fit || need > 2 * fit);
+        p->fold_out = pair_out && fit > 0 && (need <= fit || need > 2 * fit);
     }
     TransformSet t1, t2;
     ar_status st = cached_transforms(n1, bc, s, &t1);
@@ -1158,6 +1162,188 @@ uint16_t* transform_input_planes(TransformPlan* p, size_t* plane_stride, int* ld
 }
 
 int* transform_error_flag(TransformPlan* p) { return p->err; }
+
+ar_status transform_spectral_view(const TransformPlan* p, const uint16_t** planes,
+                                  size_t* pstride, int* ld, int* nplanes, const float** dfold) {
+    if (!p->folded) return fail(AR_ERR_UNSUPPORTED, "spectral view of a non-AR plan");
+    *planes = p->W.planes;
+    *pstride = p->W.pstride;
+    *ld = p->W.ld;
+    *nplanes = p->np;
+    *dfold = p->dfold;
+    return AR_OK;
+}
+
+// ------------------------------------------------------ grouped transforms --
+// The four contractions of x += tau D z for many AR plans, one grouped launch
+// per contraction (tc_contract_group_kernel): every plan's tiles of G1, then of
+// G2, ... as work items, largest K first.  Each plan's input planes must have
+// been written by its reblur (DIN_SPLIT); its G4 must be the unpaired one.
+struct TransformGroup {
+    int np = 3, count = 0;
+    GroupJob* jobs[4] = {nullptr, nullptr, nullptr, nullptr};
+    int4* items[4] = {nullptr, nullptr, nullptr, nullptr};
+    int nitems[4] = {0, 0, 0, 0};
+};
+
+void transform_group_destroy(TransformGroup* g) {
+    if (!g) return;
+    for (int k = 0; k < 4; ++k) {
+        cudaFree(g->jobs[k]);
+        cudaFree(g->items[k]);
+    }
+    delete g;
+}
+
+namespace {
+template <int NP>
+cudaError_t group_kernel_attr() {
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(tc_contract_group_kernel<NP>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)TcMode<NP>::SMEM_BYTES);
+    });
+    return attr;
+}
+}  // namespace
+
+ar_status transform_group_create(TransformPlan* const* plans, int count, float* const* outs,
+                                 const float* const* fs, double* const* sumsq, float tau,
+                                 TransformGroup** out) {
+    if (count < 1) return fail(AR_ERR_INVALID_ARG, "empty transform group");
+    const int np = plans[0]->np;
+    for (int j = 0; j < count; ++j) {
+        const TransformPlan* p = plans[j];
+        if (!p->folded || p->fold_out || p->np != np)
+            return fail(AR_ERR_UNSUPPORTED, "grouped transform: plan %d is not an unpaired AR "
+                                            "plan of the group's precision", j);
+    }
+    const int mi = mode_index(np);
+    std::vector<GroupJob> jobs[4];
+    std::vector<std::pair<int, int4>> items[4];          // (K of the tile, item)
+    for (int j = 0; j < count; ++j) {
+        TransformPlan* p = plans[j];
+        const FoldDims f1 = fold_dims(p->n1), f2 = fold_dims(p->n2);
+        TcEpiArgs e[4] = {};
+        const Operand* A[4];
+        const Operand* B[4];
+        const Operand* O[4];
+        // as transform_apply's folded chain (DIN_SPLIT, DOUT_AXPY)
+        e[0].mode = TE_SPLIT_T;
+        e[0].planes = p->U.planes;
+        e[0].pstride = p->U.pstride;
+        e[0].ld = p->U.ld;
+        e[0].pair = PAIR_MIRROR;
+        e[0].mrows = p->n1;
+        e[0].npair = f1.h;
+        e[0].nminus = f1.ha;
+        e[0].kout = f1.Kh;
+        e[0].kdiag = p->fold_y ? 1 : 0;
+        A[0] = &p->P;
+        B[0] = p->fold_y ? &p->Ttf2 : &p->Ttp2;
+        O[0] = &p->U;
+        e[1].mode = TE_SCALE_SPLIT_T;
+        e[1].planes = p->W.planes;
+        e[1].pstride = p->W.pstride;
+        e[1].ld = p->W.ld;
+        e[1].d = p->dfold;
+        e[1].ldd = 2 * f2.Hs;
+        e[1].kdiag = 1;
+        A[1] = &p->U;
+        B[1] = &p->Ttf1;
+        O[1] = &p->W;
+        e[2].mode = TE_SPLIT_T;
+        e[2].planes = p->V.planes;
+        e[2].pstride = p->V.pstride;
+        e[2].ld = p->V.ld;
+        e[2].kdiag = 1;
+        A[2] = &p->W;
+        B[2] = &p->Tsf2;
+        O[2] = &p->V;
+        e[3].mode = TE_AXPY_T;
+        e[3].out = outs[j];
+        e[3].ldo = p->n2;
+        e[3].tau = tau;
+        e[3].f = fs ? fs[j] : nullptr;
+        e[3].sumsq = (fs && fs[j] && sumsq) ? sumsq[j] : nullptr;
+        e[3].pair = PAIR_HALVES;
+        e[3].mhalf = f2.Hs;
+        e[3].npair = f2.h;
+        e[3].nminus = f2.ha;
+        e[3].nout = p->n2;
+        e[3].late_trigger = 1;
+        A[3] = &p->V;
+        B[3] = &p->Tsp1;
+        O[3] = nullptr;
+        for (int k = 0; k < 4; ++k) {
+            GroupJob gj;
+            std::memset(&gj, 0, sizeof(gj));
+            gj.tmA = A[k]->map[mi];
+            gj.tmA64 = e[k].pair ? A[k]->map64[mi] : A[k]->map[mi];
+            gj.tmB = B[k]->map[mi];
+            gj.tmO = !O[k] ? A[k]->map[mi]
+                           : (e[k].pair == PAIR_MIRROR ? O[k]->omapf[mi] : O[k]->omap[mi]);
+            gj.M = A[k]->rows;
+            gj.N = B[k]->rows;
+            gj.K = A[k]->K;
+            gj.ep = e[k];
+            gj.err = p->err;
+            const int mt = e[k].pair ? (e[k].npair + BM / 2 - 1) / (BM / 2) : (A[k]->rows + BM - 1) / BM;
+            const int nt = (B[k]->rows + BN - 1) / BN;
+            const int keff = e[k].kdiag ? A[k]->K / 2 : A[k]->K;
+            const int job = (int)jobs[k].size();
+            jobs[k].push_back(gj);
+            for (int a = 0; a < mt; ++a)
+                for (int b = 0; b < nt; ++b) items[k].push_back({keff, make_int4(job, a, b, 0)});
+        }
+    }
+    TransformGroup* g = new (std::nothrow) TransformGroup();
+    if (!g) return fail(AR_ERR_ALLOC, "host allocation of the transform group");
+    g->np = np;
+    g->count = count;
+    cudaError_t ce = np == 2 ? group_kernel_attr<2>() : group_kernel_attr<3>();
+    for (int k = 0; ce == cudaSuccess && k < 4; ++k) {
+        std::stable_sort(items[k].begin(), items[k].end(),
+                         [](const std::pair<int, int4>& a, const std::pair<int, int4>& b) {
+                             return a.first > b.first;
+                         });
+        std::vector<int4> it(items[k].size());
+        for (size_t i = 0; i < it.size(); ++i) it[i] = items[k][i].second;
+        g->nitems[k] = (int)it.size();
+        ce = cudaMalloc((void**)&g->jobs[k], jobs[k].size() * sizeof(GroupJob));
+        if (ce == cudaSuccess) ce = cudaMalloc((void**)&g->items[k], it.size() * sizeof(int4));
+        if (ce == cudaSuccess)
+            ce = cudaMemcpy(g->jobs[k], jobs[k].data(), jobs[k].size() * sizeof(GroupJob),
+                            cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpy(g->items[k], it.data(), it.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    }
+    if (ce != cudaSuccess) {
+        transform_group_destroy(g);
+        return cuda_fail(ce, "transform group buffers");
+    }
+    *out = g;
+    return AR_OK;
+}
+
+ar_status transform_group_apply(TransformGroup* g, int iter, cudaStream_t s) {
+    for (int k = 0; k < 4; ++k) {
+        ProfScope prof(AR_PROF_CONTRACTION, s);
+        count_launch();
+        const dim3 grid((unsigned)g->nitems[k], 1, SPLITK);
+        cudaError_t e = g->np == 2
+            ? launch_pdl(tc_contract_group_kernel<2>, grid, dim3(NTHREADS),
+                         (size_t)TcMode<2>::SMEM_BYTES, s, (const GroupJob*)g->jobs[k],
+                         (const int4*)g->items[k], iter)
+            : launch_pdl(tc_contract_group_kernel<3>, grid, dim3(NTHREADS),
+                         (size_t)TcMode<3>::SMEM_BYTES, s, (const GroupJob*)g->jobs[k],
+                         (const int4*)g->items[k], iter);
+        if (e != cudaSuccess) return cuda_fail(e, "grouped contraction launch");
+    }
+    return AR_OK;
+}
 
 int transform_launches(const TransformPlan* p, DInput din) {
     return (din == DIN_FP32 ? 1 : 0) + (p->bc == AR_BC_PERIODIC ? 7 : 4);

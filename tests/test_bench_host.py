@@ -59,3 +59,36 @@ def test_counters_are_withheld_when_the_kernel_code_changes(bench, tmp_path, mon
     assert bench.measured_traffic("stencil") == 1234
     open(src, "a").write("__global__ void k2() {}\n")
     assert bench.measured_traffic("stencil") is None
+
+
+def test_bench_stable_alpha_follows_the_pinned_symbol_ratio(bench):
+    """The bench's per-PSF alpha (its own NumPy restatement of the stability ratio)
+    equals the reading pinned on the oracle's symbols: for the bench's motion PSF
+    0.3, for the 2048^2 workload's Gaussian 0.1, and for random batch PSFs the
+    smallest half-decade value whose oracle ratio stays below 2."""
+    import numpy as np
+
+    import oracle as O
+    from paper_1211_0393_gb300 import workloads as W
+    assert bench.stable_alpha(W.psf_config2()) == 0.3
+    assert bench.stable_alpha(W.psf_config4()) == 0.1
+
+    def oracle_ratio(h, alpha):
+        q1, q2 = O.psf_support(h)
+        x = np.linspace(0, np.pi, 181)
+        x1, x2 = x[:, None], x[None, :]
+        hp = np.zeros((181, 181), dtype=complex)
+        hm = np.zeros_like(hp)
+        for a in range(-q1, q1 + 1):
+            for b in range(-q2, q2 + 1):
+                hp += h[a + q1, b + q2] * np.exp(-1j * (a * x1 + b * x2))
+                hm += h[a + q1, b + q2] * np.exp(-1j * (-a * x1 + b * x2))
+        e = np.maximum(np.abs(hp) ** 2, np.abs(hm) ** 2)
+        return float((e / (O.symbol(O.symmetrize(h), x, x) ** 2 + alpha)).max())
+
+    for sp in W.batch_specs(6):
+        a = bench.stable_alpha(sp["psf"])
+        assert a == 1.0 or oracle_ratio(sp["psf"], a) < 2.0
+        smaller = [v for v in bench.ALPHA_GRID if v < a]
+        if smaller:
+            assert oracle_ratio(sp["psf"], smaller[-1]) >= 2.0

@@ -1,5 +1,13 @@
-"""Batched restoration (one CUDA graph over many uneven images) against
-per-image ar_restore_ex calls and, for one image, the FP64 oracle."""
+"""Batched restoration (one persistent stencil launch and four grouped
+contractions per iteration for many uneven images) against per-image
+ar_restore_ex calls and the FP64 oracle.
+
+The stencils of the batch are the single-image stencils' code, so plain
+Landweber (stencils only) is bit-identical to per-image calls.  Preconditioned,
+the batch's contractions read the unfolded reblur and run the last product
+unpaired, a different float32 rounding of the same transform: both are within
+the per-iterate bound tol(alpha) of the exact iterate, so within 2 tol(alpha) of
+each other (bf16x2: 2 tol_fast)."""
 
 import numpy as np
 import pytest
@@ -9,6 +17,16 @@ import oracle as O
 from paper_1211_0393_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+
+def tol_alpha(alpha):
+    return max(1e-5, 3 * U32 / alpha)
+
+
+def tol_fast(alpha):
+    return max(1e-4, 3 * 2.0 ** -16 / alpha)
 
 
 @pytest.fixture(scope="module")
@@ -21,58 +39,90 @@ def ar():
     return mod
 
 
-def _images(sides, seed):
+def _images(sides, seed, alpha=0.5):
     rng = np.random.default_rng(seed)
     ims = []
     for n1, n2, q in sides:
         h = W.psf_random(q, q, rng)
         f = rng.uniform(0, 1, (n1, n2))
         g = O.ar_blur(f, h) + 0.005 * rng.standard_normal((n1, n2))
-        ims.append({"g": torch.from_numpy(g.astype(np.float32)).cuda(), "psf": h, "alpha": 1.0,
+        ims.append({"g": torch.from_numpy(g.astype(np.float32)).cuda(), "psf": h, "alpha": alpha,
                     "f_true": torch.from_numpy(f.astype(np.float32)).cuda(),
                     "x_out": torch.empty(n1, n2, device="cuda"), "f64": f, "g64": g.astype(np.float32)})
     return ims
 
 
-SIDES = [(64, 96, 2), (128, 128, 7), (37, 53, 3), (200, 120, 10), (96, 64, 15), (130, 257, 4),
-         (3, 5, 0), (64, 64, 4)]
+# n2 % 4 == 0 (TMA rows), q <= 15; sizes from one tile to several waves of tiles,
+# supports from 3x3 to 31x31, a small image whose tiles are all border tiles
+SIDES = [(64, 96, 2), (128, 128, 7), (37, 52, 3), (200, 120, 10), (96, 64, 15), (130, 256, 4),
+         (5, 8, 1), (64, 64, 4), (300, 196, 12)]
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a.astype(np.float64) - b) / np.linalg.norm(b))
 
 
 @pytest.mark.parametrize("precondition,precision", [(True, "fp32"), (True, "bf16x2"), (False, "fp32")])
-def test_batch_equals_per_image_restore(ar, precondition, precision):
-    if not precondition:
-        sides = SIDES
-    else:
-        sides = [s for s in SIDES if min(s[0], s[1]) >= 2 * s[2] + 3 and min(s[0], s[1]) >= 3]
+def test_batch_matches_per_image_restore(ar, precondition, precision):
+    sides = SIDES if not precondition else [s for s in SIDES if min(s[0], s[1]) >= 2 * s[2] + 3]
     ims = _images(sides, 11)
     iters = 7
-    B = ar.Batch(ims, tau=1.0, iters=iters, precondition=precondition, precision=precision,
-                 concurrency=3)
+    B = ar.Batch(ims, tau=1.0, iters=iters, precondition=precondition, precision=precision)
+    tol = (tol_fast(0.5) if precision == "bf16x2" else tol_alpha(0.5)) if precondition else 0.0
+    first = None
     for run in range(2):                      # replays must reproduce the same result
         B.run()
         tr, best, kpr = B.results()
-        assert kpr > 0
+        assert 0 < kpr <= 2 * len(ims) + 5 * iters + 1
+        xs = [im["x_out"].clone() for im in ims]
+        if first is None:
+            first = xs
+        else:
+            assert all(torch.equal(a, b) for a, b in zip(first, xs))
         for j, im in enumerate(ims):
             x, trj, bj = ar.ar_restore(im["g"], im["psf"], im["alpha"], 1.0, iters, precondition,
                                        f_true=im["f_true"], precision=precision)
-            xb = im["x_out"].cpu().numpy()
-            np.testing.assert_array_equal(xb, x.cpu().numpy())
-            np.testing.assert_allclose(tr[j], trj, rtol=1e-12)
-            assert best[j] == bj
+            xb = xs[j].cpu().numpy()
+            if precondition:
+                assert rel(xb, x.cpu().numpy().astype(np.float64)) <= 2 * tol, j
+                assert np.all(np.abs(tr[j] - trj) <= 2 * tol * (1 + trj)), j
+            else:
+                np.testing.assert_array_equal(xb, x.cpu().numpy())
+                # the RRE sums group float32 partials of a thread's rows (at most 18
+                # squares, relative error <= 18 2^-24) by the tile geometry
+                np.testing.assert_allclose(tr[j], trj, rtol=18 * U32)
+                assert best[j] == bj
     B.close()
 
 
-def test_batch_image_matches_oracle(ar):
-    ims = _images([(96, 80, 5), (64, 64, 4)], 12)
-    B = ar.Batch(ims, iters=5, precondition=True, concurrency=2)
+def test_batch_images_match_oracle(ar):
+    sides = [(96, 80, 5), (64, 64, 4), (130, 100, 9), (48, 200, 2)]
+    ims = _images(sides, 12)
+    iters = 5
+    B = ar.Batch(ims, iters=iters, precondition=True)
     B.run()
     tr, best, _ = B.results()
-    im = ims[0]
-    xo, to, _ = O.restore(im["g64"].astype(np.float64), im["psf"], 1.0, 1.0, 5, True,
-                          f_true=im["f_true"].cpu().numpy().astype(np.float64))
-    x = im["x_out"].cpu().numpy().astype(np.float64)
-    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) <= 1e-5
-    np.testing.assert_allclose(tr[0], to, rtol=1e-5)
+    for j, im in enumerate(ims):
+        xo, to, _ = O.restore(im["g64"].astype(np.float64), im["psf"], im["alpha"], 1.0, iters,
+                              True, f_true=im["f_true"].cpu().numpy().astype(np.float64))
+        x = im["x_out"].cpu().numpy()
+        assert rel(x, xo) <= tol_alpha(im["alpha"]), j
+        assert np.all(np.abs(tr[j] - to) <= tol_alpha(im["alpha"]) * (1 + to)), j
+    B.close()
+
+
+def test_batch_autotuner_reports_its_candidates(ar):
+    ims = _images([(128, 128, 7), (256, 192, 3), (64, 64, 15)], 14)
+    B = ar.Batch(ims, iters=4, precondition=True, tuning=0)
+    t = B.tuning()
+    assert len(t["candidates"]) >= 2
+    best = min(t["candidates"], key=lambda c: c["ms_3_iters"])
+    assert (best["geometry"], best["ctas_per_sm"]) == (t["geometry"], t["ctas_per_sm"])
+    B.run()
+    B.results()
+    B2 = ar.Batch(ims, iters=4, precondition=True, tuning=1)
+    assert B2.tuning() == {"geometry": "64-row", "ctas_per_sm": 1, "candidates": []}
+    B2.close()
     B.close()
 
 
@@ -82,3 +132,10 @@ def test_batch_rejects_aliasing_outputs(ar):
     with pytest.raises(ar.ARError) as ei:
         ar.Batch(ims, iters=2)
     assert ei.value.name == "AR_ERR_ALIAS"
+
+
+def test_batch_rejects_unsupported_shapes(ar):
+    ims = _images([(32, 30, 2)], 15)           # n2 % 4 != 0: the batched stencil's TMA rows
+    with pytest.raises(ar.ARError) as ei:
+        ar.Batch(ims, iters=2)
+    assert ei.value.name == "AR_ERR_UNSUPPORTED"

@@ -200,3 +200,65 @@ def test_restore_prec_with_symmetrized_preconditioner_equals_restore(ar):
     assert torch.equal(x1, x2) and b1 == b2
     np.testing.assert_allclose(t1, t2, rtol=1e-12, atol=0)
     P.close()
+
+
+def test_restoration_targets_match_oracle(ar):
+    """Tables read off the symmetrized D-Landweber's own iterates (GPU) against the
+    oracle's on the same seeded scene, noise field and PSFs.  Bound: a frequency's
+    shrunk departure (mu^ - lambda^2) w / (w + rho) moves by at most about
+    e sqrt(K) / (tau d sqrt(rho)) when its spectral values W_k carry an absolute
+    error e; float32 transforms give e ~ 2^-24 x the largest |W| (sums with
+    cancellation); rho = 5 w_mean, and a 64^2 scene's largest weight is about
+    1e3 w_mean, so rho >= 5e-3 max|W|^2 K; with K = 6 and tau d >= 1/(1 + 0.3)
+    that is about 5e-6 per frequency, and a node is a weighted mean of them;
+    checked at 1e-4."""
+    n = 64
+    rng = np.random.default_rng(21)
+    f = rng.uniform(0, 1, (n, n)).astype(np.float32)
+    e = rng.standard_normal((n, n)).astype(np.float32)
+    H = psfs(22, 3)
+    got = ar.corr_restoration_targets(torch.from_numpy(f).cuda(), torch.from_numpy(e).cuda(), H,
+                                      0.005, 0.3, 1.0, 6)
+    assert got.shape == (3, 33, 33)
+    for i in range(3):
+        want = O.restoration_target(H[i], f.astype(np.float64), e.astype(np.float64), 0.005, 0.3,
+                                    1.0, 6)
+        assert np.max(np.abs(got[i] - want)) <= 1e-4, (i, np.max(np.abs(got[i] - want)))
+        assert np.max(np.abs(want)) > 1e-2            # a nonzero target is compared
+
+
+def test_restoration_targets_vanish_for_a_symmetric_psf(ar):
+    """Theorem 2 with A' = A: a strongly symmetric PSF leaves no departure to fit."""
+    n = 48
+    rng = np.random.default_rng(23)
+    a = np.arange(-7, 8)
+    h = np.exp(-0.5 * (a[:, None] ** 2 / 3.0 + a[None, :] ** 2 / 5.0))
+    h = (h / h.sum())[None]
+    f = torch.from_numpy(rng.uniform(0, 1, (n, n)).astype(np.float32)).cuda()
+    e = torch.from_numpy(rng.standard_normal((n, n)).astype(np.float32)).cuda()
+    got = ar.corr_restoration_targets(f, e, h, 0.01, 0.3, 1.0, 6)
+    assert np.max(np.abs(got)) <= 1e-4
+
+
+def test_training_on_given_tables_matches_oracle(ar):
+    """ar_corr_train_tables: the first loss is the initial model's against the given
+    tables, and the parameters after one Adam step follow the oracle's (the
+    determined entries as in test_adam_steps_match_oracle_elementwise)."""
+    P = model_params(9)
+    H = psfs(10, 8)
+    T = np.random.default_rng(11).normal(0.0, 0.1, (8, 33, 33))
+    M = ar.Corr(flat(P))
+    loss = M.train(H, epochs=1, batch=8, lr=1e-3, tables=T)
+    got = unflat(M.params())
+    M.close()
+    X = np.stack([O.corr_input(h) for h in H])
+    Tt = T.reshape(8, -1).astype(np.float32).astype(np.float64)
+    Y, cache = O.mlp_forward(P, X)
+    l0, dY = O.mse_loss(Y, Tt)
+    G = O.mlp_backward(P, cache, dY)
+    Po = {k: v.copy() for k, v in P.items()}
+    O.adam_step(Po, G, {}, lr=1e-3)
+    assert loss[0] == pytest.approx(l0, rel=1e-5)
+    for k in O.PARAM_ORDER:
+        det = np.abs(G[k]) >= 1e-3 * np.max(np.abs(G[k]))
+        assert np.max(np.abs(got[k] - Po[k])[det]) <= 2e-5, k
