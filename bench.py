@@ -539,9 +539,11 @@ PREC4_ALPHA = 0.1      # smallest half-decade alpha for which tau = 1 is stable 
 def precision_2048_form(ar, torch, dev, stream, flush, steps):
     """The 2048^2 precision workload (ellipses, 21x21 asymmetric Gaussian PSF,
     1% noise, 50 D-Landweber iterations): throughput and restoration error of
-    the float32-grade (bf16x3) and fast (bf16x2) contractions, and how far the
-    fast iterates drift from the float32-grade ones step by step.  (The error
-    of both against the FP64 oracle per step is checked by the GPU tests.)"""
+    the float32-grade (bf16x3) and fast (bf16x2) dense contractions and of the
+    FFT-style float32 transform (a Good-Thomas 23 x 89 DFT per 1D transform),
+    the library's measured choice between dense and FFT-style per size, and how
+    far the fast iterates drift from the float32-grade ones step by step.  (The
+    error of each against the FP64 oracle per step is checked by the GPU tests.)"""
     wl = W.WORKLOADS["ellipses2048_gauss21"]
     n1, n2 = wl["n"]
     h = W.psf_config4()
@@ -554,7 +556,7 @@ def precision_2048_form(ar, torch, dev, stream, flush, steps):
     f_d = torch.from_numpy(f.astype(np.float32)).to(dev)
     out = {"workload": f"ellipses{n1}_gauss21: {n1}x{n2}, 21x21 asymmetric Gaussian, 1% noise, "
                        f"alpha {PREC4_ALPHA}, {ITERS} iterations"}
-    for prec in ("fp32", "bf16x2"):
+    for prec in ("fp32", "bf16x2", "fft"):
         x = torch.empty_like(g_d)
 
         def step():
@@ -575,6 +577,14 @@ def precision_2048_form(ar, torch, dev, stream, flush, steps):
         out[prec] = {"value": round(n1 * n2 * ITERS * steps / 1e6 / (tot / 1e3), 2), "unit": UNIT,
                      "ms_per_step": round(tot / steps, 3), "rre_best": round(float(np.min(tr)), 6),
                      "best_iter": best, "rre_final": round(float(tr[-1]), 6)}
+    # AR_PRECISION_AUTO: the library's measured choice between the dense tensor-core
+    # contractions and the FFT-style transform (Good-Thomas 23 x 89 at 2048)
+    choice = {}
+    for side in (n1, 1024):
+        P = ar.ar_symprec_setup(h, side, side, PREC4_ALPHA, precision="auto")
+        choice[str(side)] = ar.ar_symprec_precision(P)
+        P.close()
+    out["auto_choice"] = choice
     drift = []
     for k in (1, 2, 5, 10, 50):
         xa, _, _ = ar.ar_restore(g_d, h, PREC4_ALPHA, TAU, k, True)

@@ -63,14 +63,28 @@ typedef enum ar_status {
  * separable Hartley basis (see ar_symprec_setup_bc). */
 typedef enum ar_bc { AR_BC_ANTIREFLECTIVE = 0, AR_BC_REFLECTIVE = 1, AR_BC_PERIODIC = 2 } ar_bc;
 
-/* Arithmetic of the AR transform contractions (tensor cores).
- *  AR_PRECISION_FP32:   operands split into three bfloat16 planes, the six
- *                       products with i + j <= 2 accumulated in float32:
- *                       float32-grade (the default).
+/* Arithmetic of the AR transform pair (Theorem 1) inside the preconditioner.
+ *  AR_PRECISION_FP32:   dense contractions on the tensor cores, operands
+ *                       split into three bfloat16 planes, the six products
+ *                       with i + j <= 2 accumulated in float32: float32-grade
+ *                       (the default).
  *  AR_PRECISION_BF16X2: two planes, the three products with i + j <= 1:
  *                       about 2^-16 relative per contraction, roughly half
- *                       the tensor work and two thirds of the operand bytes. */
-typedef enum ar_precision { AR_PRECISION_FP32 = 0, AR_PRECISION_BF16X2 = 1 } ar_precision;
+ *                       the tensor work and two thirds of the operand bytes.
+ *  AR_PRECISION_FFT:    FFT-style, float32 on the CUDA cores: every 1D
+ *                       transform is its boundary terms plus a DST-I taken
+ *                       from one real DFT of length n_j - 1, split by Good
+ *                       and Thomas into two small dense DFTs of coprime
+ *                       lengths (2047 = 23 x 89 at n = 2048).  AR BCs only,
+ *                       and both n_j - 1 must split into coprime factors of
+ *                       at most 256 (AR_ERR_UNSUPPORTED otherwise).
+ *  AR_PRECISION_AUTO:   AR_PRECISION_FFT or AR_PRECISION_FP32, whichever the
+ *                       library measures faster for the size (one timing of
+ *                       each the first time a size is seen on a device, kept
+ *                       for the process); AR_PRECISION_FP32 where the FFT-style
+ *                       form does not apply. */
+typedef enum ar_precision { AR_PRECISION_FP32 = 0, AR_PRECISION_BF16X2 = 1,
+                            AR_PRECISION_FFT = 2, AR_PRECISION_AUTO = 3 } ar_precision;
 
 /* Opaque preconditioner: the symmetrized-PSF eigenvalues and Tikhonov filter
  * for one (PSF, n1, n2, alpha), plus the AR transform operands and scratch
@@ -174,6 +188,10 @@ AR_API ar_status ar_symprec_eigenvalues(const ar_prec* P, double* lambda_host, d
 
 /* Sizes a preconditioner was built for (either pointer may be NULL). */
 AR_API ar_status ar_symprec_shape(const ar_prec* P, int* n1, int* n2);
+
+/* The transform arithmetic P runs with (an ar_precision other than
+ * AR_PRECISION_AUTO: the choice AR_PRECISION_AUTO made). */
+AR_API ar_status ar_symprec_precision(const ar_prec* P, int* precision);
 
 /* Free a preconditioner (NULL is a no-op).  Waits for its pending work. */
 AR_API void ar_symprec_destroy(ar_prec* P);

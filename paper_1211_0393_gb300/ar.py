@@ -35,7 +35,7 @@ EXPORTS = [
     "ar_corr_targets", "ar_corr_train", "ar_corr_predict", "ar_symprec_setup_corrected",
     "ar_restore_prec", "ar_restore_residuals", "ar_set_stencil_wait_polls",
     "ar_inject_alloc_failures", "ar_corr_train_tables", "ar_corr_restoration_targets",
-    "ar_batch_tuning",
+    "ar_batch_tuning", "ar_symprec_precision",
 ]
 
 DEFAULT_WAIT_POLLS = 1 << 24
@@ -49,7 +49,8 @@ class BatchItem(ctypes.Structure):
                 ("n2", ctypes.c_int), ("q1", ctypes.c_int), ("q2", ctypes.c_int),
                 ("alpha", ctypes.c_double), ("f_true", ctypes.c_void_p), ("x_out", ctypes.c_void_p)]
 
-PRECISION = {"fp32": 0, "bf16x2": 1}
+PRECISION = {"fp32": 0, "bf16x2": 1, "fft": 2, "auto": 3}
+PRECISION_NAME = {v: k for k, v in PRECISION.items()}
 
 # ar_bc: the method's anti-reflective BCs and the two comparison BCs
 BC = {"ar": 0, "reflective": 1, "periodic": 2}
@@ -116,6 +117,8 @@ def lib() -> ctypes.CDLL:
         L.ar_batch_run.restype = _i
         L.ar_batch_results.argtypes = [_vp, _vp, _vp, _vp]
         L.ar_batch_results.restype = _i
+        L.ar_symprec_precision.argtypes = [_vp, ctypes.POINTER(_i)]
+        L.ar_symprec_precision.restype = _i
         L.ar_batch_tuning.argtypes = [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i),
                                       ctypes.POINTER(_i), _vp, _vp, _vp, _i]
         L.ar_batch_tuning.restype = _i
@@ -243,8 +246,10 @@ def ar_symprec_setup(psf, n1: int, n2: int, alpha: float, stream=None,
                      precision: str = "fp32", bc: str = "ar") -> Prec:
     """Build the optimal preconditioner of ``bc`` (float64 setup on the GPU).
 
-    ``precision``: "fp32" (three bf16 planes, six products) or "bf16x2" (two
-    planes, three products) for the transform contractions.  ``bc``: "ar"
+    ``precision``: "fp32" (three bf16 planes, six products), "bf16x2" (two
+    planes, three products) for the transform contractions, "fft" (the
+    FFT-style float32 transform, AR only) or "auto" (the faster of "fft" and
+    "fp32" for the size, measured once).  ``bc``: "ar"
     (symmetrized PSF, AR transform), "reflective" (symmetrized PSF, DCT-III)
     or "periodic" (circulant of the PSF)."""
     h = _host_psf(psf)
@@ -277,6 +282,14 @@ def ar_symprec_eigenvalues(P: Prec) -> tuple[np.ndarray, np.ndarray]:
     _check(lib().ar_symprec_eigenvalues(P.handle, lam.ctypes.data, d.ctypes.data),
            "ar_symprec_eigenvalues")
     return lam, d
+
+
+def ar_symprec_precision(P: Prec) -> str:
+    """The transform arithmetic P runs with ("fp32", "bf16x2" or "fft"; the choice
+    of "auto")."""
+    v = _i()
+    _check(lib().ar_symprec_precision(P.handle, ctypes.byref(v)), "ar_symprec_precision")
+    return PRECISION_NAME[v.value]
 
 
 def ar_symprec_shape(P: Prec) -> tuple[int, int]:

@@ -10,8 +10,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 namespace ar {
@@ -171,6 +173,10 @@ ar_status apply_common(const float* x, float* y, int n1, int n2, const float* ps
 void prec_release(ar_prec* P, cudaStream_t s) {
     if (!P) return;
     transform_plan_release(P->plan, s);
+    if (P->fst) {
+        cudaStreamSynchronize(s);
+        fst_plan_destroy(P->fst);
+    }
     for (void* q : {(void*)P->lam64, (void*)P->d64, (void*)P->d32, (void*)P->d32_odd})
         if (q) cudaFreeAsync(q, s);
     delete P;
@@ -227,11 +233,15 @@ ar_status prec_build(const double* psf_host, int q1, int q2, int n1, int n2, dou
         if (st == AR_OK)
             st = setup_eigen(h64, q1, q2, n1, n2, alpha, bc, P->lam64, P->d64, P->d32, P->d32_odd,
                              work, s, delta);
-        // the reblur stencil writes the transform input folded (q <= 15, TMA path)
-        if (st == AR_OK)
-            st = transform_plan_create(n1, n2, bc, precision, s, &P->plan,
-                                       !grouped && (q1 > q2 ? q1 : q2) <= 15, !grouped);
-        if (st == AR_OK) st = transform_set_filter(P->plan, P->d32, s);
+        if (precision == AR_PRECISION_FFT) {
+            if (st == AR_OK) st = fst_plan_create(n1, n2, s, &P->fst);
+        } else {
+            // the reblur stencil writes the transform input folded (q <= 15, TMA path)
+            if (st == AR_OK)
+                st = transform_plan_create(n1, n2, bc, precision, s, &P->plan,
+                                           !grouped && (q1 > q2 ? q1 : q2) <= 15, !grouped);
+            if (st == AR_OK) st = transform_set_filter(P->plan, P->d32, s);
+        }
     }
     if (st != AR_OK) {
         ar_symprec_destroy(P);
@@ -298,7 +308,9 @@ static ar_status restore_run(const float* g, const double* psf_host, int n1, int
             if (e != cudaSuccess) st = cuda_fail(e, "restore initialisation");
         }
         if (st == AR_OK && pc && !Pext) {
-            st = prec_build(psf_host, q1, q2, n1, n2, alpha, bc, precision, s, false, &P);
+            int prec = precision;
+            st = resolve_precision(precision, bc, n1, n2, s, &prec);
+            if (st == AR_OK) st = prec_build(psf_host, q1, q2, n1, n2, alpha, bc, prec, s, false, &P);
             PP = P;
         }
         if (st == AR_OK && f_true) st = reduce_sq(f_true, n, dsum + iters, s);
@@ -319,7 +331,11 @@ static ar_status restore_run(const float* g, const double* psf_host, int n1, int
         reblur.x = r;
         reblur.aux = nullptr;
         reblur.flip = 1;
-        if (pc && st == AR_OK) {
+        if (pc && st == AR_OK && PP->fst) {
+            // A' r into the FFT-style transform's float32 input
+            reblur.out = fst_input(PP->fst);
+            reblur.mode = CONV_STORE;
+        } else if (pc && st == AR_OK) {
             // A' r is written straight into the transform's bf16x3 operand planes
             reblur.out = nullptr;
             reblur.mode = CONV_SPLIT3;
@@ -333,7 +349,7 @@ static ar_status restore_run(const float* g, const double* psf_host, int n1, int
         // successors: the reblur's is a contraction (no room beside the stencil) or
         // the blur; the blur's is a stencil (launched early beside the blur, the
         // folding reblur's CTAs ran slower: measured)
-        reblur.early_trigger = reblur.mode == CONV_SPLIT3 ? 1 : 0;
+        reblur.early_trigger = reblur.mode == CONV_SPLIT3 || reblur.mode == CONV_STORE ? 1 : 0;
         blur.spread = reblur.spread = 1;
         reblur.f = f_true;
         for (int it = 0; st == AR_OK && it < iters; ++it) {
@@ -342,7 +358,10 @@ static ar_status restore_run(const float* g, const double* psf_host, int n1, int
             st = conv_launch(blur, s);                           // r = g - A x_k
             if (!pc) reblur.sumsq = f_true ? dsum + it : nullptr;
             if (st == AR_OK) st = conv_launch(reblur, s);        // z = A' r  (or x += tau A' r)
-            if (st == AR_OK && pc)                               // x += tau D z
+            if (st == AR_OK && pc && PP->fst)                    // x += tau D z
+                st = fst_apply(PP->fst, PP->d32, nullptr, x_out, true, (float)tau, s, f_true,
+                               f_true ? dsum + it : nullptr);
+            else if (st == AR_OK && pc)
                 st = transform_apply(PP->plan, PP->d32, PP->d32_odd, nullptr, DIN_SPLIT, x_out,
                                      DOUT_AXPY, (float)tau, s, f_true,
                                      f_true ? dsum + it : nullptr);
@@ -359,7 +378,7 @@ static ar_status restore_run(const float* g, const double* psf_host, int n1, int
             if (e == cudaSuccess && dres)
                 e = cudaMemcpyAsync(rsums.data(), dres, rsums.size() * sizeof(double),
                                     cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess && PP)
+            if (e == cudaSuccess && PP && PP->plan)
                 e = cudaMemcpyAsync(&timeout, transform_error_flag(PP->plan), sizeof(int),
                                     cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess)
@@ -393,6 +412,99 @@ static ar_status restore_run(const float* g, const double* psf_host, int n1, int
     return AR_OK;
 }
 
+ar_status check_precision(int precision, int bc, int n1, int n2) {
+    if (precision < AR_PRECISION_FP32 || precision > AR_PRECISION_AUTO)
+        return fail(AR_ERR_INVALID_ARG, "unknown precision %d", precision);
+    if (precision == AR_PRECISION_FFT && bc != AR_BC_ANTIREFLECTIVE)
+        return fail(AR_ERR_UNSUPPORTED, "the FFT-style transform serves AR BCs only");
+    if (precision == AR_PRECISION_FFT && !fst_supported(n1, n2))
+        return fail(AR_ERR_UNSUPPORTED,
+                    "FFT-style transform: n_j - 1 must split into coprime factors <= 256 "
+                    "(n = %d x %d)", n1, n2);
+    return AR_OK;
+}
+
+namespace {
+// AR_PRECISION_AUTO's measured choice per (device, n1, n2).
+std::mutex g_choice_mu;
+std::map<std::tuple<int, int, int>, int> g_choice;
+
+// Device milliseconds of one D application (median of three after a warm-up):
+// the dense chain with its input already in operand form, or the FFT-style one.
+ar_status time_transform(int precision, int n1, int n2, cudaStream_t s, float* ms) {
+    const size_t n = (size_t)n1 * n2;
+    float *d = nullptr, *y = nullptr, *z = nullptr;
+    TransformPlan* tp = nullptr;
+    FstPlan* fp = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ar_status st = AR_OK;
+    cudaError_t ce = cudaMalloc((void**)&d, n * sizeof(float));
+    if (ce == cudaSuccess) ce = cudaMalloc((void**)&y, n * sizeof(float));
+    if (ce == cudaSuccess) ce = cudaMalloc((void**)&z, n * sizeof(float));
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(d, 0, n * sizeof(float), s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(y, 0, n * sizeof(float), s);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) st = cuda_fail(ce, "transform timing buffers");
+    if (st == AR_OK) {
+        if (precision == AR_PRECISION_FFT) st = fst_plan_create(n1, n2, s, &fp);
+        else st = transform_plan_create(n1, n2, AR_BC_ANTIREFLECTIVE, precision, s, &tp, true);
+    }
+    if (st == AR_OK && tp) st = transform_set_filter(tp, d, s);
+    auto once = [&](bool first) {
+        if (fp) return fst_apply(fp, d, nullptr, z, false, 0.f, s);
+        return transform_apply(tp, d, nullptr, first ? y : nullptr, first ? DIN_FP32 : DIN_SPLIT, z,
+                               DOUT_STORE, 0.f, s);
+    };
+    if (st == AR_OK) st = once(true);
+    float t[3] = {0.f, 0.f, 0.f};
+    for (int r = 0; st == AR_OK && r < 3; ++r) {
+        cudaEventRecord(e0, s);
+        st = once(false);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(AR_ERR_CUDA, "transform timing");
+        if (st == AR_OK) cudaEventElapsedTime(&t[r], e0, e1);
+    }
+    cudaStreamSynchronize(s);
+    if (tp) transform_plan_destroy(tp);
+    if (fp) fst_plan_destroy(fp);
+    cudaFree(d);
+    cudaFree(y);
+    cudaFree(z);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    const float lo = t[0] < t[1] ? t[0] : t[1], hi = t[0] < t[1] ? t[1] : t[0];
+    *ms = t[2] < lo ? lo : (t[2] > hi ? hi : t[2]);
+    return st;
+}
+}  // namespace
+
+ar_status resolve_precision(int precision, int bc, int n1, int n2, cudaStream_t s, int* out) {
+    *out = precision;
+    if (precision != AR_PRECISION_AUTO) return AR_OK;
+    *out = AR_PRECISION_FP32;
+    if (bc != AR_BC_ANTIREFLECTIVE || !fst_supported(n1, n2)) return AR_OK;
+    int dev = 0;
+    AR_CUDA(cudaGetDevice(&dev));
+    const auto key = std::make_tuple(dev, n1, n2);
+    {
+        std::lock_guard<std::mutex> lock(g_choice_mu);
+        auto it = g_choice.find(key);
+        if (it != g_choice.end()) {
+            *out = it->second;
+            return AR_OK;
+        }
+    }
+    float t_dense = 0.f, t_fft = 0.f;
+    AR_TRY(time_transform(AR_PRECISION_FP32, n1, n2, s, &t_dense));
+    AR_TRY(time_transform(AR_PRECISION_FFT, n1, n2, s, &t_fft));
+    const int choice = t_fft < t_dense ? AR_PRECISION_FFT : AR_PRECISION_FP32;
+    std::lock_guard<std::mutex> lock(g_choice_mu);
+    g_choice[key] = choice;
+    *out = choice;
+    return AR_OK;
+}
+
 // Argument checks shared by every entry point that takes ar_restore_bc's
 // arguments, so that they accept exactly the same inputs.
 static ar_status validate_restore_args(const float* g, const double* psf_host, int n1, int n2,
@@ -401,10 +513,11 @@ static ar_status validate_restore_args(const float* g, const double* psf_host, i
                                        const float* f_true, const float* x_out,
                                        const double* rre_trace, const int* best_iter) {
     if (!g || !psf_host || !x_out) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
-    if (precision != AR_PRECISION_FP32 && precision != AR_PRECISION_BF16X2)
-        return fail(AR_ERR_INVALID_ARG, "unknown precision %d", precision);
     AR_TRY(check_bc(bc));
     const bool pc = precondition != 0;
+    if (pc) AR_TRY(check_precision(precision, bc, n1, n2));
+    else if (precision < AR_PRECISION_FP32 || precision > AR_PRECISION_AUTO)
+        return fail(AR_ERR_INVALID_ARG, "unknown precision %d", precision);
     AR_TRY(check_image_sizes(n1, n2, pc ? 3 : 1));
     AR_TRY(check_support(n1, n2, q1, q2, pc && bc == AR_BC_ANTIREFLECTIVE ? 3 : 1));
     if (iters < 0) return fail(AR_ERR_INVALID_ARG, "iters must be >= 0 (got %d)", iters);
@@ -491,9 +604,8 @@ ar_status ar_symprec_setup_ex(const double* psf_host, int q1, int q2, int n1, in
 ar_status ar_symprec_setup_bc(const double* psf_host, int q1, int q2, int n1, int n2, double alpha,
                               int bc, int precision, void* stream, ar_prec** out) {
     if (!psf_host || !out) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
-    if (precision != AR_PRECISION_FP32 && precision != AR_PRECISION_BF16X2)
-        return fail(AR_ERR_INVALID_ARG, "unknown precision %d", precision);
     AR_TRY(check_bc(bc));
+    AR_TRY(check_precision(precision, bc, n1, n2));
     AR_TRY(check_image_sizes(n1, n2, 3));
     // AR needs the interior grid of size n - 2 to hold the support
     AR_TRY(check_support(n1, n2, q1, q2, bc == AR_BC_ANTIREFLECTIVE ? 3 : 1));
@@ -502,7 +614,9 @@ ar_status ar_symprec_setup_bc(const double* psf_host, int q1, int q2, int n1, in
     AR_TRY(check_psf_host(psf_host, q1, q2));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     ar_prec* P = nullptr;
-    AR_TRY(prec_build(psf_host, q1, q2, n1, n2, alpha, bc, precision, s, true, &P));
+    int prec = precision;
+    AR_TRY(resolve_precision(precision, bc, n1, n2, s, &prec));
+    AR_TRY(prec_build(psf_host, q1, q2, n1, n2, alpha, bc, prec, s, true, &P));
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         ar_symprec_destroy(P);
@@ -548,6 +662,8 @@ ar_status ar_symprec_solve(const ar_prec* P, const float* y, float* z, void* str
     if (dev != P->device) return fail(AR_ERR_INVALID_ARG, "preconditioner belongs to device %d", P->device);
     const size_t nb = (size_t)P->n1 * P->n2 * sizeof(float);
     if (y != z && overlaps(y, nb, z, nb)) return fail(AR_ERR_ALIAS, "z partially overlaps y");
+    if (P->fst)
+        return fst_apply(P->fst, P->d32, y, z, false, 0.f, static_cast<cudaStream_t>(stream));
     return transform_apply(P->plan, P->d32, P->d32_odd, y, DIN_FP32, z, DOUT_STORE, 0.f,
                            static_cast<cudaStream_t>(stream));
 }
@@ -558,6 +674,12 @@ ar_status ar_symprec_eigenvalues(const ar_prec* P, double* lambda_host, double* 
     const size_t nb = (size_t)P->n1 * P->n2 * sizeof(double);
     if (lambda_host) AR_CUDA(cudaMemcpy(lambda_host, P->lam64, nb, cudaMemcpyDeviceToHost));
     if (d_host) AR_CUDA(cudaMemcpy(d_host, P->d64, nb, cudaMemcpyDeviceToHost));
+    return AR_OK;
+}
+
+ar_status ar_symprec_precision(const ar_prec* P, int* precision) {
+    if (!P || !precision) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
+    *precision = P->precision;
     return AR_OK;
 }
 
@@ -572,6 +694,7 @@ void ar_symprec_destroy(ar_prec* P) {
     if (!P) return;
     cudaDeviceSynchronize();
     transform_plan_destroy(P->plan);
+    fst_plan_destroy(P->fst);
     cudaFree(P->lam64);
     cudaFree(P->d64);
     cudaFree(P->d32);

@@ -226,6 +226,26 @@ int* transform_error_flag(TransformPlan* p);
 ar_status transform_spectral_view(const TransformPlan* p, const uint16_t** planes,
                                   size_t* pstride, int* ld, int* nplanes, const float** dfold);
 
+// ------------------------------------------------- FFT-style transform ---
+// D y = T diag(d) T~ y with each 1D AR transform as boundary terms plus a DST-I
+// from a Good-Thomas factored real DFT (ar_fst.cu).  AR BCs, n_j - 1 split into
+// coprime factors <= 256.
+struct FstPlan;
+bool fst_supported(int n1, int n2);
+ar_status fst_plan_create(int n1, int n2, cudaStream_t s, FstPlan** out);
+void fst_plan_destroy(FstPlan* p);
+// The plan's float32 input buffer (n1 x n2): the reblur writes z there.
+float* fst_input(FstPlan* p);
+// out = D y (axpy false) or out += tau D y with sum (out_new - f)^2 added to
+// *sumsq; y null reads fst_input(p).  d32: the filter, natural order.
+ar_status fst_apply(FstPlan* p, const float* d32, const float* y, float* out, bool axpy, float tau,
+                    cudaStream_t s, const float* f = nullptr, double* sumsq = nullptr);
+
+// AR_PRECISION_AUTO resolved for an image size and BC (measured once per
+// device and size); other precisions are returned as given.
+ar_status resolve_precision(int precision, int bc, int n1, int n2, cudaStream_t s, int* out);
+ar_status check_precision(int precision, int bc, int n1, int n2);
+
 // ---------------------------------------------------------------- setup ---
 // FP64 eigenvalue setup on the GPU.  AR and Reflective: symmetrize (eq.
 // simmetrizzata2d), symbol (eq. funzione_generatrice) on the grid of the BC
@@ -307,5 +327,6 @@ struct ar_prec {
     double* d64;
     float* d32;
     float* d32_odd;      // Periodic only: minus the part of d odd in both frequencies
-    ar::TransformPlan* plan;
+    ar::TransformPlan* plan;   // dense contractions (null with the FFT-style form)
+    ar::FstPlan* fst;          // AR_PRECISION_FFT: the FFT-style transform
 };
