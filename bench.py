@@ -290,9 +290,10 @@ PEAKS = load_peaks()
 def kernel_rooflines(ar, torch, dev, step):
     """Device time per kernel class over one profiled step of the same workload.
 
-    The library brackets every kernel it launches with CUDA events on its launch
-    stream (profiled kernels run serialized, without dependent-launch overlap).
-    The dominant class is the one with the largest share of the step.
+    The library brackets its launches with CUDA events on the launch stream: each
+    stencil alone, and the four dependent contractions of each application of D
+    as one interval (their dependent-launch overlap kept), counted as four
+    launches.  The dominant class is the one with the largest share of the step.
 
     Work counted for the contraction is the method's: one launch applies a
     one-dimensional AR transform (a dense DST-I plus its boundary columns) to

@@ -321,9 +321,10 @@ AR_API ar_status ar_restore_residuals(const float* g, const double* psf_host,
  * last run and copies the RRE traces (count x iters doubles, may be NULL), the
  * best iterations (count ints, may be NULL) and the number of kernels one run
  * launches.  The stencils of a run equal those of ar_restore_ex bit for bit;
- * the contractions read the unfolded reblur (the single-image loop folds it
- * into the first product) and run the last product unpaired, so the iterates
- * agree with ar_restore_ex within the restoration's float32 tolerance.
+ * the contractions may pair their tiles differently from the single-image
+ * loop (the batch always runs the last product in parity-paired clusters), so
+ * the iterates agree with ar_restore_ex within the restoration's float32
+ * tolerance.
  * Errors: AR_ERR_INVALID_ARG (item index in the detail), AR_ERR_ALIAS (an
  * output overlapping any input or output of the batch),
  * AR_ERR_PSF_NOT_NORMALIZED, AR_ERR_UNSUPPORTED, AR_ERR_ALLOC, AR_ERR_CUDA;
@@ -346,12 +347,14 @@ AR_API ar_status ar_batch_results(ar_batch* B, double* rre_traces, int* best_ite
                                   unsigned long long* kernels_per_run);
 AR_API void ar_batch_destroy(ar_batch* B);
 /* The stencil configuration the batch runs with (geometry 0: 64-row tiles, 1:
- * 54-row tiles; persistent CTAs per SM) and, when autotuned, every timed
- * candidate (up to max_candidates of them: geometry, CTAs per SM, device
+ * 54-row tiles; persistent CTAs per SM), the transform's form (bit 0: the
+ * reblur writes the first product's input folded along the columns; bit 1:
+ * the last product runs in parity-paired clusters) and, when autotuned, every
+ * timed candidate (up to max_candidates of them: geometry, CTAs per SM, device
  * milliseconds of three batch iterations).  Any output may be NULL. */
 AR_API ar_status ar_batch_tuning(const ar_batch* B, int* geometry, int* ctas_per_sm,
-                                 int* candidates, int* cand_geometry, int* cand_ctas,
-                                 double* cand_ms, int max_candidates);
+                                 int* transform, int* candidates, int* cand_geometry,
+                                 int* cand_ctas, double* cand_ms, int max_candidates);
 
 /*
  * Spectral correction of the symmetrized preconditioner (learned form).

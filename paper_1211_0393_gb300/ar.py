@@ -120,7 +120,7 @@ def lib() -> ctypes.CDLL:
         L.ar_symprec_precision.argtypes = [_vp, ctypes.POINTER(_i)]
         L.ar_symprec_precision.restype = _i
         L.ar_batch_tuning.argtypes = [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i),
-                                      ctypes.POINTER(_i), _vp, _vp, _vp, _i]
+                                      ctypes.POINTER(_i), ctypes.POINTER(_i), _vp, _vp, _vp, _i]
         L.ar_batch_tuning.restype = _i
         L.ar_batch_destroy.argtypes = [_vp]
         L.ar_batch_destroy.restype = None
@@ -449,15 +449,16 @@ class Batch:
 
     def tuning(self) -> dict:
         """The stencil configuration in use and the autotuner's timed candidates."""
-        geo, ctas, n = _i(), _i(), _i()
+        geo, ctas, tf, n = _i(), _i(), _i(), _i()
         cg = np.zeros(16, dtype=np.int32)
         cc = np.zeros(16, dtype=np.int32)
         cm = np.zeros(16, dtype=np.float64)
         _check(lib().ar_batch_tuning(self.handle, ctypes.byref(geo), ctypes.byref(ctas),
-                                     ctypes.byref(n), cg.ctypes.data, cc.ctypes.data,
-                                     cm.ctypes.data, 16), "ar_batch_tuning")
+                                     ctypes.byref(tf), ctypes.byref(n), cg.ctypes.data,
+                                     cc.ctypes.data, cm.ctypes.data, 16), "ar_batch_tuning")
         k = min(n.value, 16)
         return {"geometry": ("64-row", "54-row")[geo.value], "ctas_per_sm": ctas.value,
+                "folded_input": bool(tf.value & 1), "paired_last_product": bool(tf.value & 2),
                 "candidates": [{"geometry": ("64-row", "54-row")[int(cg[i])],
                                 "ctas_per_sm": int(cc[i]), "ms_3_iters": float(cm[i])}
                                for i in range(k)]}

@@ -239,7 +239,7 @@ ar_status prec_build(const double* psf_host, int q1, int q2, int n1, int n2, dou
             // the reblur stencil writes the transform input folded (q <= 15, TMA path)
             if (st == AR_OK)
                 st = transform_plan_create(n1, n2, bc, precision, s, &P->plan,
-                                           !grouped && (q1 > q2 ? q1 : q2) <= 15, !grouped);
+                                           (q1 > q2 ? q1 : q2) <= 15, grouped ? 2 : 1);
             if (st == AR_OK) st = transform_set_filter(P->plan, P->d32, s);
         }
     }

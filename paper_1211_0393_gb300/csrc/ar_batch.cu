@@ -245,10 +245,8 @@ ar_status ar_batch_create(const ar_batch_item* items, int count, double tau, int
         if (pc) {
             reblur.out = nullptr;
             reblur.mode = CONV_SPLIT3;
-            int folded = 0;
             reblur.planes = transform_input_planes(B->precs[j]->plan, &reblur.plane_stride,
-                                                   &reblur.ld, &folded);
-            if (folded) st = fail(AR_ERR_CUDA, "batch plan of item %d expects a folded input", j);
+                                                   &reblur.ld, &reblur.fold);
         } else {
             reblur.out = it.x_out;
             reblur.mode = CONV_AXPY;
@@ -386,10 +384,18 @@ ar_status ar_batch_results(ar_batch* B, double* rre_traces, int* best_iters,
     return st;
 }
 
-ar_status ar_batch_tuning(const ar_batch* B, int* geometry, int* ctas_per_sm, int* candidates,
-                          int* cand_geometry, int* cand_ctas, double* cand_ms, int max_candidates) {
+ar_status ar_batch_tuning(const ar_batch* B, int* geometry, int* ctas_per_sm, int* transform,
+                          int* candidates, int* cand_geometry, int* cand_ctas, double* cand_ms,
+                          int max_candidates) {
     if (!B) return fail(AR_ERR_INVALID_ARG, "null batch");
     if (geometry) *geometry = B->geometry;
+    if (transform) {
+        *transform = 0;
+        if (B->precondition && B->count > 0) {
+            *transform |= B->reblurs[0].fold ? 1 : 0;
+            *transform |= transform_group_paired(B->tg) ? 2 : 0;
+        }
+    }
     if (ctas_per_sm) *ctas_per_sm = B->ctas_per_sm;
     const int n = (int)B->cand_ms.size();
     if (candidates) *candidates = n;

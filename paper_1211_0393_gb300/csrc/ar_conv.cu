@@ -774,6 +774,7 @@ struct ConvJob {
     CUtensorMap mr;          // reblur input r_j
     ConvArgs blur, reblur;
     int q, ntx, ntiles;
+    int ncp, nunits;         // folded reblur: column pairs per row band, work units
 };
 
 template <int Q, class G>
@@ -790,6 +791,72 @@ __device__ __forceinline__ void group_tile(const ConvArgs& a, float* box, float*
         compute_tile<Q, true, G>(a, tile, WB, coef, r0, c0);
     else
         compute_tile<Q, false, G>(a, tile, WB, coef, r0, c0);
+}
+
+// A folded reblur unit: the tile at columns [c0, c0 + 64) (box A) and its mirror
+// at [cm, cm + 64), cm = n2 - c0 - 64 (box B), by the whole CTA one after the
+// other; column c0 + j pairs with column 63 - j of the mirror.  Writes the
+// bf16x3 split of y+_t = y_t + y_{n2-1-t} at column t and y-_t at Kh + t
+// (t = c0 + j), zeros past ceil(n2/2) resp. floor(n2/2), as the single-image
+// folding reblur.
+template <int Q, class G>
+__device__ __forceinline__ void group_fold_unit(const ConvArgs& a, float* boxA, float* boxB,
+                                                float* coef, int r0, int c0, int tid) {
+    constexpr int PADL = (Q + 3) & ~3;
+    constexpr int WB = TX + 2 * PADL, RS = G::RS;
+    const int cm = a.n2 - c0 - TX;
+    load_coefs<Q>(a, coef, tid, TX * G::TY);
+    __syncthreads();
+    float* ta = boxA + (PADL - Q);
+    float* tb = boxB + (PADL - Q);
+    const bool rows_out = r0 - Q < 0 || r0 + G::TH + Q > a.n1;
+    if (rows_out || c0 - Q < 0 || c0 + TX + Q > a.n2) fixup_tile<Q, G>(a, ta, WB, r0, c0, tid, TX * G::TY);
+    if (rows_out || cm - Q < 0 || cm + TX + Q > a.n2) fixup_tile<Q, G>(a, tb, WB, r0, cm, tid, TX * G::TY);
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    float acc[RS];
+    tile_acc<Q, G>(ta, WB, coef, tx, ty, acc);
+    __syncthreads();                     // box A consumed: it takes A's results
+#pragma unroll
+    for (int r = 0; r < RS; ++r) boxA[(ty * RS + r) * TX + tx] = acc[r];
+    tile_acc<Q, G>(tb, WB, coef, tx, ty, acc);
+    __syncthreads();                     // box B consumed: it takes B's results
+#pragma unroll
+    for (int r = 0; r < RS; ++r) boxB[(ty * RS + r) * TX + tx] = acc[r];
+    __syncthreads();
+    const int h = (a.n2 + 1) / 2, ha = a.n2 / 2, kh = (h + 63) / 64 * 64;
+    const int t = c0 + tx;
+#pragma unroll
+    for (int r = 0; r < RS; ++r) {
+        const int rr = ty * RS + r, row = r0 + rr;
+        if (row >= a.n1 || t >= kh) continue;
+        const float va = boxA[rr * TX + tx], vb = boxB[rr * TX + (TX - 1 - tx)];
+        split3_store(a.planes, a.plane_stride, (size_t)row * a.ld + t, t < h ? va + vb : 0.f);
+        split3_store(a.planes, a.plane_stride, (size_t)row * a.ld + kh + t, t < ha ? va - vb : 0.f);
+    }
+}
+
+template <class G>
+__device__ __forceinline__ void group_fold_dispatch(int q, const ConvArgs& a, float* boxA,
+                                                    float* boxB, float* coef, int r0, int c0,
+                                                    int tid) {
+    switch (q) {
+        case 0: group_fold_unit<0, G>(a, boxA, boxB, coef, r0, c0, tid); break;
+        case 1: group_fold_unit<1, G>(a, boxA, boxB, coef, r0, c0, tid); break;
+        case 2: group_fold_unit<2, G>(a, boxA, boxB, coef, r0, c0, tid); break;
+        case 3: group_fold_unit<3, G>(a, boxA, boxB, coef, r0, c0, tid); break;
+        case 4: group_fold_unit<4, G>(a, boxA, boxB, coef, r0, c0, tid); break;
+        case 5: group_fold_unit<5, G>(a, boxA, boxB, coef, r0, c0, tid); break;
+        case 6: group_fold_unit<6, G>(a, boxA, boxB, coef, r0, c0, tid); break;
+        case 7: group_fold_unit<7, G>(a, boxA, boxB, coef, r0, c0, tid); break;
+        case 8: group_fold_unit<8, G>(a, boxA, boxB, coef, r0, c0, tid); break;
+        case 9: group_fold_unit<9, G>(a, boxA, boxB, coef, r0, c0, tid); break;
+        case 10: group_fold_unit<10, G>(a, boxA, boxB, coef, r0, c0, tid); break;
+        case 11: group_fold_unit<11, G>(a, boxA, boxB, coef, r0, c0, tid); break;
+        case 12: group_fold_unit<12, G>(a, boxA, boxB, coef, r0, c0, tid); break;
+        case 13: group_fold_unit<13, G>(a, boxA, boxB, coef, r0, c0, tid); break;
+        case 14: group_fold_unit<14, G>(a, boxA, boxB, coef, r0, c0, tid); break;
+        default: group_fold_unit<15, G>(a, boxA, boxB, coef, r0, c0, tid); break;
+    }
 }
 
 template <class G>
@@ -841,17 +908,28 @@ conv_group_kernel(const ConvJob* __restrict__ jobs, const int2* __restrict__ ite
     __syncthreads();
     pdl_wait();                          // x_j and the planes come from the previous kernels
     const uint32_t polls = g_conv_wait_polls;
-    bool req[2] = {false, false};        // thread 0: a copy into buffer b is in flight / landed
+    bool req[2] = {false, false};        // thread 0: a copy on barrier b is in flight / landed
+    // a folded reblur unit takes both buffers (its tile and the mirror tile), so
+    // it is never prefetched and nothing is prefetched beside it
+    auto is_fold = [&](int item) { return item >= nblur && jobs[items[item].x].reblur.fold; };
     auto request = [&](int item, int b) {
         const int2 w = items[item];
         const ConvJob& J = jobs[w.x];
-        const int r0 = (w.y / J.ntx) * G::TH, c0 = (w.y % J.ntx) * TX;
         const int padl = (J.q + 3) & ~3;
         const uint32_t bytes = (uint32_t)(TX + 2 * padl) * (uint32_t)(G::TH + 2 * J.q) * 4u;
-        fence_proxy_async_smem();        // generic writes to the buffer (fix-up) before the copy
-        mbar_arrive_expect_tx(bar0 + 8u * b, bytes);
-        tma_load_2d(smem_u32(box(b)), item >= nblur ? &J.mr : &J.mx, c0 - padl, r0 - J.q,
-                    bar0 + 8u * b);
+        fence_proxy_async_smem();        // generic writes to the buffers (fix-up) before the copy
+        if (is_fold(item)) {
+            const int r0 = (w.y / J.ncp) * G::TH, c0 = (w.y % J.ncp) * TX;
+            const int cm = J.reblur.n2 - c0 - TX;
+            mbar_arrive_expect_tx(bar0 + 8u * b, 2u * bytes);
+            tma_load_2d(smem_u32(box(0)), &J.mr, c0 - padl, r0 - J.q, bar0 + 8u * b);
+            tma_load_2d(smem_u32(box(1)), &J.mr, cm - padl, r0 - J.q, bar0 + 8u * b);
+        } else {
+            const int r0 = (w.y / J.ntx) * G::TH, c0 = (w.y % J.ntx) * TX;
+            mbar_arrive_expect_tx(bar0 + 8u * b, bytes);
+            tma_load_2d(smem_u32(box(b)), item >= nblur ? &J.mr : &J.mx, c0 - padl, r0 - J.q,
+                        bar0 + 8u * b);
+        }
         req[b] = true;
     };
     auto ready = [&](int item) {         // a reblur tile's image has all its blur tiles done
@@ -889,7 +967,7 @@ conv_group_kernel(const ConvJob* __restrict__ jobs, const int2* __restrict__ ite
             if (!slot[2]) {              // the next item, prefetched when it can start
                 const int nx = atomicAdd(ctr, 1);
                 slot[b ^ 1] = nx;
-                if (nx < nitems && ready(nx)) {
+                if (nx < nitems && !is_fold(item) && !is_fold(nx) && ready(nx)) {
                     fence_proxy_async_global();
                     request(nx, b ^ 1);
                 }
@@ -911,8 +989,13 @@ conv_group_kernel(const ConvJob* __restrict__ jobs, const int2* __restrict__ ite
         const bool re = item >= nblur;
         ConvArgs a = re ? J.reblur : J.blur;
         if (a.sumsq) a.sumsq += iter;
-        const int r0 = (w.y / J.ntx) * G::TH, c0 = (w.y % J.ntx) * TX;
-        group_dispatch<G>(J.q, a, box(b), coef, r0, c0, tid);
+        if (re && a.fold) {
+            const int r0 = (w.y / J.ncp) * G::TH, c0 = (w.y % J.ncp) * TX;
+            group_fold_dispatch<G>(J.q, a, box(0), box(1), coef, r0, c0, tid);
+        } else {
+            const int r0 = (w.y / J.ntx) * G::TH, c0 = (w.y % J.ntx) * TX;
+            group_dispatch<G>(J.q, a, box(b), coef, r0, c0, tid);
+        }
         if (!re) {
             __syncthreads();             // the tile's r is written
             if (tid == 0) {
@@ -1014,10 +1097,10 @@ ar_status conv_group_create(const ConvArgs* blurs, const ConvArgs* reblurs, int 
         const int q = b.q1 > b.q2 ? b.q1 : b.q2;
         if (q > QMAX_FAST || b.bc == AR_BC_PERIODIC || (b.n2 & 3) != 0 ||
             (reinterpret_cast<uintptr_t>(b.x) & 15) != 0 || (reinterpret_cast<uintptr_t>(r.x) & 15) != 0 ||
-            b.mode != CONV_RESIDUAL || r.fold)
+            b.mode != CONV_RESIDUAL || (r.fold && r.mode != CONV_SPLIT3))
             return fail(AR_ERR_UNSUPPORTED,
-                        "batched stencil: image %d needs q <= 15, n2 %% 4 == 0, aligned rows, "
-                        "an unfolded reblur and a non-periodic BC", j);
+                        "batched stencil: image %d needs q <= 15, n2 %% 4 == 0, aligned rows "
+                        "and a non-periodic BC", j);
         ConvJob& J = jobs[(size_t)j];
         std::memset(&J, 0, sizeof(J));
         J.blur = b;
@@ -1025,6 +1108,8 @@ ar_status conv_group_create(const ConvArgs* blurs, const ConvArgs* reblurs, int 
         J.q = q;
         J.ntx = (b.n2 + TX - 1) / TX;
         J.ntiles = J.ntx * ((b.n1 + th - 1) / th);
+        J.ncp = ((b.n2 + 1) / 2 + TX - 1) / TX;
+        J.nunits = J.ncp * ((b.n1 + th - 1) / th);
         if (!make_box_map(b.x, b.n1, b.n2, q, th, &J.mx) || !make_box_map(r.x, r.n1, r.n2, q, th, &J.mr))
             return fail(AR_ERR_CUDA, "batched stencil: tensor map of image %d", j);
         cost[(size_t)j] = (double)b.n1 * b.n2 * (2 * q + 1) * (2 * q + 1);
@@ -1035,15 +1120,20 @@ ar_status conv_group_create(const ConvArgs* blurs, const ConvArgs* reblurs, int 
     for (int j = 0; j < count; ++j) order[(size_t)j] = j;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[(size_t)a] > cost[(size_t)b]; });
     std::vector<int2> items;
-    for (int pass = 0; pass < 2; ++pass)
-        for (int j : order)
-            for (int t = 0; t < jobs[(size_t)j].ntiles; ++t) items.push_back(make_int2(j, t));
+    for (int j : order)                                   // blur tiles
+        for (int t = 0; t < jobs[(size_t)j].ntiles; ++t) items.push_back(make_int2(j, t));
+    const int nblur = (int)items.size();
+    for (int j : order) {                                 // reblur tiles, or folded units
+        const ConvJob& J = jobs[(size_t)j];
+        const int n = J.reblur.fold ? J.nunits : J.ntiles;
+        for (int t = 0; t < n; ++t) items.push_back(make_int2(j, t));
+    }
     ConvGroup* g = new (std::nothrow) ConvGroup();
     if (!g) return fail(AR_ERR_ALLOC, "host allocation of the batched stencil");
     g->geometry = geometry;
     g->count = count;
     g->nitems = (int)items.size();
-    g->nblur = g->nitems / 2;
+    g->nblur = nblur;
     g->iters = iters;
     g->stride = 1 + count;
     g->buf = box_bytes(qmax, th);

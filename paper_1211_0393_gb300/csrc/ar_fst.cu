@@ -397,7 +397,7 @@ static ar_status fst_transpose(const float* in, float* out, int rows, int cols, 
 
 ar_status fst_apply(FstPlan* p, const float* d32, const float* y, float* out, bool axpy, float tau,
                     cudaStream_t s, const float* f, double* sumsq) {
-    ProfScope prof(AR_PROF_CONTRACTION, s);
+    ProfScope prof(AR_PROF_CONTRACTION, s, 6);
     const int n1 = p->n1, n2 = p->n2;
     const float* src = y ? y : p->in;
     FstArgs a{};

@@ -161,12 +161,11 @@ struct TransformPlan;
 // AR_PRECISION_BF16X2 (two planes, three products); bc: an ar_bc value.
 // fold_input: the stencil producing the DIN_SPLIT input can write it folded
 // along the columns (AR plans then take it so when n2 is a multiple of 4).
-// pair_out: AR plans may run their last contraction in parity-paired clusters
-// of four when that fits (false: always the unpaired kernel, as grouped
-// launches need).
+// pair_out: AR plans run their last contraction in parity-paired clusters of
+// four never (0), when all clusters fit at once or waves are unavoidable (1),
+// or always (2, grouped launches, whose items come in many waves anyway).
 ar_status transform_plan_create(int n1, int n2, int bc, int precision, cudaStream_t stream,
-                                TransformPlan** out, bool fold_input = false,
-                                bool pair_out = true);
+                                TransformPlan** out, bool fold_input = false, int pair_out = 1);
 void transform_plan_destroy(TransformPlan* p);
 // Frees the plan's buffers in the order of stream s (after its pending work).
 void transform_plan_release(TransformPlan* p, cudaStream_t s);
@@ -207,14 +206,16 @@ int transform_launches(const TransformPlan* p, DInput din);
 
 // The four contractions of x_j += tau D_j z_j for many AR plans in four grouped
 // launches (one per contraction, every plan's tiles as work items, largest K
-// first).  Each plan must be unpaired (transform_plan_create with pair_out
-// false) and read its input as written by its reblur (DIN_SPLIT); fs[j] (may be
+// first).  The plans must agree on the last contraction's pairing
+// (transform_plan_create's pair_out) and read their input as written by their
+// reblur (DIN_SPLIT); fs[j] (may be
 // null) and sumsq[j] give the RRE accumulation, sumsq[j] + iter per iteration.
 struct TransformGroup;
 ar_status transform_group_create(TransformPlan* const* plans, int count, float* const* outs,
                                  const float* const* fs, double* const* sumsq, float tau,
                                  TransformGroup** out);
 ar_status transform_group_apply(TransformGroup* g, int iter, cudaStream_t s);
+bool transform_group_paired(const TransformGroup* g);
 void transform_group_destroy(TransformGroup* g);
 
 // Device int set to 1 by a contraction kernel whose bounded wait gave up.
@@ -304,14 +305,17 @@ bool corr_on_current_device(const ar_corr* model);
 // Launch accounting: every kernel launch site calls count_launch(k).
 void count_launch(unsigned k = 1);
 
-// Profiling (ar_profile_begin/end): bracket a launch with prof_begin/prof_end.
-int prof_begin(int kind, cudaStream_t s);
+// Profiling (ar_profile_begin/end): bracket `launches` kernel launches of one
+// class with prof_begin/prof_end; scopes opened inside a recording scope are
+// not recorded (dependent launches are timed together, overlap included).
+int prof_begin(int kind, cudaStream_t s, unsigned launches);
 void prof_end(int idx, cudaStream_t s);
 
 struct ProfScope {
     int idx;
     cudaStream_t s;
-    ProfScope(int kind, cudaStream_t st) : idx(prof_begin(kind, st)), s(st) {}
+    ProfScope(int kind, cudaStream_t st, unsigned launches = 1)
+        : idx(prof_begin(kind, st, launches)), s(st) {}
     ~ProfScope() { prof_end(idx, s); }
 };
 

@@ -15,8 +15,13 @@ namespace {
 
 struct Rec {
     int kind;
+    unsigned launches;
     cudaEvent_t a, b;
 };
+
+// Scopes opened inside a recording scope on the same thread are not recorded:
+// an interval that brackets several dependent launches is timed as a whole.
+thread_local int g_depth = 0;
 
 std::mutex g_mu;
 std::atomic<bool> g_on{false};
@@ -36,20 +41,22 @@ cudaEvent_t get_event() {
 
 }  // namespace
 
-int prof_begin(int kind, cudaStream_t s) {
-    if (!g_on.load(std::memory_order_relaxed)) return -1;
+int prof_begin(int kind, cudaStream_t s, unsigned launches) {
+    if (!g_on.load(std::memory_order_relaxed) || g_depth > 0) return -1;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
         return -1;                        // a captured graph is not timed kernel by kernel
     std::lock_guard<std::mutex> lock(g_mu);
-    Rec r{kind, get_event(), get_event()};
+    Rec r{kind, launches, get_event(), get_event()};
     cudaEventRecord(r.a, s);
     g_recs.push_back(r);
+    ++g_depth;
     return (int)g_recs.size() - 1;
 }
 
 void prof_end(int idx, cudaStream_t s) {
     if (idx < 0) return;
+    --g_depth;
     std::lock_guard<std::mutex> lock(g_mu);
     if (idx < (int)g_recs.size()) cudaEventRecord(g_recs[idx].b, s);
 }
@@ -83,7 +90,7 @@ ar_status ar_profile_end(double* ms, unsigned long long* launches, int nkinds) {
             st = fail(AR_ERR_CUDA, "ar_profile_end: event timing failed");
         if (r.kind >= 0 && r.kind < nkinds) {
             ms[r.kind] += t;
-            launches[r.kind] += 1;
+            launches[r.kind] += r.launches;
         }
         g_pool.push_back(r.a);
         g_pool.push_back(r.b);

@@ -584,6 +584,20 @@ tc_contract_group_kernel(const GroupJob* __restrict__ jobs, const int4* __restri
     tc_contract_body<NP, false>(J.tmA, J.tmA64, J.tmB, J.tmO, J.M, J.N, J.K, ep, J.err, it.y, it.z);
 }
 
+// The parity-paired last contraction of many problems: an item is a tile pair
+// (n tile c of both parities), the cluster (1, 2, SPLITK) at grid y = parity.
+template <int NP>
+__global__ void __cluster_dims__(1, 2, SPLITK) __launch_bounds__(NTHREADS, 1)
+tc_contract_group_pair_kernel(const GroupJob* __restrict__ jobs, const int4* __restrict__ items,
+                              int iter) {
+    const int4 it = items[blockIdx.x];                    // (job, m tile, n tile pair, -)
+    const GroupJob& J = jobs[it.x];
+    TcEpiArgs ep = J.ep;
+    if (ep.sumsq) ep.sumsq += iter;
+    tc_contract_body<NP, true>(J.tmA, J.tmA64, J.tmB, J.tmO, J.M, J.N, J.K, ep, J.err, it.y,
+                               2 * it.z + (int)(blockIdx.y & 1u));
+}
+
 // ---------------------------------------------------------------- matrices --
 // Q_{m-2}[s, t] = sqrt(2/(m-1)) sin(s t pi/(m-1)) depends only on
 // r = (s t) mod 2(m-1): tab[r] holds the 2(m-1) distinct values, in float64.
@@ -1055,7 +1069,7 @@ struct TransformPlan {
 };
 
 ar_status transform_plan_create(int n1, int n2, int bc, int precision, cudaStream_t s,
-                                TransformPlan** out, bool fold_input, bool pair_out) {
+                                TransformPlan** out, bool fold_input, int pair_out) {
     TransformPlan* p = new (std::nothrow) TransformPlan();
     if (!p) return fail(AR_ERR_ALLOC, "host allocation of the transform plan");
     p->n1 = n1;
@@ -1070,7 +1084,7 @@ ar_status transform_plan_create(int n1, int n2, int bc, int precision, cudaStrea
         const FoldDims f1 = fold_dims(n1), f2 = fold_dims(n2);
         const int need = ((f2.h + BM / 2 - 1) / (BM / 2)) * (f1.Hs / BN);
         const int fit = p->np == 2 ? max_quad_clusters<2>() : max_quad_clusters<3>();
-        p->fold_out = pair_out && fit > 0 && (need <= fit || need > 2 * fit);
+        p->fold_out = fit > 0 && (pair_out == 2 || (pair_out == 1 && (need <= fit || need > 2 * fit)));
     }
     TransformSet t1, t2;
     ar_status st = cached_transforms(n1, bc, s, &t1);
@@ -1181,6 +1195,7 @@ ar_status transform_spectral_view(const TransformPlan* p, const uint16_t** plane
 // been written by its reblur (DIN_SPLIT); its G4 must be the unpaired one.
 struct TransformGroup {
     int np = 3, count = 0;
+    bool pair_g4 = false;
     GroupJob* jobs[4] = {nullptr, nullptr, nullptr, nullptr};
     int4* items[4] = {nullptr, nullptr, nullptr, nullptr};
     int nitems[4] = {0, 0, 0, 0};
@@ -1204,6 +1219,10 @@ cudaError_t group_kernel_attr() {
         attr = cudaFuncSetAttribute(tc_contract_group_kernel<NP>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)TcMode<NP>::SMEM_BYTES);
+        if (attr == cudaSuccess)
+            attr = cudaFuncSetAttribute(tc_contract_group_pair_kernel<NP>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)TcMode<NP>::SMEM_BYTES);
     });
     return attr;
 }
@@ -1214,11 +1233,12 @@ ar_status transform_group_create(TransformPlan* const* plans, int count, float* 
                                  TransformGroup** out) {
     if (count < 1) return fail(AR_ERR_INVALID_ARG, "empty transform group");
     const int np = plans[0]->np;
+    const bool pair = plans[0]->fold_out;
     for (int j = 0; j < count; ++j) {
         const TransformPlan* p = plans[j];
-        if (!p->folded || p->fold_out || p->np != np)
-            return fail(AR_ERR_UNSUPPORTED, "grouped transform: plan %d is not an unpaired AR "
-                                            "plan of the group's precision", j);
+        if (!p->folded || p->fold_out != pair || p->np != np)
+            return fail(AR_ERR_UNSUPPORTED, "grouped transform: plan %d is not an AR plan of the "
+                                            "group's precision and G4 pairing", j);
     }
     const int mi = mode_index(np);
     std::vector<GroupJob> jobs[4];
@@ -1277,6 +1297,15 @@ ar_status transform_group_create(TransformPlan* const* plans, int count, float* 
         A[3] = &p->V;
         B[3] = &p->Tsp1;
         O[3] = nullptr;
+        if (pair) {                       // N folded too: block diagonal, parity tiles paired
+            e[3].kdiag = 1;
+            e[3].npar = 1;
+            e[3].nhalf = f1.Hs;
+            e[3].npairn = f1.h;
+            e[3].nminusn = f1.ha;
+            e[3].noutn = p->n1;
+            B[3] = &p->Tsf1;
+        }
         for (int k = 0; k < 4; ++k) {
             GroupJob gj;
             std::memset(&gj, 0, sizeof(gj));
@@ -1291,7 +1320,8 @@ ar_status transform_group_create(TransformPlan* const* plans, int count, float* 
             gj.ep = e[k];
             gj.err = p->err;
             const int mt = e[k].pair ? (e[k].npair + BM / 2 - 1) / (BM / 2) : (A[k]->rows + BM - 1) / BM;
-            const int nt = (B[k]->rows + BN - 1) / BN;
+            // a paired item covers the n tile c of both parities (the N halves)
+            const int nt = e[k].npar ? e[k].nhalf / BN : (B[k]->rows + BN - 1) / BN;
             const int keff = e[k].kdiag ? A[k]->K / 2 : A[k]->K;
             const int job = (int)jobs[k].size();
             jobs[k].push_back(gj);
@@ -1303,6 +1333,7 @@ ar_status transform_group_create(TransformPlan* const* plans, int count, float* 
     if (!g) return fail(AR_ERR_ALLOC, "host allocation of the transform group");
     g->np = np;
     g->count = count;
+    g->pair_g4 = pair;
     cudaError_t ce = np == 2 ? group_kernel_attr<2>() : group_kernel_attr<3>();
     for (int k = 0; ce == cudaSuccess && k < 4; ++k) {
         std::stable_sort(items[k].begin(), items[k].end(),
@@ -1328,18 +1359,19 @@ ar_status transform_group_create(TransformPlan* const* plans, int count, float* 
     return AR_OK;
 }
 
+bool transform_group_paired(const TransformGroup* g) { return g && g->pair_g4; }
+
 ar_status transform_group_apply(TransformGroup* g, int iter, cudaStream_t s) {
     for (int k = 0; k < 4; ++k) {
         ProfScope prof(AR_PROF_CONTRACTION, s);
         count_launch();
-        const dim3 grid((unsigned)g->nitems[k], 1, SPLITK);
-        cudaError_t e = g->np == 2
-            ? launch_pdl(tc_contract_group_kernel<2>, grid, dim3(NTHREADS),
-                         (size_t)TcMode<2>::SMEM_BYTES, s, (const GroupJob*)g->jobs[k],
-                         (const int4*)g->items[k], iter)
-            : launch_pdl(tc_contract_group_kernel<3>, grid, dim3(NTHREADS),
-                         (size_t)TcMode<3>::SMEM_BYTES, s, (const GroupJob*)g->jobs[k],
-                         (const int4*)g->items[k], iter);
+        const bool pk = k == 3 && g->pair_g4;
+        const dim3 grid((unsigned)g->nitems[k], pk ? 2 : 1, SPLITK);
+        auto kern = g->np == 2 ? (pk ? tc_contract_group_pair_kernel<2> : tc_contract_group_kernel<2>)
+                               : (pk ? tc_contract_group_pair_kernel<3> : tc_contract_group_kernel<3>);
+        const size_t smem = g->np == 2 ? (size_t)TcMode<2>::SMEM_BYTES : (size_t)TcMode<3>::SMEM_BYTES;
+        cudaError_t e = launch_pdl(kern, grid, dim3(NTHREADS), smem, s, (const GroupJob*)g->jobs[k],
+                                   (const int4*)g->items[k], iter);
         if (e != cudaSuccess) return cuda_fail(e, "grouped contraction launch");
     }
     return AR_OK;
@@ -1378,6 +1410,8 @@ ar_status transform_apply(TransformPlan* p, const float* d32, const float* d32_o
         count_launch();
         AR_CUDA(cudaGetLastError());
     }
+    // the four contractions are dependent launches: timed as one interval
+    ProfScope prof(AR_PROF_CONTRACTION, s, (unsigned)transform_launches(p, DIN_SPLIT));
     if (p->folded) {
         // G1: U = fold_1((Y Ttp2^T)^T)   A = Y rows paired (i, n1-1-i), output K-folded
         // G2: W = d o (U Ttf1^T)^T       block diagonal in K

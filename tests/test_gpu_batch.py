@@ -4,10 +4,11 @@ ar_restore_ex calls and the FP64 oracle.
 
 The stencils of the batch are the single-image stencils' code, so plain
 Landweber (stencils only) is bit-identical to per-image calls.  Preconditioned,
-the batch's contractions read the unfolded reblur and run the last product
-unpaired, a different float32 rounding of the same transform: both are within
-the per-iterate bound tol(alpha) of the exact iterate, so within 2 tol(alpha) of
-each other (bf16x2: 2 tol_fast)."""
+the batch always runs the last product in parity-paired clusters (the
+single-image loop only where they fit in one wave), a different float32
+rounding of the same transform: both are within the per-iterate bound
+tol(alpha) of the exact iterate, so within 2 tol(alpha) of each other (bf16x2:
+2 tol_fast)."""
 
 import numpy as np
 import pytest
@@ -120,8 +121,10 @@ def test_batch_autotuner_reports_its_candidates(ar):
     assert (best["geometry"], best["ctas_per_sm"]) == (t["geometry"], t["ctas_per_sm"])
     B.run()
     B.results()
+    assert t["folded_input"] and t["paired_last_product"]
     B2 = ar.Batch(ims, iters=4, precondition=True, tuning=1)
-    assert B2.tuning() == {"geometry": "64-row", "ctas_per_sm": 1, "candidates": []}
+    t2 = B2.tuning()
+    assert (t2["geometry"], t2["ctas_per_sm"], t2["candidates"]) == ("64-row", 1, [])
     B2.close()
     B.close()
 
