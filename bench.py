@@ -852,6 +852,16 @@ def quality_vs_plain(ar, torch, stream, g_d, f_d, h, flush, oracle_best):
         out["iteration_ratio_plain_over_precond"] = round(kp / kd, 3)
         out["time_ratio_plain_over_precond"] = round(out["plain_ms_to_target"] /
                                                      out["precond_ms_to_target"], 3)
+    # the alpha reading: the bench takes the smallest half-decade alpha for which
+    # tau = 1 is stable; the survey's rule would minimise iterations to the best RRE
+    sweep = {}
+    for a in (0.03, 0.1, 0.3, 1.0):
+        _, tr_a, best_a = ar.ar_restore(g_d, h, a, TAU, ITERS, True, f_true=f_d)
+        tr_a = np.nan_to_num(np.asarray(tr_a), nan=np.inf)
+        sweep[str(a)] = {"best_rre": round(float(np.min(tr_a)), 6), "best_iter": best_a,
+                         "final_rre": float(tr_a[-1]),
+                         "iters_to_target": first(tr_a)}
+    out["alpha_sweep"] = sweep
     return out
 
 
@@ -914,6 +924,7 @@ def cpu_baseline(h, g, f):
                          "thread_env": {v: env[v] for v in THREAD_VARS}}
     finally:
         os.unlink(path)
+    extra = oracle_plan_extras()
     return {"value": legs["all"]["value"], "unit": UNIT, "cores": legs["all"]["threads"],
             "kind": "oracle",
             "sample": (f"FP64 NumPy oracle, D-Landweber on the {WORKLOAD} workload, "
@@ -921,7 +932,44 @@ def cpu_baseline(h, g, f):
                        f"{CPU_SAMPLE_ITERS['1']} with one thread (setup included), median of 3 "
                        f"runs each, each run a fresh process"),
             "single_thread": legs["1"], "all_cores": legs["all"],
-            "cpu": cpu_model(), "cpu_count": os.cpu_count()}
+            "cpu": cpu_model(), "cpu_count": os.cpu_count(), **extra}
+
+
+PLAIN_SAMPLE_ITERS = 20
+PAPER_LANDWEBER_ITERS = 12824     # Table 2, Bridge, AR-BCs: plain Landweber iterations to best RRE
+
+
+def oracle_plan_extras():
+    """The rest of the CPU-baseline plan, default threads: config 1 (64^2, 9 x 9
+    Gaussian, 1% noise, alpha 0.03, 20 D-Landweber iterations, FP64) run in full,
+    and plain Landweber at 256^2 on the bench's PSF timed per iteration and
+    extrapolated, labelled as such, to the paper's 12,824 iterations (Table 2)."""
+    import oracle as O
+
+    h1 = W.psf_config1()
+    q1, q2 = O.psf_support(h1)
+    ext, f, e = W.make_inputs(64, 64, h1, "blocks", 0)
+    g = W.add_noise(W.crop(O.ar_blur(ext, h1), q1, q2), e, 0.01)
+    t0 = time.perf_counter()
+    O.restore(g, h1, 0.03, 1.0, 20, True, f_true=f)
+    t_c1 = time.perf_counter() - t0
+    h2 = W.psf_config2()
+    q1, q2 = O.psf_support(h2)
+    ext, f, e = W.make_inputs(256, 256, h2, "ellipses", 1)
+    g = W.add_noise(W.crop(O.ar_blur(ext, h2), q1, q2), e, NU)
+    O.restore(g, h2, ALPHA, TAU, 1, False)
+    t0 = time.perf_counter()
+    O.restore(g, h2, ALPHA, TAU, PLAIN_SAMPLE_ITERS, False)
+    per = (time.perf_counter() - t0) / PLAIN_SAMPLE_ITERS
+    return {"config1_full": {"seconds": round(t_c1, 4), "workload": "64^2 blocks, 9x9 Gaussian, "
+                                                                   "1% noise, alpha 0.03, 20 "
+                                                                   "D-Landweber iterations, FP64"},
+            "plain_landweber_256": {"seconds_per_iteration": round(per, 5),
+                                    "measured_iterations": PLAIN_SAMPLE_ITERS,
+                                    "extrapolated_seconds_for_12824_iterations":
+                                        round(per * PAPER_LANDWEBER_ITERS, 1),
+                                    "note": "extrapolation: per-iteration time x the paper's "
+                                            "plain Landweber count (Table 2), not a run"}}
 
 
 def oracle_sample_main(path, iters):

@@ -142,3 +142,55 @@ def test_batch_rejects_unsupported_shapes(ar):
     with pytest.raises(ar.ARError) as ei:
         ar.Batch(ims, iters=2)
     assert ei.value.name == "AR_ERR_UNSUPPORTED"
+
+
+def test_full_batch_configuration_sampled_images_match_oracle(ar):
+    """The benchmarked batch configuration itself: all 96 images (sides from
+    {128..1024} per axis, own PSF 5x5..31x31, 0.5% noise, each PSF's alpha the
+    smallest stable half-decade value), 50 iterations, autotuned, in one batch.
+    The three smallest images are compared with the FP64 oracle's 50-iteration
+    restorations (inputs blurred by the oracle), iterate and RRE trace."""
+    import importlib.util
+    import os
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench_for_alpha", os.path.join(root, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    argv, sys.argv = sys.argv, ["bench.py"]
+    try:
+        spec.loader.exec_module(bench)
+    finally:
+        sys.argv = argv
+    iters = 50
+    ims = []
+    for sp in W.batch_specs(96):
+        ext, f, e = W.batch_inputs(sp)
+        h = sp["psf"]
+        q1, q2 = O.psf_support(h)
+        n = sp["n1"] * sp["n2"]
+        small = n <= 128 * 192
+        # the oracle blurs the small images it checks; the rest only need to be run
+        if small:
+            gc = W.crop(O.ar_blur(ext, h), q1, q2)
+        else:
+            gc = W.crop(ar.ar_blur_apply(torch.from_numpy(ext.astype(np.float32)).cuda(),
+                                         torch.from_numpy(h.astype(np.float32)).cuda())
+                        .cpu().numpy().astype(np.float64), q1, q2)
+        g = W.add_noise(gc, e, 0.005).astype(np.float32)
+        ims.append({"g": torch.from_numpy(g).cuda(), "psf": h, "alpha": bench.stable_alpha(h),
+                    "f_true": torch.from_numpy(f.astype(np.float32)).cuda(),
+                    "x_out": torch.empty(sp["n1"], sp["n2"], device="cuda"), "g64": g,
+                    "f64": f.astype(np.float32).astype(np.float64), "n": n, "small": small})
+    B = ar.Batch(ims, iters=iters, precondition=True, tuning=0)
+    B.run()
+    tr, best, _ = B.results()
+    order = sorted((j for j, im in enumerate(ims) if im["small"]), key=lambda j: ims[j]["n"])[:3]
+    assert len(order) == 3
+    for j in order:
+        im = ims[j]
+        xo, to, bo = O.restore(im["g64"].astype(np.float64), im["psf"], im["alpha"], 1.0, iters,
+                               True, f_true=im["f64"])
+        tol = tol_alpha(im["alpha"])
+        assert rel(im["x_out"].cpu().numpy(), xo) <= tol, (j, im["alpha"])
+        assert np.all(np.abs(tr[j] - to) <= tol * (1 + to)), j
+    B.close()
