@@ -86,6 +86,23 @@ typedef enum ar_bc { AR_BC_ANTIREFLECTIVE = 0, AR_BC_REFLECTIVE = 1, AR_BC_PERIO
 typedef enum ar_precision { AR_PRECISION_FP32 = 0, AR_PRECISION_BF16X2 = 1,
                             AR_PRECISION_FFT = 2, AR_PRECISION_AUTO = 3 } ar_precision;
 
+/* Arithmetic of the blur and reblur stencils (the convolution of eq.
+ * modello_discreto under the extension rules of Section 2.2 / 2.1).  OR
+ * AR_STENCIL_F16X2 into the precision argument of ar_restore_ex,
+ * ar_restore_bc and ar_restore_residuals, or pass it to ar_blur_apply_ex /
+ * ar_reblur_apply_ex.
+ *  AR_STENCIL_FP32:  float32 FMAs on the CUDA cores (the default).
+ *  AR_STENCIL_F16X2: banded-Toeplitz products on the tensor cores.  Each
+ *                    128 x 64 output tile scales its input box by a power of two
+ *                    (largest magnitude to [2^14, 2^15)) and splits it into two
+ *                    fp16 parts, as it does the PSF; three of the four products
+ *                    accumulate in float32 (about 2^-21 relative per term, the
+ *                    float32 stencil's order).  Serves q1, q2 <= 8 under AR and
+ *                    Reflective BCs with n2 % 4 == 0 and a 16-byte aligned
+ *                    input; other arguments take AR_STENCIL_FP32. */
+#define AR_STENCIL_FP32 0
+#define AR_STENCIL_F16X2 16
+
 /* Opaque preconditioner: the symmetrized-PSF eigenvalues and Tikhonov filter
  * for one (PSF, n1, n2, alpha), plus the AR transform operands and scratch
  * used by ar_symprec_solve.  Owned by the library; free with
@@ -125,6 +142,18 @@ AR_API ar_status ar_blur_apply_bc(const float* x, float* y, int n1, int n2,
                                   const float* psf, int q1, int q2, int bc, void* stream);
 AR_API ar_status ar_reblur_apply_bc(const float* x, float* y, int n1, int n2,
                                     const float* psf, int q1, int q2, int bc, void* stream);
+
+/*
+ * ar_blur_apply_bc / ar_reblur_apply_bc with the stencil arithmetic `stencil`
+ * (AR_STENCIL_FP32 or AR_STENCIL_F16X2).  With AR_STENCIL_F16X2 the call
+ * allocates (stream-ordered) and frees a plan of about 70 KB for the PSF.
+ * Arguments and errors as ar_blur_apply_bc, plus AR_ERR_INVALID_ARG for an
+ * unknown stencil and AR_ERR_ALLOC when the plan cannot be allocated.
+ */
+AR_API ar_status ar_blur_apply_ex(const float* x, float* y, int n1, int n2, const float* psf,
+                                  int q1, int q2, int bc, int stencil, void* stream);
+AR_API ar_status ar_reblur_apply_ex(const float* x, float* y, int n1, int n2, const float* psf,
+                                    int q1, int q2, int bc, int stencil, void* stream);
 
 /*
  * Build the optimal AR preconditioner (Theorem 4) for a PSF and image size:
@@ -261,7 +290,9 @@ AR_API ar_status ar_restore_plain_static(const float* g, const double* psf_host,
                                          double* rre_trace, int* best_iter, void* stream);
 
 /* ar_restore with an explicit ar_precision for the preconditioner's
- * contractions (ignored when precondition == 0).  ar_restore is
+ * contractions (ignored when precondition == 0), optionally OR-ed with
+ * AR_STENCIL_F16X2 for the blur and reblur stencils (honoured with and
+ * without the preconditioner).  ar_restore is
  * ar_restore_ex(..., AR_PRECISION_FP32, ...). */
 AR_API ar_status ar_restore_ex(const float* g, const double* psf_host,
                                int n1, int n2, int q1, int q2, double alpha, double tau,

@@ -35,7 +35,7 @@ EXPORTS = [
     "ar_corr_targets", "ar_corr_train", "ar_corr_predict", "ar_symprec_setup_corrected",
     "ar_restore_prec", "ar_restore_residuals", "ar_set_stencil_wait_polls",
     "ar_inject_alloc_failures", "ar_corr_train_tables", "ar_corr_restoration_targets",
-    "ar_batch_tuning", "ar_symprec_precision",
+    "ar_batch_tuning", "ar_symprec_precision", "ar_blur_apply_ex", "ar_reblur_apply_ex",
 ]
 
 DEFAULT_WAIT_POLLS = 1 << 24
@@ -51,6 +51,9 @@ class BatchItem(ctypes.Structure):
 
 PRECISION = {"fp32": 0, "bf16x2": 1, "fft": 2, "auto": 3}
 PRECISION_NAME = {v: k for k, v in PRECISION.items()}
+
+# stencil arithmetic (ar.h AR_STENCIL_*): float32 FMAs or tensor-core fp16 split
+STENCIL = {"fp32": 0, "f16x2": 16}
 
 # ar_bc: the method's anti-reflective BCs and the two comparison BCs
 BC = {"ar": 0, "reflective": 1, "periodic": 2}
@@ -83,6 +86,8 @@ def lib() -> ctypes.CDLL:
             "ar_reblur_apply": [_vp, _vp, _i, _i, _vp, _i, _i, _vp],
             "ar_blur_apply_bc": [_vp, _vp, _i, _i, _vp, _i, _i, _i, _vp],
             "ar_reblur_apply_bc": [_vp, _vp, _i, _i, _vp, _i, _i, _i, _vp],
+            "ar_blur_apply_ex": [_vp, _vp, _i, _i, _vp, _i, _i, _i, _i, _vp],
+            "ar_reblur_apply_ex": [_vp, _vp, _i, _i, _vp, _i, _i, _i, _i, _vp],
             "ar_symprec_setup_bc": [_vp, _i, _i, _i, _i, _d, _i, _i, _vp, ctypes.POINTER(_vp)],
             "ar_restore_bc": [_vp, _vp, _i, _i, _i, _i, _d, _d, _i, _i, _i, _i, _vp, _vp, _vp, _vp,
                               _vp, _vp],
@@ -188,20 +193,21 @@ def _host_psf(psf) -> np.ndarray:
 
 
 def ar_blur_apply(x: torch.Tensor, psf: torch.Tensor, y: torch.Tensor | None = None,
-                  stream=None, bc: str = "ar") -> torch.Tensor:
+                  stream=None, bc: str = "ar", stencil: str = "fp32") -> torch.Tensor:
     """``y = A_n x`` (blur under ``bc``: "ar", "reflective" or "periodic").
 
-    ``psf`` is a float32 CUDA tensor of odd sides."""
-    return _apply("ar_blur_apply", x, psf, y, stream, bc)
+    ``psf`` is a float32 CUDA tensor of odd sides; ``stencil`` "fp32" (CUDA-core
+    FMAs) or "f16x2" (tensor cores, two-plane fp16 split, where it applies)."""
+    return _apply("ar_blur_apply", x, psf, y, stream, bc, stencil)
 
 
 def ar_reblur_apply(x: torch.Tensor, psf: torch.Tensor, y: torch.Tensor | None = None,
-                    stream=None, bc: str = "ar") -> torch.Tensor:
+                    stream=None, bc: str = "ar", stencil: str = "fp32") -> torch.Tensor:
     """``y = A' x`` (the blur under ``bc`` with the PSF rotated by 180 degrees)."""
-    return _apply("ar_reblur_apply", x, psf, y, stream, bc)
+    return _apply("ar_reblur_apply", x, psf, y, stream, bc, stencil)
 
 
-def _apply(name, x, psf, y, stream, bc="ar"):
+def _apply(name, x, psf, y, stream, bc="ar", stencil="fp32"):
     _image(x, "x")
     if not isinstance(psf, torch.Tensor) or not psf.is_cuda or psf.dtype != torch.float32:
         raise TypeError("psf must be a float32 CUDA tensor")
@@ -213,7 +219,11 @@ def _apply(name, x, psf, y, stream, bc="ar"):
     if y.shape != x.shape:
         raise ValueError("y must have the shape of x")
     n1, n2 = x.shape
-    if bc == "ar":
+    if stencil != "fp32":
+        name += "_ex"
+        _check(getattr(lib(), name)(x.data_ptr(), y.data_ptr(), n1, n2, psf.data_ptr(), q1, q2,
+                                    BC[bc], STENCIL[stencil], _stream(stream)), name)
+    elif bc == "ar":
         _check(getattr(lib(), name)(x.data_ptr(), y.data_ptr(), n1, n2, psf.data_ptr(), q1, q2,
                                     _stream(stream)), name)
     else:
@@ -301,8 +311,9 @@ def ar_symprec_shape(P: Prec) -> tuple[int, int]:
 def ar_restore(g: torch.Tensor, psf, alpha: float, tau: float = 1.0, iters: int = 20,
                precondition: bool = True, x0: torch.Tensor | None = None,
                f_true: torch.Tensor | None = None, x_out: torch.Tensor | None = None,
-               trace: bool = True, stream=None, precision: str = "fp32", bc: str = "ar"):
-    """(D-)Landweber restoration under ``bc``.
+               trace: bool = True, stream=None, precision: str = "fp32", bc: str = "ar",
+               stencil: str = "fp32"):
+    """(D-)Landweber restoration under ``bc``; ``stencil`` as ``ar_blur_apply``.
 
     Returns ``(x, rre_trace or None, best_iter or None)``."""
     _image(g, "g")
@@ -317,7 +328,7 @@ def ar_restore(g: torch.Tensor, psf, alpha: float, tau: float = 1.0, iters: int 
     best = _i(0)
     _check(lib().ar_restore_bc(
         g.data_ptr(), h.ctypes.data, n1, n2, q1, q2, float(alpha), float(tau), int(iters),
-        BC[bc], 1 if precondition else 0, PRECISION[precision],
+        BC[bc], 1 if precondition else 0, PRECISION[precision] | STENCIL[stencil],
         _image(x0, "x0").data_ptr() if x0 is not None else None,
         _image(f_true, "f_true").data_ptr() if f_true is not None else None,
         x_out.data_ptr(),
@@ -330,7 +341,8 @@ def ar_restore(g: torch.Tensor, psf, alpha: float, tau: float = 1.0, iters: int 
 def ar_restore_residuals(g: torch.Tensor, psf, alpha: float, tau: float = 1.0, iters: int = 20,
                          precondition: bool = True, x0: torch.Tensor | None = None,
                          f_true: torch.Tensor | None = None, x_out: torch.Tensor | None = None,
-                         stream=None, precision: str = "fp32", bc: str = "ar"):
+                         stream=None, precision: str = "fp32", bc: str = "ar",
+                         stencil: str = "fp32"):
     """``ar_restore`` that also returns the residual norms ``||g - A x_k||_F`` of the
     iterates, k = 0 .. iters.
 
@@ -348,7 +360,7 @@ def ar_restore_residuals(g: torch.Tensor, psf, alpha: float, tau: float = 1.0, i
     best = _i(0)
     _check(lib().ar_restore_residuals(
         g.data_ptr(), h.ctypes.data, n1, n2, q1, q2, float(alpha), float(tau), int(iters),
-        BC[bc], 1 if precondition else 0, PRECISION[precision],
+        BC[bc], 1 if precondition else 0, PRECISION[precision] | STENCIL[stencil],
         _image(x0, "x0").data_ptr() if x0 is not None else None,
         _image(f_true, "f_true").data_ptr() if f_true is not None else None,
         x_out.data_ptr(),

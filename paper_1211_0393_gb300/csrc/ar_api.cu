@@ -146,8 +146,10 @@ ar_status check_bc(int bc) {
 }
 
 ar_status apply_common(const float* x, float* y, int n1, int n2, const float* psf, int q1, int q2,
-                       int bc, void* stream, int flip) {
+                       int bc, void* stream, int flip, int stencil = AR_STENCIL_FP32) {
     if (!x || !y || !psf) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
+    if (stencil != AR_STENCIL_FP32 && stencil != AR_STENCIL_F16X2)
+        return fail(AR_ERR_INVALID_ARG, "unknown stencil arithmetic %d", stencil);
     AR_TRY(check_bc(bc));
     AR_TRY(check_image_sizes(n1, n2, 1));
     AR_TRY(check_support(n1, n2, q1, q2, 1));
@@ -166,7 +168,16 @@ ar_status apply_common(const float* x, float* y, int n1, int n2, const float* ps
     a.flip = flip;
     a.mode = CONV_STORE;
     a.bc = bc;
-    return conv_launch(a, static_cast<cudaStream_t>(stream));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (stencil == AR_STENCIL_F16X2 && conv_tc_applies(a)) {
+        Scratch ws(s);
+        uint8_t* plan = nullptr;
+        AR_TRY(ws.get(&plan, kConvTcPlanBytes));
+        AR_TRY(conv_tc_plan(psf, q1, q2, flip, plan, s));
+        a.tcplan = plan;
+        return conv_launch(a, s);    // the plan is freed in stream order after the stencil
+    }
+    return conv_launch(a, s);
 }
 
 // Builds the preconditioner's device data on `s` without synchronizing.
@@ -266,6 +277,8 @@ static ar_status restore_run(const float* g, const double* psf_host, int n1, int
                              double* res_trace = nullptr) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     set_pool_threshold_once();
+    const bool tc_stencil = (precision & AR_STENCIL_F16X2) != 0;
+    precision &= ~AR_STENCIL_F16X2;
     const size_t n = (size_t)n1 * n2;
     const size_t nb = n * sizeof(float);
     const size_t k = (size_t)(2 * q1 + 1) * (2 * q2 + 1);
@@ -352,6 +365,17 @@ static ar_status restore_run(const float* g, const double* psf_host, int n1, int
         reblur.early_trigger = reblur.mode == CONV_SPLIT3 || reblur.mode == CONV_STORE ? 1 : 0;
         blur.spread = reblur.spread = 1;
         reblur.f = f_true;
+        if (st == AR_OK && tc_stencil && conv_tc_applies(blur)) {
+            // the PSF's tensor-core plans for A and A' (the reblur's input r is
+            // aligned like x_out when x_out is; conv_launch checks each call)
+            uint8_t *pa = nullptr, *pr = nullptr;
+            st = ws.get(&pa, kConvTcPlanBytes);
+            if (st == AR_OK) st = ws.get(&pr, kConvTcPlanBytes);
+            if (st == AR_OK) st = conv_tc_plan(psf, q1, q2, 0, pa, s);
+            if (st == AR_OK) st = conv_tc_plan(psf, q1, q2, 1, pr, s);
+            blur.tcplan = pa;
+            reblur.tcplan = pr;
+        }
         for (int it = 0; st == AR_OK && it < iters; ++it) {
             // the RRE numerator ||x_{k+1} - f||^2 is accumulated by the kernel that writes x_{k+1}
             blur.sumsq = dres ? dres + it : nullptr;             // ||r||^2 when requested
@@ -515,6 +539,7 @@ static ar_status validate_restore_args(const float* g, const double* psf_host, i
     if (!g || !psf_host || !x_out) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
     AR_TRY(check_bc(bc));
     const bool pc = precondition != 0;
+    precision &= ~AR_STENCIL_F16X2;       // the stencil flag combines with every precision
     if (pc) AR_TRY(check_precision(precision, bc, n1, n2));
     else if (precision < AR_PRECISION_FP32 || precision > AR_PRECISION_AUTO)
         return fail(AR_ERR_INVALID_ARG, "unknown precision %d", precision);
@@ -587,6 +612,16 @@ ar_status ar_blur_apply_bc(const float* x, float* y, int n1, int n2, const float
 ar_status ar_reblur_apply_bc(const float* x, float* y, int n1, int n2, const float* psf, int q1,
                              int q2, int bc, void* stream) {
     return apply_common(x, y, n1, n2, psf, q1, q2, bc, stream, 1);
+}
+
+ar_status ar_blur_apply_ex(const float* x, float* y, int n1, int n2, const float* psf, int q1,
+                           int q2, int bc, int stencil, void* stream) {
+    return apply_common(x, y, n1, n2, psf, q1, q2, bc, stream, 0, stencil);
+}
+
+ar_status ar_reblur_apply_ex(const float* x, float* y, int n1, int n2, const float* psf, int q1,
+                             int q2, int bc, int stencil, void* stream) {
+    return apply_common(x, y, n1, n2, psf, q1, q2, bc, stream, 1, stencil);
 }
 
 ar_status ar_symprec_setup(const double* psf_host, int q1, int q2, int n1, int n2, double alpha,

@@ -27,6 +27,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <cstdint>
@@ -598,6 +599,624 @@ conv_tma_fold_kernel(const __grid_constant__ CUtensorMap tmx, const ConvArgs a, 
     }
 }
 
+// ------------------------------------------------ tensor-core stencils ---
+// The same convolution as banded-Toeplitz products on the tensor cores
+// (tcgen05, kind::f16), for supports q1, q2 <= 8 under AR and Reflective BCs.
+// An output tile is TCM = 128 rows (the MMA's M: one TMEM lane per row) by
+// TCW = 64 columns.  Its halo box (rows r0 - 8 .. r0 + 135, columns c0 - 8 ..
+// c0 + 71) arrives by TMA as float32, receives the boundary fix-up, is scaled
+// by a power of two 2^ex that brings its largest magnitude into [2^14, 2^15),
+// and is split into two fp16 planes, x 2^ex = x_hi + x_lo, x_lo the fp16
+// rounding of the remainder.  A plane is K-major without swizzling: for each
+// group of 8 box columns the box rows follow each other at 16-byte stride, so
+// the operand "box rows u .. u + 127" is the plane's start address plus 16 u
+// bytes: the input rows of PSF row s1 = 8 - u for every output row at once.
+// The PSF, scaled by 2^eh the same way, is split into fp16 parts Th + Tl and
+// laid out per PSF row as Toeplitz bands (conv_tc_plan_kernel).  Output chunk
+// c (16 columns) reads box columns [16c, 16c + 32): the first half from the
+// 16-column slice c of the box (band B0), the second from slice c + 1 (B1).
+// Per PSF row and slice s two MMAs (K = 16, N = 64) accumulate into chunks s-1
+// and s at once: x_hi against [Th B1 | Tl B1 | Th B0 | Tl B0] and x_lo against
+// [0 | Th B1 | 0 | Th B0]; every chunk keeps P = sum x_hi Th and R = sum
+// (x_hi Tl + x_lo Th) in TMEM, and y = (P + R) 2^-ex 2^-eh.  The split
+// represents x and h to 2^-22 relative (11 + 11 bits); the dropped product
+// x_lo Tl is below 2^-22 of each term; products are exact and accumulate in
+// float32.  Elements far below the tile's largest (2^-28 of it) fall into
+// fp16's subnormal range, an absolute error below 2^-39 of that largest.
+constexpr int TCM = 128, TCW = 64, TCQ = 8;
+constexpr int TCHB = TCM + 2 * TCQ;            // 144 box rows
+constexpr int TCWB = TCW + 2 * TCQ;            // 80 box columns
+constexpr int TCNG = TCWB / 8;                 // 10 groups of 8 columns
+constexpr int TCNR = TCHB + 1;                 // plane rows per group (one spare: spreads
+                                               // the split's 16-byte stores over the banks)
+constexpr int TCU = 2 * TCQ + 1;               // PSF rows of the plan
+constexpr int TCTHREADS = 256;
+constexpr uint32_t TC_BOX_BYTES = (uint32_t)TCWB * TCHB * 4;
+constexpr uint32_t TC_PLANE_BYTES = (uint32_t)TCNG * TCNR * 16;
+constexpr uint32_t TC_BTILE = 64 * 16 * 2;    // N = 64 rows x K = 16 fp16
+constexpr uint32_t TC_PLAN_HEAD = 16;          // int eh, padding
+constexpr uint32_t TC_TMEM_COLS = 256;         // two accumulator sets of 4 chunks x 32
+using GTC = Geo<8, 16>;                        // 128-row tiles for fixup_tile
+
+// Shared-memory layout of the tile kernel (fold = 1: one plane set and a
+// receive buffer for the partner's results instead of the second set).
+template <int FOLD>
+struct TcSmem {
+    static constexpr uint32_t BOX = 0;
+    static constexpr uint32_t PLANES = TC_BOX_BYTES;
+    static constexpr uint32_t RECV = PLANES + 2 * TC_PLANE_BYTES;           // fold only
+    static constexpr uint32_t BT =
+        FOLD ? RECV + (uint32_t)TCM * (TCW + 1) * 4 : PLANES + 4 * TC_PLANE_BYTES;
+    static constexpr uint32_t BARS = BT + (uint32_t)TCU * 2 * TC_BTILE;
+    static constexpr uint32_t TOTAL = BARS + 128;
+    static constexpr size_t SMEM = TOTAL + 1024;                            // alignment slack
+    static_assert(BT % 16 == 0 && BARS % 8 == 0, "aligned regions");
+};
+
+// 2^e for e in [-126, 127] (exact).
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+
+// Exponent that brings magnitude bits mb (|v| as uint32) into [2^14, 2^15):
+// 0 for zero or non-finite maxima, clamped so that 2^e and 2^-e are normal.
+__device__ __forceinline__ int tc_scale_exp(uint32_t mb) {
+    if (mb == 0u || mb >= 0x7F800000u) return 0;
+    int e;
+    frexpf(__uint_as_float(mb), &e);                     // max = f 2^e, f in [0.5, 1)
+    const int ex = 15 - e;
+    return ex < -126 ? -126 : (ex > 126 ? 126 : ex);
+}
+
+// The plan of one PSF for the tensor-core stencils: int eh at byte 0, then for
+// each PSF row u = 0 .. 16 (s1 = 8 - u) the B tiles of the hi and lo planes,
+// N = 64 rows of K = 16 fp16, K-major without swizzle ([k / 8][n][k % 8]):
+//   rows  0..15: Th B1,  16..31: Tl B1 (hi) / Th B1 (lo),
+//   rows 32..47: Th B0,  48..63: Tl B0 (hi) / Th B0 (lo),
+// the lo tile's rows 0..15 and 32..47 zero.  Row n of band Bb holds, for output
+// column j = n % 16 of a chunk and k = 0..15, the tap h(s1, s2) with
+// s2 = j + 8 - (16 b + k) (0 outside the support); A' (flip) takes h(-s1, -s2).
+__global__ void __launch_bounds__(TCTHREADS)
+conv_tc_plan_kernel(const float* __restrict__ psf, int q1, int q2, int flip, uint8_t* plan) {
+    __shared__ uint32_t red[TCTHREADS / 32];
+    const int tid = threadIdx.x;
+    const int kw = 2 * q2 + 1, count = (2 * q1 + 1) * kw;
+    uint32_t mb = 0;
+    for (int i = tid; i < count; i += TCTHREADS) mb = max(mb, __float_as_uint(fabsf(psf[i])));
+    mb = __reduce_max_sync(0xffffffffu, mb);
+    if ((tid & 31) == 0) red[tid >> 5] = mb;
+    __syncthreads();
+    mb = 0;
+    for (int w = 0; w < TCTHREADS / 32; ++w) mb = max(mb, red[w]);
+    const int eh = tc_scale_exp(mb);
+    const float sc = pow2f(eh);
+    if (tid == 0) *reinterpret_cast<int*>(plan) = eh;
+    uint16_t* tiles = reinterpret_cast<uint16_t*>(plan + TC_PLAN_HEAD);
+    constexpr int PER_U = 2 * 64 * 16;
+    for (int i = tid; i < TCU * PER_U; i += TCTHREADS) {
+        const int u = i / PER_U, rem = i % PER_U;
+        const int p = rem / (64 * 16), n = (rem / 16) % 64, k = rem % 16;
+        const int band = n < 32 ? 1 : 0, part = (n / 16) & 1, j = n % 16;
+        const int s1 = TCQ - u, s2 = j + TCQ - (16 * band + k);
+        float hv = 0.f;
+        if (s1 >= -q1 && s1 <= q1 && s2 >= -q2 && s2 <= q2) {
+            const int t1 = flip ? -s1 : s1, t2 = flip ? -s2 : s2;
+            hv = psf[(t1 + q1) * kw + (t2 + q2)];
+        }
+        const float hs = hv * sc;
+        const __half th = __float2half_rn(hs);
+        const __half tl = __float2half_rn(hs - __half2float(th));
+        const __half v = p == 0 ? (part == 0 ? th : tl) : (part == 0 ? __float2half_rn(0.f) : th);
+        tiles[(size_t)(u * 2 + p) * (TC_BTILE / 2) + (k / 8) * 64 * 8 + n * 8 + k % 8] =
+            __half_as_ushort(v);
+    }
+}
+
+// Box of tile i: fix-up, scale and split into the plane pair at `hi` (lo one
+// plane further).  Returns the scale exponent; called by every thread.
+__device__ __forceinline__ int tc_split_box(const ConvArgs& a, float* box, uint8_t* hi, int r0,
+                                            int c0, uint32_t* red) {
+    const int tid = threadIdx.x;
+    if (r0 - TCQ < 0 || r0 + TCM + TCQ > a.n1 || c0 - TCQ < 0 || c0 + TCW + TCQ > a.n2)
+        fixup_tile<TCQ, GTC>(a, box, TCWB, r0, c0, tid, TCTHREADS);
+    const float4* b4 = reinterpret_cast<const float4*>(box);
+    uint32_t mb = 0;
+    for (int it = tid; it < TCHB * TCNG; it += TCTHREADS) {
+        const int row = it / TCNG, g = it % TCNG;
+        const float4 v0 = b4[row * (TCWB / 4) + 2 * g], v1 = b4[row * (TCWB / 4) + 2 * g + 1];
+        mb = max(mb, max(max(__float_as_uint(fabsf(v0.x)), __float_as_uint(fabsf(v0.y))),
+                         max(__float_as_uint(fabsf(v0.z)), __float_as_uint(fabsf(v0.w)))));
+        mb = max(mb, max(max(__float_as_uint(fabsf(v1.x)), __float_as_uint(fabsf(v1.y))),
+                         max(__float_as_uint(fabsf(v1.z)), __float_as_uint(fabsf(v1.w)))));
+    }
+    mb = __reduce_max_sync(0xffffffffu, mb);
+    if ((tid & 31) == 0) red[tid >> 5] = mb;
+    __syncthreads();
+    mb = 0;
+#pragma unroll
+    for (int w = 0; w < TCTHREADS / 32; ++w) mb = max(mb, red[w]);
+    const int ex = tc_scale_exp(mb);
+    const float sc = pow2f(ex);
+    uint8_t* lo = hi + TC_PLANE_BYTES;
+    for (int it = tid; it < TCHB * TCNG; it += TCTHREADS) {
+        const int row = it / TCNG, g = it % TCNG;
+        const float4 v0 = b4[row * (TCWB / 4) + 2 * g], v1 = b4[row * (TCWB / 4) + 2 * g + 1];
+        const float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float s0 = v[2 * e] * sc, s1 = v[2 * e + 1] * sc;
+            const __half h0 = __float2half_rn(s0), h1 = __float2half_rn(s1);
+            const __half l0 = __float2half_rn(s0 - __half2float(h0));
+            const __half l1 = __float2half_rn(s1 - __half2float(h1));
+            h[e] = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
+            l[e] = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
+        }
+        const size_t off = ((size_t)g * TCNR + row) * 16;
+        *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+    tc::fence_proxy_async_smem();        // the planes are read by the tensor cores
+    return ex;
+}
+
+// The MMAs of one tile (one thread): planes at `hi` (lo one plane further),
+// accumulators at TMEM column d, PSF rows u0 .. u1 of the B tiles at `bt`.
+__device__ __forceinline__ void tc_issue(uint32_t hi, uint32_t bt, uint32_t d, int u0, int u1) {
+    using namespace tc;
+    constexpr uint32_t LBO = TCNR * 16;
+    const uint64_t ah0 = desc_k_none(hi, LBO, 128), al0 = desc_k_none(hi + TC_PLANE_BYTES, LBO, 128);
+    const uint64_t b0 = desc_k_none(bt, 64 * 16, 128);
+    constexpr uint32_t id32 = idesc_f16_f32(TCM, 32), id64 = idesc_f16_f32(TCM, 64);
+    constexpr uint64_t HALF0 = (32 * 16) >> 4;           // B rows 32..63: band B0
+    constexpr int NS = TCW / 16;                          // chunks; slices 0 .. NS
+    for (int u = u0; u <= u1; ++u) {
+        const uint64_t bh = b0 + (uint64_t)((u * 2) * TC_BTILE >> 4);
+        const uint64_t bl = bh + (uint64_t)(TC_BTILE >> 4);
+        const bool first = u == u0;
+#pragma unroll
+        for (int s = 0; s <= NS; ++s) {
+            const uint64_t ao = (uint64_t)(((2 * s) * LBO + u * 16) >> 4);
+            if (s == 0) {
+                mma_bf16(d, ah0 + ao, bh + HALF0, id32, first ? 0u : 1u);
+                mma_bf16(d, al0 + ao, bl + HALF0, id32, 1u);
+            } else if (s == NS) {
+                mma_bf16(d + 32 * (NS - 1), ah0 + ao, bh, id32, 1u);
+                mma_bf16(d + 32 * (NS - 1), al0 + ao, bl, id32, 1u);
+            } else {
+                if (first) {         // chunk s starts here: initialise it alone
+                    mma_bf16(d + 32 * s, ah0 + ao, bh + HALF0, id32, 0u);
+                    mma_bf16(d + 32 * (s - 1), ah0 + ao, bh, id32, 1u);
+                } else {
+                    mma_bf16(d + 32 * (s - 1), ah0 + ao, bh, id64, 1u);
+                }
+                mma_bf16(d + 32 * (s - 1), al0 + ao, bl, id64, 1u);
+            }
+        }
+    }
+}
+
+// bf16x3 split of 16 consecutive values into the three planes at element
+// offset off (16-byte aligned rows: 8-element vector stores).
+__device__ __forceinline__ void split3_store16(uint16_t* planes, size_t pstride, size_t off,
+                                               const float (&y)[16], int nvalid) {
+    if (nvalid < 16) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (j < nvalid) split3_store(planes, pstride, off + j, y[j]);
+        return;
+    }
+    uint32_t w[3][8];
+#pragma unroll
+    for (int j = 0; j < 16; j += 2) {
+        uint32_t lo3[3], hi3[3];
+        float v0 = y[j], v1 = y[j + 1];
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            const __nv_bfloat16 b0 = __float2bfloat16_rn(v0), b1 = __float2bfloat16_rn(v1);
+            lo3[p] = __bfloat16_as_ushort(b0);
+            hi3[p] = __bfloat16_as_ushort(b1);
+            v0 -= __bfloat162float(b0);
+            v1 -= __bfloat162float(b1);
+        }
+#pragma unroll
+        for (int p = 0; p < 3; ++p) w[p][j / 2] = lo3[p] | (hi3[p] << 16);
+    }
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        uint4* dst = reinterpret_cast<uint4*>(planes + p * pstride + off);
+        dst[0] = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+        dst[1] = make_uint4(w[p][4], w[p][5], w[p][6], w[p][7]);
+    }
+}
+
+// Epilogue of 16 outputs y[0..15] of row `row` at columns col .. col + 15
+// (n2 % 4 == 0, col % 16 == 0); returns the squares the mode sums.
+__device__ __forceinline__ float tc_store16(const ConvArgs& a, int row, int col, const float (&y)[16],
+                                            bool vec3) {
+    const int nv = min(16, a.n2 - col);
+    if (nv <= 0) return 0.f;
+    const size_t o = (size_t)row * a.n2 + col;
+    float sq = 0.f;
+    if (a.mode == CONV_SPLIT3) {
+        if (vec3) {
+            split3_store16(a.planes, a.plane_stride, (size_t)row * a.ld + col, y, nv);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (j < nv) split3_store(a.planes, a.plane_stride, (size_t)row * a.ld + col + j, y[j]);
+        }
+        return 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (4 * q >= nv) break;
+        float4* p4 = reinterpret_cast<float4*>(a.out + o) + q;
+        const float4 yv = make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
+        if (a.mode == CONV_STORE) {
+            *p4 = yv;
+        } else if (a.mode == CONV_RESIDUAL) {
+            const float4 g = __ldg(reinterpret_cast<const float4*>(a.aux + o) + q);
+            const float4 r = make_float4(g.x - yv.x, g.y - yv.y, g.z - yv.z, g.w - yv.w);
+            *p4 = r;
+            if (a.sumsq) sq += r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
+        } else {                                           // CONV_AXPY
+            const float4 xo = *p4;
+            const float4 xn = make_float4(fmaf(a.tau, yv.x, xo.x), fmaf(a.tau, yv.y, xo.y),
+                                          fmaf(a.tau, yv.z, xo.z), fmaf(a.tau, yv.w, xo.w));
+            *p4 = xn;
+            if (a.f) {
+                const float4 f = __ldg(reinterpret_cast<const float4*>(a.f + o) + q);
+                const float e0 = xn.x - f.x, e1 = xn.y - f.y, e2 = xn.z - f.z, e3 = xn.w - f.w;
+                sq += e0 * e0 + e1 * e1 + e2 * e2 + e3 * e3;
+            }
+        }
+    }
+    return sq;
+}
+
+// The results of this thread's chunk c of the tile in D (TMEM, lane base
+// included): y = (P + R) scale.
+__device__ __forceinline__ void tc_load_chunk(uint32_t d, int c, float scale, float (&y)[16]) {
+    float P[16], R[16];
+    tc::tmem_ld16x2(d + 32 * c, d + 32 * c + 16, P, R);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) y[j] = (P[j] + R[j]) * scale;
+}
+
+// Persistent tensor-core stencil (every mode but the folded one).  Each CTA
+// walks the tiles t = blockIdx.x + i gridDim.x.  While the tensor cores run
+// tile i, the threads fix up and split the box of tile i + 1 into the other
+// plane set and the TMA brings the box of tile i + 2; then they read tile i's
+// accumulators and apply the epilogue.
+__global__ void __launch_bounds__(TCTHREADS, 1)
+conv_tc_kernel(const __grid_constant__ CUtensorMap tmx, const ConvArgs a, const uint8_t* plan,
+               int ntx, int ntiles, int vec3) {
+    using namespace tc;
+    using L = TcSmem<0>;
+    extern __shared__ __align__(1024) uint8_t smem_tc[];
+    uint8_t* sb = smem_tc + ((1024u - (smem_u32(smem_tc) & 1023u)) & 1023u);
+    const uint32_t sbase = smem_u32(sb);
+    float* box = reinterpret_cast<float*>(sb + L::BOX);
+    const uint32_t box_bar = sbase + L::BARS, b_bar = box_bar + 8, mma_bar = box_bar + 16;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sb + L::BARS + 32);
+    int* sex = reinterpret_cast<int*>(sb + L::BARS + 40);
+    uint32_t* red = reinterpret_cast<uint32_t*>(sb + L::BARS + 48);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int u0 = TCQ - a.q1, u1 = TCQ + a.q1;
+    const int nmine = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+    if (tid == 0) {
+        mbar_init(box_bar, 1);
+        mbar_init(b_bar, 1);
+        mbar_init(mma_bar, 1);
+        mbar_init(mma_bar + 8, 1);
+        fence_mbar_init();
+        prefetch_tmap(&tmx);
+    }
+    if (warp == 0) {
+        tmem_alloc(smem_u32(tslot), TC_TMEM_COLS);
+        tmem_relinquish();
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tslot;
+    if (tid == 0 && nmine > 0) {         // the plan does not depend on the previous kernel
+        const uint32_t bytes = (uint32_t)(u1 - u0 + 1) * 2 * TC_BTILE;
+        mbar_arrive_expect_tx(b_bar, bytes);
+        bulk_load(sbase + L::BT + (uint32_t)u0 * 2 * TC_BTILE,
+                  plan + TC_PLAN_HEAD + (size_t)u0 * 2 * TC_BTILE, bytes, b_bar);
+    }
+    const float seh = pow2f(-__ldg(reinterpret_cast<const int*>(plan)));
+    pdl_wait();                          // the input image comes from the previous kernel
+
+    auto tile_origin = [&](int i, int* r0, int* c0) {
+        const int t = blockIdx.x + i * gridDim.x;
+        *r0 = (t / ntx) * TCM;
+        *c0 = (t % ntx) * TCW;
+    };
+    auto request = [&](int i) {          // thread 0
+        int r0, c0;
+        tile_origin(i, &r0, &c0);
+        fence_proxy_async_smem();        // the fix-up's generic writes before the async copy
+        mbar_arrive_expect_tx(box_bar, TC_BOX_BYTES);
+        tma_load_2d(sbase + L::BOX, &tmx, c0 - TCQ, r0 - TCQ, box_bar);
+    };
+    const uint32_t polls = g_conv_wait_polls;
+    auto plane_set = [&](int i) { return sb + L::PLANES + (uint32_t)(i & 1) * 2 * TC_PLANE_BYTES; };
+    // box i -> plane set i & 1; false (on every thread) when a wait gave up
+    auto stage = [&](int i) -> bool {
+        bool ok = mbar_wait(box_bar, (uint32_t)(i & 1), polls);
+        if (i == 0) ok = ok && mbar_wait(b_bar, 0, polls);
+        if (__syncthreads_or(!ok)) return false;
+        int r0, c0;
+        tile_origin(i, &r0, &c0);
+        const int ex = tc_split_box(a, box, plane_set(i), r0, c0, red);
+        if (tid == 0) sex[i & 1] = ex;
+        return true;
+    };
+
+    bool failed = false;
+    int issued = 0, requested = 0, staged = 0, li = 0;
+    if (nmine > 0) {
+        if (tid == 0) request(0);
+        requested = 1;
+        if (!stage(0)) {
+            failed = true;
+        } else {
+            staged = 1;
+            fence_before_sync();
+            __syncthreads();             // box consumed, planes written
+            if (tid == 0) {
+                if (nmine > 1) request(1);
+                fence_after_sync();
+                tc_issue(smem_u32(plane_set(0)), sbase + L::BT, tmem, u0, u1);
+                mma_commit(mma_bar);
+            }
+            requested = nmine > 1 ? 2 : 1;
+            issued = 1;
+        }
+    }
+    for (; !failed && li < nmine; ++li) {
+        if (li + 1 < nmine) {
+            if (!stage(li + 1)) {
+                failed = true;
+                break;
+            }
+            staged = li + 2;
+            fence_before_sync();
+            __syncthreads();
+            if (tid == 0) {
+                if (li + 2 < nmine) request(li + 2);
+                fence_after_sync();
+                tc_issue(smem_u32(plane_set(li + 1)), sbase + L::BT,
+                         tmem + (uint32_t)((li + 1) & 1) * 128, u0, u1);
+                mma_commit(mma_bar + 8u * ((li + 1) & 1));
+            }
+            if (li + 2 < nmine) requested = li + 3;
+            issued = li + 2;
+        }
+        const bool ok = mbar_wait(mma_bar + 8u * (li & 1), (uint32_t)((li >> 1) & 1), polls);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        fence_after_sync();
+        if (a.early_trigger && li == nmine - 1) pdl_trigger();
+        int r0, c0;
+        tile_origin(li, &r0, &c0);
+        const int quarter = warp & 3, hw = warp >> 2;
+        const int m = quarter * 32 + lane, row = r0 + m;
+        const float scale = pow2f(-sex[li & 1]) * seh;
+        const uint32_t d = tmem + (uint32_t)(li & 1) * 128 + ((uint32_t)(quarter * 32) << 16);
+        float sq = 0.f;
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            const int c = 2 * hw + cc;
+            float y[16];
+            tc_load_chunk(d, c, scale, y);
+            if (row < a.n1) sq += tc_store16(a, row, c0 + 16 * c, y, vec3 != 0);
+        }
+        if (a.sumsq) add_sumsq(a.sumsq, sq);
+        fence_before_sync();
+    }
+    if (!a.early_trigger) pdl_trigger();
+    if (failed && tid == 0) {
+        atomicExch(&g_conv_timeout, 1);
+        // copies and MMAs possibly still in flight: wait for them (bounded)
+        // before the shared memory and the TMEM are released
+        for (int i = staged; i < requested; ++i) mbar_wait(box_bar, (uint32_t)(i & 1));
+        for (int i = li; i < issued; ++i) mbar_wait(mma_bar + 8u * (i & 1), (uint32_t)((i >> 1) & 1));
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after_sync();
+        tmem_dealloc(tmem, TC_TMEM_COLS);
+    }
+}
+
+// Folding variant (CONV_SPLIT3 with fold): a cluster of two CTAs per work
+// unit, rank 0 on the tile at columns [c0, c0 + 64) and rank 1 on its mirror
+// [n2 - c0 - 64, n2 - c0).  Column t = c0 + j pairs with n2 - 1 - t, column
+// 63 - j of the mirror tile.  Each rank sends its results to the other's
+// receive buffer (distributed shared memory); rank 0 writes the bf16x3 split
+// of y+_t = y_t + y_{n2-1-t} at column t (zero from ceil(n2/2) on), rank 1 that
+// of y-_t = y_t - y_{n2-1-t} at column Kh + t (zero from floor(n2/2) on).  One
+// plane set: the split of the next unit waits for the current unit's MMAs.  A
+// wait that gives up on either rank is exchanged with the peer, and both ranks
+// leave the loop after the same cluster barrier.
+constexpr int TC_RECV_PITCH = TCW + 1;          // conflict-free column reads of the buffer
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(TCTHREADS, 1)
+conv_tc_fold_kernel(const __grid_constant__ CUtensorMap tmx, const ConvArgs a, const uint8_t* plan,
+                    int ncp, int nunits, int vec3) {
+    using namespace tc;
+    using L = TcSmem<1>;
+    extern __shared__ __align__(1024) uint8_t smem_tc[];
+    uint8_t* sb = smem_tc + ((1024u - (smem_u32(smem_tc) & 1023u)) & 1023u);
+    const uint32_t sbase = smem_u32(sb);
+    float* box = reinterpret_cast<float*>(sb + L::BOX);
+    const float* recv = reinterpret_cast<const float*>(sb + L::RECV);
+    const uint32_t box_bar = sbase + L::BARS, b_bar = box_bar + 8, mma_bar = box_bar + 16;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sb + L::BARS + 32);
+    int* sex = reinterpret_cast<int*>(sb + L::BARS + 40);
+    uint32_t* red = reinterpret_cast<uint32_t*>(sb + L::BARS + 48);
+    int* pbad_flag = reinterpret_cast<int*>(sb + L::BARS + 84);   // written by the peer
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t rank = cluster_ctarank(), peer = rank ^ 1u;
+    const int u0 = TCQ - a.q1, u1 = TCQ + a.q1;
+    const int h = (a.n2 + 1) / 2, ha = a.n2 / 2, kh = (h + 63) / 64 * 64;
+    const int cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+    const int nmine = cid < nunits ? (nunits - 1 - cid) / ncl + 1 : 0;   // the same on both ranks
+
+    if (tid == 0) {
+        mbar_init(box_bar, 1);
+        mbar_init(b_bar, 1);
+        mbar_init(mma_bar, 1);
+        fence_mbar_init();
+        prefetch_tmap(&tmx);
+    }
+    if (warp == 0) {
+        tmem_alloc(smem_u32(tslot), TC_TMEM_COLS);
+        tmem_relinquish();
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tslot;
+    if (tid == 0 && nmine > 0) {
+        const uint32_t bytes = (uint32_t)(u1 - u0 + 1) * 2 * TC_BTILE;
+        mbar_arrive_expect_tx(b_bar, bytes);
+        bulk_load(sbase + L::BT + (uint32_t)u0 * 2 * TC_BTILE,
+                  plan + TC_PLAN_HEAD + (size_t)u0 * 2 * TC_BTILE, bytes, b_bar);
+    }
+    const float seh = pow2f(-__ldg(reinterpret_cast<const int*>(plan)));
+    pdl_wait();
+
+    auto unit_origin = [&](int i, int* r0, int* c0) {
+        const int un = cid + i * ncl;
+        *r0 = (un / ncp) * TCM;
+        *c0 = (un % ncp) * TCW;                         // rank 0's tile; the mirror is n2 - c0 - 64
+    };
+    auto request = [&](int i) {
+        int r0, c0;
+        unit_origin(i, &r0, &c0);
+        const int cg = rank == 0 ? c0 : a.n2 - c0 - TCW;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(box_bar, TC_BOX_BYTES);
+        tma_load_2d(sbase + L::BOX, &tmx, cg - TCQ, r0 - TCQ, box_bar);
+    };
+    const uint32_t polls = g_conv_wait_polls;
+    uint8_t* planes = sb + L::PLANES;
+    const uint32_t rpeer = mapa(smem_u32(recv), peer);
+    const uint32_t rflag = mapa(smem_u32(pbad_flag), peer);
+    const int quarter = warp & 3, hw = warp >> 2;
+    const int m = quarter * 32 + lane;
+    bool failed = false;
+    int li = 0, requested = 0, consumed = 0, issued = 0;
+    if (nmine > 0 && tid == 0) request(0);
+    requested = nmine > 0 ? 1 : 0;
+    for (; li < nmine; ++li) {
+        int r0, c0;
+        unit_origin(li, &r0, &c0);
+        const int cg = rank == 0 ? c0 : a.n2 - c0 - TCW;
+        // 1. box -> planes -> MMAs (the previous unit's MMAs have completed)
+        bool ok = mbar_wait(box_bar, (uint32_t)(li & 1), polls);
+        if (li == 0) ok = ok && mbar_wait(b_bar, 0, polls);
+        bool bad = __syncthreads_or(!ok);
+        if (!bad) {
+            const int ex = tc_split_box(a, box, planes, r0, cg, red);
+            consumed = li + 1;
+            if (tid == 0) sex[0] = ex;
+            fence_before_sync();
+            __syncthreads();
+            if (tid == 0) {
+                if (li + 1 < nmine) request(li + 1);
+                fence_after_sync();
+                tc_issue(smem_u32(planes), sbase + L::BT, tmem, u0, u1);
+                mma_commit(mma_bar);
+            }
+            if (li + 1 < nmine) requested = li + 2;
+            issued = li + 1;
+            ok = mbar_wait(mma_bar, (uint32_t)(li & 1), polls);
+            bad = __syncthreads_or(!ok);
+            fence_after_sync();
+        }
+        if (li == nmine - 1) pdl_trigger();
+        // 2. this tile's results -> the peer's receive buffer [row][TC_RECV_PITCH]
+        const float scale = pow2f(-sex[0]) * seh;
+        const uint32_t d = tmem + ((uint32_t)(quarter * 32) << 16);
+        float y[2][16];
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            const int c = 2 * hw + cc;
+            if (!bad) {
+                tc_load_chunk(d, c, scale, y[cc]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) y[cc][j] = 0.f;
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                st_cluster_f32(rpeer + 4u * (m * TC_RECV_PITCH + 16 * c + j), y[cc][j]);
+        }
+        if (tid == 0)
+            asm volatile("st.shared::cluster.b32 [%0], %1;" ::"r"(rflag), "r"(bad ? 1 : 0) : "memory");
+        fence_before_sync();
+        cluster_sync();                  // the peer's results and status have arrived
+        const bool pbad = *reinterpret_cast<volatile int*>(pbad_flag) != 0;
+        // 3. the folded outputs of 16 columns per chunk
+        const int row = r0 + m;
+        if (!bad && !pbad && row < a.n1) {
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+                const int c = 2 * hw + cc;
+                float v[16];
+                int ocol;
+                if (rank == 0) {         // t = c0 + 16 c + j: y(16 c + j) + y_peer(63 - 16 c - j)
+                    const int t0 = c0 + 16 * c;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        v[j] = t0 + j < h ? y[cc][j] + recv[m * TC_RECV_PITCH + (TCW - 1 - 16 * c - j)]
+                                          : 0.f;
+                    ocol = t0;
+                } else {                 // t = c0 + 48 - 16 c + j: y_peer(t - c0) - y(15 + 16 c - j)
+                    const int t0 = c0 + 48 - 16 * c;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        v[j] = t0 + j < ha ? recv[m * TC_RECV_PITCH + (48 - 16 * c + j)] - y[cc][15 - j]
+                                           : 0.f;
+                    ocol = kh + t0;
+                }
+                if (vec3) {
+                    split3_store16(a.planes, a.plane_stride, (size_t)row * a.ld + ocol, v, 16);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        split3_store(a.planes, a.plane_stride, (size_t)row * a.ld + ocol + j, v[j]);
+                }
+            }
+        }
+        fence_before_sync();
+        cluster_sync();                  // both buffers read before the next unit refills them
+        if (bad || pbad) {
+            failed = true;
+            break;
+        }
+    }
+    if (failed && tid == 0) {
+        atomicExch(&g_conv_timeout, 1);
+        for (int i = consumed; i < requested; ++i) mbar_wait(box_bar, (uint32_t)(i & 1));
+        for (int i = li; i < issued; ++i) mbar_wait(mma_bar, (uint32_t)(i & 1));
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after_sync();
+        tmem_dealloc(tmem, TC_TMEM_COLS);
+    }
+}
+
 // Generic path for large supports: one output per thread, taps read straight
 // from the (L2-resident) input through the virtual extension.
 __global__ void __launch_bounds__(256)
@@ -753,6 +1372,60 @@ cudaError_t launch_tiles(const ConvArgs& a, cudaStream_t s) {
     count_launch();
     conv_fast_kernel<Q, RW><<<grid, dim3(TX, G64::TY), 0, s>>>(a);
     return cudaGetLastError();
+}
+
+// ------------------------------------------------ tensor-core stencils (host)
+bool make_tc_map(const ConvArgs& a, CUtensorMap* map) {
+    auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder());
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)a.n2, (cuuint64_t)a.n1};
+    cuuint64_t strides[1] = {(cuuint64_t)a.n2 * 4};
+    cuuint32_t box[2] = {(cuuint32_t)TCWB, (cuuint32_t)TCHB};
+    cuuint32_t es[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(a.x), dims, strides, box,
+               es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+cudaError_t launch_tc(const ConvArgs& a, cudaStream_t s) {
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    static int max_clusters = 0;         // co-resident clusters of the folding kernel
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)TcSmem<0>::SMEM);
+        if (attr == cudaSuccess)
+            attr = cudaFuncSetAttribute(conv_tc_fold_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)TcSmem<1>::SMEM);
+        if (attr == cudaSuccess) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(2 * (sm_count() / 2));
+            cfg.blockDim = dim3(TCTHREADS);
+            cfg.dynamicSmemBytes = TcSmem<1>::SMEM;
+            attr = cudaOccupancyMaxActiveClusters(&max_clusters, conv_tc_fold_kernel, &cfg);
+        }
+        if (max_clusters < 1) max_clusters = 1;
+    });
+    if (attr != cudaSuccess) return attr;
+    CUtensorMap map;
+    if (!make_tc_map(a, &map)) return cudaErrorInvalidValue;
+    const bool vec3 = a.mode == CONV_SPLIT3 && (reinterpret_cast<uintptr_t>(a.planes) & 15) == 0 &&
+                      a.ld % 8 == 0 && a.plane_stride % 8 == 0;
+    const int nty = (a.n1 + TCM - 1) / TCM;
+    count_launch();
+    if (a.fold) {
+        const int h = (a.n2 + 1) / 2;
+        const int ncp = (h + TCW - 1) / TCW, nunits = ncp * nty;
+        const int ncl = nunits < max_clusters ? nunits : max_clusters;
+        return launch_pdl(conv_tc_fold_kernel, dim3(2 * ncl), dim3(TCTHREADS), TcSmem<1>::SMEM, s,
+                          map, a, a.tcplan, ncp, nunits, vec3 ? 1 : 0);
+    }
+    const int ntx = (a.n2 + TCW - 1) / TCW, ntiles = ntx * nty;
+    const int grid = ntiles < sm_count() ? ntiles : sm_count();
+    return launch_pdl(conv_tc_kernel, dim3(grid), dim3(TCTHREADS), TcSmem<0>::SMEM, s, map, a,
+                      a.tcplan, ntx, ntiles, vec3 ? 1 : 0);
 }
 
 // ------------------------------------------------ batched stencils -------
@@ -1192,9 +1865,32 @@ ar_status conv_set_wait_polls(unsigned polls) {
     return AR_OK;
 }
 
+ar_status conv_tc_plan(const float* psf, int q1, int q2, int flip, uint8_t* plan,
+                       cudaStream_t s) {
+    if (q1 > TCQ || q2 > TCQ || q1 < 0 || q2 < 0)
+        return fail(AR_ERR_UNSUPPORTED, "tensor-core stencil plans take q <= %d", TCQ);
+    count_launch();
+    conv_tc_plan_kernel<<<1, TCTHREADS, 0, s>>>(psf, q1, q2, flip, plan);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core stencil plan");
+    return AR_OK;
+}
+
+bool conv_tc_applies(const ConvArgs& a) {
+    // the epilogue moves 16-byte vectors of x, the output and the mode's inputs
+    auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+    return a.q1 <= TCQ && a.q2 <= TCQ && a.bc != AR_BC_PERIODIC && (a.n2 & 3) == 0 && al(a.x) &&
+           al(a.out) && al(a.aux) && al(a.f);
+}
+
 ar_status conv_launch(const ConvArgs& a, cudaStream_t s) {
     if (a.n1 <= 0 || a.n2 <= 0) return AR_OK;
     ProfScope prof(AR_PROF_STENCIL, s);
+    if (a.tcplan && conv_tc_applies(a)) {
+        const cudaError_t e = launch_tc(a, s);
+        if (e != cudaSuccess) return cuda_fail(e, "tensor-core stencil launch");
+        return AR_OK;
+    }
     const int q = a.q1 > a.q2 ? a.q1 : a.q2;
     if (a.fold && q > QMAX_FAST) return fail(AR_ERR_UNSUPPORTED, "folded output needs q <= 15");
     cudaError_t e;

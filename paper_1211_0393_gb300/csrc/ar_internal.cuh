@@ -89,7 +89,22 @@ struct ConvArgs {
                          // as programmatic dependents)
     int spread;          // the launch owns the GPU (the single-image loop): a grid
                          // that fits one wave takes at most two CTAs per SM
+    const uint8_t* tcplan;  // non-null: this PSF's plan for the tensor-core stencil
+                            // (conv_tc_plan), used where that path applies
+                            // (conv_tc_applies); the float32 stencil elsewhere
 };
+
+// Bytes of a tensor-core stencil plan (device memory, 16-byte aligned).
+constexpr size_t kConvTcPlanBytes = 16 + 17 * 2 * 2048;
+
+// Writes the plan of the device PSF (2q1+1) x (2q2+1) for y = A x (flip 0) or
+// y = A' x (flip 1) on `stream`; q1, q2 <= 8.
+ar_status conv_tc_plan(const float* psf, int q1, int q2, int flip, uint8_t* plan,
+                       cudaStream_t stream);
+
+// True when the tensor-core stencil serves these arguments: q1, q2 <= 8, AR or
+// Reflective BC, n2 % 4 == 0 and a 16-byte aligned input image.
+bool conv_tc_applies(const ConvArgs& a);
 
 // Launches the AR stencil on `stream` (validated arguments).
 ar_status conv_launch(const ConvArgs& a, cudaStream_t stream);

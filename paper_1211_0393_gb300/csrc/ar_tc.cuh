@@ -78,6 +78,16 @@ __device__ __forceinline__ void tma_store_3d(const void* tmap, int c0, int c1, i
         : "memory");
 }
 
+// Untiled bulk copy global -> shared of `bytes` (a multiple of 16; both
+// addresses 16-byte aligned), completion counted on `bar`.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
 __device__ __forceinline__ void bulk_commit() {
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
@@ -274,6 +284,28 @@ __device__ __forceinline__ uint64_t desc_k_sw64(uint32_t saddr) {
     d |= (uint64_t)1u << 46;                          // descriptor version
     d |= (uint64_t)4u << 61;                          // 64-byte swizzle
     return d;
+}
+
+// Shared-memory matrix descriptor of a K-major operand without swizzling: core
+// matrices of 8 rows x 16 bytes whose rows are 16 bytes apart, `lbo` bytes
+// between core matrices adjacent along K and `sbo` bytes between 8-row groups
+// along M/N.  With sbo = 128 every row of the operand is 16 bytes after the
+// previous one, so adding 16 u bytes to the start address shifts the operand
+// by u rows (the start address only needs 16-byte alignment).
+__device__ __forceinline__ uint64_t desc_k_none(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);          // start address
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;      // leading (K) byte offset
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;      // stride (M/N) byte offset
+    d |= (uint64_t)1u << 46;                          // descriptor version; no swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D f32, A and B fp16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
+    return (1u << 4)                       // D format f32
+         | ((uint32_t)(N >> 3) << 17)      // N / 8 (A and B format 0: fp16)
+         | ((uint32_t)(M >> 4) << 24);     // M / 16
 }
 
 // Instruction descriptor, kind::f16: D f32, A and B bf16, both K-major.
