@@ -170,6 +170,7 @@ ar_status apply_common(const float* x, float* y, int n1, int n2, const float* ps
     a.bc = bc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (stencil == AR_STENCIL_F16X2 && conv_tc_applies(a)) {
+        set_pool_threshold_once();       // the plan's stream-ordered allocation stays pooled
         Scratch ws(s);
         uint8_t* plan = nullptr;
         AR_TRY(ws.get(&plan, kConvTcPlanBytes));

@@ -187,7 +187,15 @@ __device__ __forceinline__ void load_coefs(const ConvArgs& a, float* coef, int t
 // x_{-1-i} = x_i, x_{n+i} = x_{n-1-i}.  Edge and mirror samples lie in the
 // tile.  Only the out-of-image strips (at most q rows or columns per side) are
 // visited.
-template <int Q, class G>
+// Block barrier of a stencil: __syncthreads (BAR = 0) or named barrier BAR
+// over `nthreads` threads (the tensor-core kernel's compute warps).
+template <int BAR>
+__device__ __forceinline__ void stencil_sync(int nthreads) {
+    if (BAR == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"n"(BAR), "r"(nthreads) : "memory");
+}
+
+template <int Q, class G, int BAR = 0>
 __device__ void fixup_tile(const ConvArgs& a, float* tile, int WP, int r0, int c0, int tid,
                            int nthreads) {
     constexpr int W = TX + 2 * Q, H = G::TH + 2 * Q;
@@ -209,7 +217,7 @@ __device__ void fixup_tile(const ConvArgs& a, float* tile, int WP, int r0, int c
         const float vm = tile[(rm - rb) * WP + c];
         tile[r * WP + c] = ar ? 2.f * tile[(re - rb) * WP + c] - vm : vm;
     }
-    __syncthreads();
+    stencil_sync<BAR>(nthreads);
     // tile columns with j2 in [-q2, 0) and [n2, n2 + q2), on rows of the extended domain
     const int l0 = max(0, -a.q2 - cb), l1 = min(W, -cb);
     const int g0 = max(0, a.n2 - cb), g1 = min(W, a.n2 + a.q2 - cb);
@@ -225,7 +233,7 @@ __device__ void fixup_tile(const ConvArgs& a, float* tile, int WP, int r0, int c
         const float vm = tile[r * WP + (cm - cb)];
         tile[r * WP + c] = ar ? 2.f * tile[r * WP + (ce - cb)] - vm : vm;
     }
-    __syncthreads();
+    stencil_sync<BAR>(nthreads);
 }
 
 // Each thread computes a vertical strip of RS outputs of one column from the
@@ -648,7 +656,7 @@ struct TcSmem {
     static constexpr uint32_t BT =
         FOLD ? RECV + (uint32_t)TCM * (TCW + 1) * 4 : PLANES + 4 * TC_PLANE_BYTES;
     static constexpr uint32_t BARS = BT + (uint32_t)TCU * 2 * TC_BTILE;
-    static constexpr uint32_t TOTAL = BARS + 128;
+    static constexpr uint32_t TOTAL = BARS + 192;
     static constexpr size_t SMEM = TOTAL + 1024;                            // alignment slack
     static_assert(BT % 16 == 0 && BARS % 8 == 0, "aligned regions");
 };
@@ -676,8 +684,9 @@ __device__ __forceinline__ int tc_scale_exp(uint32_t mb) {
 // s2 = j + 8 - (16 b + k) (0 outside the support); A' (flip) takes h(-s1, -s2).
 __global__ void __launch_bounds__(TCTHREADS)
 conv_tc_plan_kernel(const float* __restrict__ psf, int q1, int q2, int flip, uint8_t* plan) {
+    // block (u, p) writes the tile of PSF row u, plane p; every block finds the scale
     __shared__ uint32_t red[TCTHREADS / 32];
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, u = blockIdx.x, p = blockIdx.y;
     const int kw = 2 * q2 + 1, count = (2 * q1 + 1) * kw;
     uint32_t mb = 0;
     for (int i = tid; i < count; i += TCTHREADS) mb = max(mb, __float_as_uint(fabsf(psf[i])));
@@ -688,12 +697,11 @@ conv_tc_plan_kernel(const float* __restrict__ psf, int q1, int q2, int flip, uin
     for (int w = 0; w < TCTHREADS / 32; ++w) mb = max(mb, red[w]);
     const int eh = tc_scale_exp(mb);
     const float sc = pow2f(eh);
-    if (tid == 0) *reinterpret_cast<int*>(plan) = eh;
-    uint16_t* tiles = reinterpret_cast<uint16_t*>(plan + TC_PLAN_HEAD);
-    constexpr int PER_U = 2 * 64 * 16;
-    for (int i = tid; i < TCU * PER_U; i += TCTHREADS) {
-        const int u = i / PER_U, rem = i % PER_U;
-        const int p = rem / (64 * 16), n = (rem / 16) % 64, k = rem % 16;
+    if (tid == 0 && u == 0 && p == 0) *reinterpret_cast<int*>(plan) = eh;
+    uint16_t* tile =
+        reinterpret_cast<uint16_t*>(plan + TC_PLAN_HEAD) + (size_t)(u * 2 + p) * (TC_BTILE / 2);
+    for (int i = tid; i < 64 * 16; i += TCTHREADS) {
+        const int n = i / 16, k = i % 16;
         const int band = n < 32 ? 1 : 0, part = (n / 16) & 1, j = n % 16;
         const int s1 = TCQ - u, s2 = j + TCQ - (16 * band + k);
         float hv = 0.f;
@@ -705,21 +713,37 @@ conv_tc_plan_kernel(const float* __restrict__ psf, int q1, int q2, int flip, uin
         const __half th = __float2half_rn(hs);
         const __half tl = __float2half_rn(hs - __half2float(th));
         const __half v = p == 0 ? (part == 0 ? th : tl) : (part == 0 ? __float2half_rn(0.f) : th);
-        tiles[(size_t)(u * 2 + p) * (TC_BTILE / 2) + (k / 8) * 64 * 8 + n * 8 + k % 8] =
-            __half_as_ushort(v);
+        tile[(k / 8) * 64 * 8 + n * 8 + k % 8] = __half_as_ushort(v);
     }
 }
 
+// Two fp16 halves of a pair of values (|x| < 2^15 after the tile's scaling):
+// Veltkamp's splitting with sigma = 2^13 + 1 gives hi with at most 11
+// significant bits (exact in fp16 in its normal range) and lo = x - hi
+// exactly; lo is rounded to fp16 (11 of its at most 13 bits).  Plain
+// round-to-nearest operations: nothing is contracted into FMAs.
+__device__ __forceinline__ void tc_split2(float x0, float x1, uint32_t* hi, uint32_t* lo) {
+    constexpr float SIGMA = 8193.f;
+    const float g0 = __fmul_rn(SIGMA, x0), g1 = __fmul_rn(SIGMA, x1);
+    const float h0 = __fsub_rn(g0, __fsub_rn(g0, x0)), h1 = __fsub_rn(g1, __fsub_rn(g1, x1));
+    const __half2 hh = __floats2half2_rn(h0, h1);
+    const __half2 ll = __floats2half2_rn(__fsub_rn(x0, h0), __fsub_rn(x1, h1));
+    *hi = *reinterpret_cast<const uint32_t*>(&hh);
+    *lo = *reinterpret_cast<const uint32_t*>(&ll);
+}
+
 // Box of tile i: fix-up, scale and split into the plane pair at `hi` (lo one
-// plane further).  Returns the scale exponent; called by every thread.
+// plane further).  Returns the scale exponent; called by the NT threads that
+// share barrier BAR (0: the whole block).
+template <int BAR, int NT>
 __device__ __forceinline__ int tc_split_box(const ConvArgs& a, float* box, uint8_t* hi, int r0,
-                                            int c0, uint32_t* red) {
-    const int tid = threadIdx.x;
+                                            int c0, uint32_t* red, int tid) {
     if (r0 - TCQ < 0 || r0 + TCM + TCQ > a.n1 || c0 - TCQ < 0 || c0 + TCW + TCQ > a.n2)
-        fixup_tile<TCQ, GTC>(a, box, TCWB, r0, c0, tid, TCTHREADS);
+        fixup_tile<TCQ, GTC, BAR>(a, box, TCWB, r0, c0, tid, NT);
     const float4* b4 = reinterpret_cast<const float4*>(box);
     uint32_t mb = 0;
-    for (int it = tid; it < TCHB * TCNG; it += TCTHREADS) {
+#pragma unroll 4
+    for (int it = tid; it < TCHB * TCNG; it += NT) {
         const int row = it / TCNG, g = it % TCNG;
         const float4 v0 = b4[row * (TCWB / 4) + 2 * g], v1 = b4[row * (TCWB / 4) + 2 * g + 1];
         mb = max(mb, max(max(__float_as_uint(fabsf(v0.x)), __float_as_uint(fabsf(v0.y))),
@@ -729,27 +753,22 @@ __device__ __forceinline__ int tc_split_box(const ConvArgs& a, float* box, uint8
     }
     mb = __reduce_max_sync(0xffffffffu, mb);
     if ((tid & 31) == 0) red[tid >> 5] = mb;
-    __syncthreads();
+    stencil_sync<BAR>(NT);
     mb = 0;
 #pragma unroll
-    for (int w = 0; w < TCTHREADS / 32; ++w) mb = max(mb, red[w]);
+    for (int w = 0; w < NT / 32; ++w) mb = max(mb, red[w]);
     const int ex = tc_scale_exp(mb);
     const float sc = pow2f(ex);
     uint8_t* lo = hi + TC_PLANE_BYTES;
-    for (int it = tid; it < TCHB * TCNG; it += TCTHREADS) {
+#pragma unroll 2
+    for (int it = tid; it < TCHB * TCNG; it += NT) {
         const int row = it / TCNG, g = it % TCNG;
         const float4 v0 = b4[row * (TCWB / 4) + 2 * g], v1 = b4[row * (TCWB / 4) + 2 * g + 1];
-        const float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
         uint32_t h[4], l[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const float s0 = v[2 * e] * sc, s1 = v[2 * e + 1] * sc;
-            const __half h0 = __float2half_rn(s0), h1 = __float2half_rn(s1);
-            const __half l0 = __float2half_rn(s0 - __half2float(h0));
-            const __half l1 = __float2half_rn(s1 - __half2float(h1));
-            h[e] = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
-            l[e] = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
-        }
+        tc_split2(v0.x * sc, v0.y * sc, &h[0], &l[0]);
+        tc_split2(v0.z * sc, v0.w * sc, &h[1], &l[1]);
+        tc_split2(v1.x * sc, v1.y * sc, &h[2], &l[2]);
+        tc_split2(v1.z * sc, v1.w * sc, &h[3], &l[3]);
         const size_t off = ((size_t)g * TCNR + row) * 16;
         *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
         *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
@@ -760,6 +779,11 @@ __device__ __forceinline__ int tc_split_box(const ConvArgs& a, float* box, uint8
 
 // The MMAs of one tile (one thread): planes at `hi` (lo one plane further),
 // accumulators at TMEM column d, PSF rows u0 .. u1 of the B tiles at `bt`.
+// Slice-major order: the MMAs of a slice accumulate into the same TMEM
+// columns back to back, and the slices run 0, 2, 4, 1, 3 so that consecutive
+// slices touch disjoint columns (an MMA into columns that the previous one
+// only partly covered waits for it).  The first MMA of slices 0, 2 and 4
+// initialises chunks 0 | 1, 2 | 3, which together cover the tile.
 __device__ __forceinline__ void tc_issue(uint32_t hi, uint32_t bt, uint32_t d, int u0, int u1) {
     using namespace tc;
     constexpr uint32_t LBO = TCNR * 16;
@@ -768,28 +792,22 @@ __device__ __forceinline__ void tc_issue(uint32_t hi, uint32_t bt, uint32_t d, i
     constexpr uint32_t id32 = idesc_f16_f32(TCM, 32), id64 = idesc_f16_f32(TCM, 64);
     constexpr uint64_t HALF0 = (32 * 16) >> 4;           // B rows 32..63: band B0
     constexpr int NS = TCW / 16;                          // chunks; slices 0 .. NS
-    for (int u = u0; u <= u1; ++u) {
-        const uint64_t bh = b0 + (uint64_t)((u * 2) * TC_BTILE >> 4);
-        const uint64_t bl = bh + (uint64_t)(TC_BTILE >> 4);
-        const bool first = u == u0;
+    static_assert(NS == 4, "slice order below");
+    constexpr int order[NS + 1] = {0, 2, 4, 1, 3};
 #pragma unroll
-        for (int s = 0; s <= NS; ++s) {
-            const uint64_t ao = (uint64_t)(((2 * s) * LBO + u * 16) >> 4);
-            if (s == 0) {
-                mma_bf16(d, ah0 + ao, bh + HALF0, id32, first ? 0u : 1u);
-                mma_bf16(d, al0 + ao, bl + HALF0, id32, 1u);
-            } else if (s == NS) {
-                mma_bf16(d + 32 * (NS - 1), ah0 + ao, bh, id32, 1u);
-                mma_bf16(d + 32 * (NS - 1), al0 + ao, bl, id32, 1u);
-            } else {
-                if (first) {         // chunk s starts here: initialise it alone
-                    mma_bf16(d + 32 * s, ah0 + ao, bh + HALF0, id32, 0u);
-                    mma_bf16(d + 32 * (s - 1), ah0 + ao, bh, id32, 1u);
-                } else {
-                    mma_bf16(d + 32 * (s - 1), ah0 + ao, bh, id64, 1u);
-                }
-                mma_bf16(d + 32 * (s - 1), al0 + ao, bl, id64, 1u);
-            }
+    for (int oi = 0; oi <= NS; ++oi) {
+        const int s = order[oi];
+        // slice 0 feeds chunk 0 (band B0), slice NS chunk NS - 1 (band B1), the
+        // others chunks s - 1 and s
+        const uint32_t dd = s == 0 ? d : d + 32 * (s - 1);
+        const uint32_t id = (s == 0 || s == NS) ? id32 : id64;
+        const uint64_t boff = s == 0 ? HALF0 : 0;
+        const uint64_t as = (uint64_t)(((2 * s) * LBO) >> 4);
+        for (int u = u0; u <= u1; ++u) {
+            const uint64_t bh = b0 + (uint64_t)((u * 2) * TC_BTILE >> 4) + boff;
+            const uint64_t ao = as + (uint64_t)u;          // 16 u bytes: box rows u .. u + 127
+            mma_bf16(dd, ah0 + ao, bh, id, (u == u0 && s % 2 == 0) ? 0u : 1u);
+            mma_bf16(dd, al0 + ao, bh + (uint64_t)(TC_BTILE >> 4), id, 1u);
         }
     }
 }
@@ -882,12 +900,57 @@ __device__ __forceinline__ void tc_load_chunk(uint32_t d, int c, float scale, fl
     for (int j = 0; j < 16; ++j) y[j] = (P[j] + R[j]) * scale;
 }
 
-// Persistent tensor-core stencil (every mode but the folded one).  Each CTA
-// walks the tiles t = blockIdx.x + i gridDim.x.  While the tensor cores run
-// tile i, the threads fix up and split the box of tile i + 1 into the other
-// plane set and the TMA brings the box of tile i + 2; then they read tile i's
-// accumulators and apply the epilogue.
-__global__ void __launch_bounds__(TCTHREADS, 1)
+// Sum of v over the NT compute threads of barrier BAR added to *sumsq (one
+// float64 atomic per CTA; float32 per-thread partials).
+template <int BAR, int NT>
+__device__ __forceinline__ void tc_add_sumsq(double* sumsq, float vf, double* part, int tid) {
+    double v = vf;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((tid & 31) == 0) part[tid >> 5] = v;
+    stencil_sync<BAR>(NT);
+    if (tid == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) t += part[w];
+        if (t != 0.0) atomicAdd(sumsq, t);
+    }
+    stencil_sync<BAR>(NT);
+}
+
+// OR of v over the NT threads of named barrier BAR.
+template <int BAR, int NT>
+__device__ __forceinline__ bool tc_bar_or(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(BAR), "n"(NT)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Persistent tensor-core stencil (every mode but the folded one), warp
+// specialised.  Warp 8 (one thread) is the producer: it requests the halo box
+// of each tile by TMA as soon as the previous box has been split, and issues
+// a tile's MMAs once its planes are written and its accumulator set (one of
+// two) has been read out.  Warps 0-7 split box i into plane set i & 1, then
+// read the accumulators of tile i - 1 and apply the epilogue, so that the
+// split and the epilogue overlap the MMAs.  Each CTA walks the tiles
+// t = blockIdx.x + i gridDim.x.  Every wait is bounded; a wait that gives up
+// raises the CTA's flag, which ends both roles, and the producer waits
+// (bounded) for its copies and MMAs in flight before the CTA exits.
+constexpr int TC_NT = 256;                       // compute threads (named barrier 1)
+constexpr int TC_TILE_THREADS = TC_NT + 32;      // plus the producer warp
+
+__global__ void __launch_bounds__(TC_TILE_THREADS, 1)
 conv_tc_kernel(const __grid_constant__ CUtensorMap tmx, const ConvArgs a, const uint8_t* plan,
                int ntx, int ntiles, int vec3) {
     using namespace tc;
@@ -896,23 +959,36 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmx, const ConvArgs a, const 
     uint8_t* sb = smem_tc + ((1024u - (smem_u32(smem_tc) & 1023u)) & 1023u);
     const uint32_t sbase = smem_u32(sb);
     float* box = reinterpret_cast<float*>(sb + L::BOX);
-    const uint32_t box_bar = sbase + L::BARS, b_bar = box_bar + 8, mma_bar = box_bar + 16;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(sb + L::BARS + 32);
-    int* sex = reinterpret_cast<int*>(sb + L::BARS + 40);
-    uint32_t* red = reinterpret_cast<uint32_t*>(sb + L::BARS + 48);
+    // mbarriers: box full / empty, B tiles, and per accumulator set b: planes
+    // full, MMAs done, accumulators free
+    const uint32_t bars = sbase + L::BARS;
+    const uint32_t box_full = bars, box_empty = bars + 8, b_bar = bars + 16;
+    auto planes_full = [&](int b) { return bars + 24 + 8u * b; };
+    auto mma_done = [&](int b) { return bars + 40 + 8u * b; };
+    auto d_free = [&](int b) { return bars + 56 + 8u * b; };
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sb + L::BARS + 72);
+    int* sflag = reinterpret_cast<int*>(sb + L::BARS + 76);
+    int* sex = reinterpret_cast<int*>(sb + L::BARS + 80);
+    uint32_t* red = reinterpret_cast<uint32_t*>(sb + L::BARS + 88);
+    double* part = reinterpret_cast<double*>(sb + L::BARS + 120);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int u0 = TCQ - a.q1, u1 = TCQ + a.q1;
     const int nmine = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
     if (tid == 0) {
-        mbar_init(box_bar, 1);
+        mbar_init(box_full, 1);
+        mbar_init(box_empty, 1);
         mbar_init(b_bar, 1);
-        mbar_init(mma_bar, 1);
-        mbar_init(mma_bar + 8, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(planes_full(b), 1);
+            mbar_init(mma_done(b), 1);
+            mbar_init(d_free(b), 1);
+        }
+        *sflag = 0;
         fence_mbar_init();
         prefetch_tmap(&tmx);
     }
-    if (warp == 0) {
+    if (warp == 8) {
         tmem_alloc(smem_u32(tslot), TC_TMEM_COLS);
         tmem_relinquish();
     }
@@ -920,116 +996,122 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmx, const ConvArgs a, const 
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem = *tslot;
-    if (tid == 0 && nmine > 0) {         // the plan does not depend on the previous kernel
-        const uint32_t bytes = (uint32_t)(u1 - u0 + 1) * 2 * TC_BTILE;
-        mbar_arrive_expect_tx(b_bar, bytes);
-        bulk_load(sbase + L::BT + (uint32_t)u0 * 2 * TC_BTILE,
-                  plan + TC_PLAN_HEAD + (size_t)u0 * 2 * TC_BTILE, bytes, b_bar);
-    }
     const float seh = pow2f(-__ldg(reinterpret_cast<const int*>(plan)));
-    pdl_wait();                          // the input image comes from the previous kernel
-
+    const uint32_t polls = g_conv_wait_polls;
     auto tile_origin = [&](int i, int* r0, int* c0) {
         const int t = blockIdx.x + i * gridDim.x;
         *r0 = (t / ntx) * TCM;
         *c0 = (t % ntx) * TCW;
     };
-    auto request = [&](int i) {          // thread 0
-        int r0, c0;
-        tile_origin(i, &r0, &c0);
-        fence_proxy_async_smem();        // the fix-up's generic writes before the async copy
-        mbar_arrive_expect_tx(box_bar, TC_BOX_BYTES);
-        tma_load_2d(sbase + L::BOX, &tmx, c0 - TCQ, r0 - TCQ, box_bar);
-    };
-    const uint32_t polls = g_conv_wait_polls;
     auto plane_set = [&](int i) { return sb + L::PLANES + (uint32_t)(i & 1) * 2 * TC_PLANE_BYTES; };
-    // box i -> plane set i & 1; false (on every thread) when a wait gave up
-    auto stage = [&](int i) -> bool {
-        bool ok = mbar_wait(box_bar, (uint32_t)(i & 1), polls);
-        if (i == 0) ok = ok && mbar_wait(b_bar, 0, polls);
-        if (__syncthreads_or(!ok)) return false;
-        int r0, c0;
-        tile_origin(i, &r0, &c0);
-        const int ex = tc_split_box(a, box, plane_set(i), r0, c0, red);
-        if (tid == 0) sex[i & 1] = ex;
-        return true;
-    };
 
-    bool failed = false;
-    int issued = 0, requested = 0, staged = 0, li = 0;
-    if (nmine > 0) {
-        if (tid == 0) request(0);
-        requested = 1;
-        if (!stage(0)) {
-            failed = true;
-        } else {
-            staged = 1;
-            fence_before_sync();
-            __syncthreads();             // box consumed, planes written
-            if (tid == 0) {
-                if (nmine > 1) request(1);
-                fence_after_sync();
-                tc_issue(smem_u32(plane_set(0)), sbase + L::BT, tmem, u0, u1);
-                mma_commit(mma_bar);
-            }
-            requested = nmine > 1 ? 2 : 1;
-            issued = 1;
+    if (warp == 8) {
+        // ---- producer
+        if (lane == 0 && nmine > 0) {    // the plan does not depend on the previous kernel
+            const uint32_t bytes = (uint32_t)(u1 - u0 + 1) * 2 * TC_BTILE;
+            mbar_arrive_expect_tx(b_bar, bytes);
+            bulk_load(sbase + L::BT + (uint32_t)u0 * 2 * TC_BTILE,
+                      plan + TC_PLAN_HEAD + (size_t)u0 * 2 * TC_BTILE, bytes, b_bar);
         }
-    }
-    for (; !failed && li < nmine; ++li) {
-        if (li + 1 < nmine) {
-            if (!stage(li + 1)) {
+        pdl_wait();                      // the input image comes from the previous kernel
+        if (lane == 0 && nmine > 0) {
+            auto request = [&](int i) {
+                int r0, c0;
+                tile_origin(i, &r0, &c0);
+                mbar_arrive_expect_tx(box_full, TC_BOX_BYTES);
+                tma_load_2d(sbase + L::BOX, &tmx, c0 - TCQ, r0 - TCQ, box_full);
+            };
+            request(0);
+            int requested = 1, issued = 0;
+            bool ok = mbar_wait(b_bar, 0, polls);
+            for (int i = 0; ok && i < nmine; ++i) {
+                if (i + 1 < nmine) {     // box i is split: the buffer takes box i + 1
+                    ok = mbar_wait(box_empty, (uint32_t)(i & 1), polls) && !*(volatile int*)sflag;
+                    if (!ok) break;
+                    request(i + 1);
+                    requested = i + 2;
+                }
+                ok = mbar_wait(planes_full(i & 1), (uint32_t)((i >> 1) & 1), polls);
+                if (ok && i >= 2) ok = mbar_wait(d_free(i & 1), (uint32_t)(((i - 2) >> 1) & 1), polls);
+                if (!ok || *(volatile int*)sflag) break;
+                fence_after_sync();
+                tc_issue(smem_u32(plane_set(i)), sbase + L::BT, tmem + (uint32_t)(i & 1) * 128, u0,
+                         u1);
+                mma_commit(mma_done(i & 1));
+                issued = i + 1;
+            }
+            if (!ok) {
+                atomicExch(sflag, 1);
+                atomicExch(&g_conv_timeout, 1);
+            }
+            // nothing in flight when the CTA exits (bounded waits; phases that
+            // already completed return at once)
+            mbar_wait(box_full, (uint32_t)((requested - 1) & 1));
+            if (issued > 0) mbar_wait(mma_done((issued - 1) & 1), (uint32_t)(((issued - 1) >> 1) & 1));
+            if (issued > 1) mbar_wait(mma_done((issued - 2) & 1), (uint32_t)(((issued - 2) >> 1) & 1));
+        }
+    } else {
+        // ---- compute warps
+        pdl_wait();                      // before writing what the previous kernel may read
+        const int quarter = warp & 3, hw = warp >> 2;
+        const int m = quarter * 32 + lane;
+        auto epilogue = [&](int j) -> bool {
+            int r0, c0;
+            tile_origin(j, &r0, &c0);
+            const int row = r0 + m;
+            bool ok = true;
+            if (tid == 0) ok = mbar_wait(mma_done(j & 1), (uint32_t)((j >> 1) & 1), polls);
+            if (tc_bar_or<1, TC_NT>(!ok)) return false;
+            fence_after_sync();
+            if (a.early_trigger && j == nmine - 1) pdl_trigger();
+            const float scale = pow2f(-sex[j & 1]) * seh;
+            const uint32_t d = tmem + (uint32_t)(j & 1) * 128 + ((uint32_t)(quarter * 32) << 16);
+            float sq = 0.f;
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+                const int c = 2 * hw + cc;
+                float y[16];
+                tc_load_chunk(d, c, scale, y);
+                if (row < a.n1) sq += tc_store16(a, row, c0 + 16 * c, y, vec3 != 0);
+            }
+            fence_before_sync();
+            if (a.sumsq) tc_add_sumsq<1, TC_NT>(a.sumsq, sq, part, tid);
+            else stencil_sync<1>(TC_NT);
+            if (tid == 0) mbar_arrive(d_free(j & 1));
+            return true;
+        };
+        bool failed = false;
+        for (int i = 0; i < nmine; ++i) {
+            bool ok = true;
+            if (tid == 0) ok = mbar_wait(box_full, (uint32_t)(i & 1), polls) && !*(volatile int*)sflag;
+            if (tc_bar_or<1, TC_NT>(!ok)) {
                 failed = true;
                 break;
             }
-            staged = li + 2;
-            fence_before_sync();
-            __syncthreads();
+            int r0, c0;
+            tile_origin(i, &r0, &c0);
+            const int ex = tc_split_box<1, TC_NT>(a, box, plane_set(i), r0, c0, red, tid);
+            if (tid == 0) sex[i & 1] = ex;
+            stencil_sync<1>(TC_NT);      // box read, planes written (each writer fenced)
             if (tid == 0) {
-                if (li + 2 < nmine) request(li + 2);
-                fence_after_sync();
-                tc_issue(smem_u32(plane_set(li + 1)), sbase + L::BT,
-                         tmem + (uint32_t)((li + 1) & 1) * 128, u0, u1);
-                mma_commit(mma_bar + 8u * ((li + 1) & 1));
+                mbar_arrive(box_empty);
+                mbar_arrive(planes_full(i & 1));
             }
-            if (li + 2 < nmine) requested = li + 3;
-            issued = li + 2;
+            if (i >= 1 && !epilogue(i - 1)) {
+                failed = true;
+                break;
+            }
         }
-        const bool ok = mbar_wait(mma_bar + 8u * (li & 1), (uint32_t)((li >> 1) & 1), polls);
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
+        if (!failed && nmine > 0 && !epilogue(nmine - 1)) failed = true;
+        if (failed && tid == 0) {
+            atomicExch(sflag, 1);
+            atomicExch(&g_conv_timeout, 1);
         }
-        fence_after_sync();
-        if (a.early_trigger && li == nmine - 1) pdl_trigger();
-        int r0, c0;
-        tile_origin(li, &r0, &c0);
-        const int quarter = warp & 3, hw = warp >> 2;
-        const int m = quarter * 32 + lane, row = r0 + m;
-        const float scale = pow2f(-sex[li & 1]) * seh;
-        const uint32_t d = tmem + (uint32_t)(li & 1) * 128 + ((uint32_t)(quarter * 32) << 16);
-        float sq = 0.f;
-#pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-            const int c = 2 * hw + cc;
-            float y[16];
-            tc_load_chunk(d, c, scale, y);
-            if (row < a.n1) sq += tc_store16(a, row, c0 + 16 * c, y, vec3 != 0);
-        }
-        if (a.sumsq) add_sumsq(a.sumsq, sq);
-        fence_before_sync();
     }
     if (!a.early_trigger) pdl_trigger();
-    if (failed && tid == 0) {
-        atomicExch(&g_conv_timeout, 1);
-        // copies and MMAs possibly still in flight: wait for them (bounded)
-        // before the shared memory and the TMEM are released
-        for (int i = staged; i < requested; ++i) mbar_wait(box_bar, (uint32_t)(i & 1));
-        for (int i = li; i < issued; ++i) mbar_wait(mma_bar + 8u * (i & 1), (uint32_t)((i >> 1) & 1));
-    }
     fence_before_sync();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 8) {
         fence_after_sync();
         tmem_dealloc(tmem, TC_TMEM_COLS);
     }
@@ -1121,11 +1203,14 @@ conv_tc_fold_kernel(const __grid_constant__ CUtensorMap tmx, const ConvArgs a, c
         unit_origin(li, &r0, &c0);
         const int cg = rank == 0 ? c0 : a.n2 - c0 - TCW;
         // 1. box -> planes -> MMAs (the previous unit's MMAs have completed)
-        bool ok = mbar_wait(box_bar, (uint32_t)(li & 1), polls);
-        if (li == 0) ok = ok && mbar_wait(b_bar, 0, polls);
+        bool ok = true;
+        if (tid == 0) {          // one thread polls; the others wait at the block barrier
+            ok = mbar_wait(box_bar, (uint32_t)(li & 1), polls);
+            if (li == 0) ok = ok && mbar_wait(b_bar, 0, polls);
+        }
         bool bad = __syncthreads_or(!ok);
         if (!bad) {
-            const int ex = tc_split_box(a, box, planes, r0, cg, red);
+            const int ex = tc_split_box<0, TCTHREADS>(a, box, planes, r0, cg, red, tid);
             consumed = li + 1;
             if (tid == 0) sex[0] = ex;
             fence_before_sync();
@@ -1138,7 +1223,7 @@ conv_tc_fold_kernel(const __grid_constant__ CUtensorMap tmx, const ConvArgs a, c
             }
             if (li + 1 < nmine) requested = li + 2;
             issued = li + 1;
-            ok = mbar_wait(mma_bar, (uint32_t)(li & 1), polls);
+            if (tid == 0) ok = mbar_wait(mma_bar, (uint32_t)(li & 1), polls);
             bad = __syncthreads_or(!ok);
             fence_after_sync();
         }
@@ -1424,8 +1509,8 @@ cudaError_t launch_tc(const ConvArgs& a, cudaStream_t s) {
     }
     const int ntx = (a.n2 + TCW - 1) / TCW, ntiles = ntx * nty;
     const int grid = ntiles < sm_count() ? ntiles : sm_count();
-    return launch_pdl(conv_tc_kernel, dim3(grid), dim3(TCTHREADS), TcSmem<0>::SMEM, s, map, a,
-                      a.tcplan, ntx, ntiles, vec3 ? 1 : 0);
+    return launch_pdl(conv_tc_kernel, dim3(grid), dim3(TC_TILE_THREADS), TcSmem<0>::SMEM, s, map,
+                      a, a.tcplan, ntx, ntiles, vec3 ? 1 : 0);
 }
 
 // ------------------------------------------------ batched stencils -------
@@ -1870,7 +1955,7 @@ ar_status conv_tc_plan(const float* psf, int q1, int q2, int flip, uint8_t* plan
     if (q1 > TCQ || q2 > TCQ || q1 < 0 || q2 < 0)
         return fail(AR_ERR_UNSUPPORTED, "tensor-core stencil plans take q <= %d", TCQ);
     count_launch();
-    conv_tc_plan_kernel<<<1, TCTHREADS, 0, s>>>(psf, q1, q2, flip, plan);
+    conv_tc_plan_kernel<<<dim3(TCU, 2), TCTHREADS, 0, s>>>(psf, q1, q2, flip, plan);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core stencil plan");
     return AR_OK;
