@@ -260,6 +260,9 @@ def run_own(args):
             x_ref = x_d.clone()
             out["forms"] = {"bf16x2": precision_form(ar, torch, stream, g_d, f_d, h, flush,
                                                      max(args.steps // 2, 3), x_ref)}
+            out["forms"]["stencil_f16x2"] = precision_form(ar, torch, stream, g_d, f_d, h, flush,
+                                                           max(args.steps // 2, 3), x_ref,
+                                                           precision="fp32", stencil="f16x2")
             if not args.no_batch:
                 out["forms"]["batched"] = batched_form(ar, torch, dev, stream, flush, 3)
             out["bcs"] = bcs_form(ar, torch, stream, g_d, f_d, h, flush, max(args.steps // 2, 3))
@@ -409,14 +412,23 @@ def measured_traffic(kind):
     return None
 
 
-def precision_form(ar, torch, stream, g_d, f_d, h, flush, steps, x_ref):
-    """The bf16x2 precision mode on the same workload: throughput, the RRE it
-    reaches, and its deviation from the float32-grade iterate after 50 steps."""
+FORM_LABEL = {
+    ("bf16x2", "fp32"): "bf16x2 contractions (two bf16 planes, three products)",
+    ("fp32", "f16x2"): "tensor-core stencils (two fp16 planes per operand, per-tile power-of-two "
+                       "scaling, three products) with the float32-grade contractions",
+}
+
+
+def precision_form(ar, torch, stream, g_d, f_d, h, flush, steps, x_ref, precision="bf16x2",
+                   stencil="fp32"):
+    """Another arithmetic on the same workload (the bf16x2 contractions, or the
+    tensor-core stencils): throughput, the RRE it reaches, and its deviation
+    from the float32-grade iterate after 50 steps."""
     x_fast = torch.empty_like(g_d)
 
     def step():
         return ar.ar_restore(g_d, h, ALPHA, TAU, ITERS, True, f_true=f_d, x_out=x_fast,
-                             precision="bf16x2")
+                             precision=precision, stencil=stencil)
 
     for _ in range(3):
         step()
@@ -430,7 +442,7 @@ def precision_form(ar, torch, stream, g_d, f_d, h, flush, steps, x_ref):
         b.synchronize()
         tot += a.elapsed_time(b)
     dev_rel = float(torch.linalg.vector_norm(x_fast - x_ref) / torch.linalg.vector_norm(x_ref))
-    return {"precision": "bf16x2 (two bf16 planes, three products)",
+    return {"precision": FORM_LABEL[(precision, stencil)],
             "value": round(N1 * N2 * ITERS * steps / 1e6 / (tot / 1e3), 2), "unit": UNIT,
             "ms_per_step": round(tot / steps, 4), "rre_best": round(float(np.min(tr)), 6),
             "best_iter": best, "rel_l2_vs_fp32_grade_x50": dev_rel}
@@ -737,7 +749,25 @@ def matvec_hbm_form(ar, torch, dev, stream, reps=10):
         ms = tot / reps
         gbs = 8.0 * n * n / (ms / 1e3) / 1e9
         tf = 2 * (2 * q + 1) ** 2 * n * n / (ms / 1e3) / 1e12
+        y32 = y.clone()
+        for _ in range(3):
+            ar.ar_blur_apply(x, hd, y, stencil="f16x2")
+        ttc = 0.0
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ar.ar_blur_apply(x, hd, y, stencil="f16x2")
+            e1.record(stream)
+            e1.synchronize()
+            ttc += e0.elapsed_time(e1)
+        mtc = ttc / reps
+        gtc = 8.0 * n * n / (mtc / 1e3) / 1e9
+        dev_tc = float((y - y32).abs().max() / y32.abs().max())
+        del y32
         out[f"{2 * q + 1}x{2 * q + 1}"] = {
+            "tensor_f16x2": {"us_per_call": round(mtc * 1e3, 2), "achieved_gbs": round(gtc, 1),
+                             "hbm_frac": round(gtc / peak, 4) if peak else None,
+                             "max_dev_vs_fp32_rel_max": dev_tc},
             "us_per_call": round(ms * 1e3, 2), "achieved_gbs": round(gbs, 1),
             "hbm_frac": round(gbs / peak, 4) if peak else None,
             "fp32_tflops": round(tf, 2), "alu_frac": round(tf / fp32_peak, 4),
