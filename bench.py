@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--stencil", default="fp32", choices=["fp32", "f16x2"],
+                    help="arithmetic of the timed step's blur and reblur (f16x2: tensor cores)")
     return ap.parse_args()
 
 
@@ -82,9 +84,10 @@ def replica_throughput(pixels, iters, steps, world, total_ms):
     return pixels * iters * steps * world / 1e6 / (total_ms / 1e3)
 
 
-def config_dict(world=1):
+def config_dict(world=1, stencil="fp32"):
     c = {"workload": WORKLOAD, "n1": N1, "n2": N2, "psf": "15x15 motion(len 11, 30 deg)+0.2 gauss",
          "iters_per_step": ITERS, "alpha": ALPHA, "tau": TAU, "precondition": True, "noise": NU,
+         "stencil": stencil,
          "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MiB write)",
          "parallelism": f"replicas{world}" if world > 1 else "single"}
     return c
@@ -182,7 +185,8 @@ def run_own(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def step():
-        return ar.ar_restore(g_d, h, ALPHA, TAU, ITERS, True, f_true=f_d, x_out=x_d)
+        return ar.ar_restore(g_d, h, ALPHA, TAU, ITERS, True, f_true=f_d, x_out=x_d,
+                             stencil=args.stencil)
 
     for _ in range(max(args.warmup, 0)):
         step()
@@ -239,7 +243,7 @@ def run_own(args):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": config_dict(world),
+            "config": config_dict(world, args.stencil),
             "e2e": {"value": round(e2e_value, 2), "unit": UNIT,
                     "h2d_bytes_per_step": int(g.nbytes + f.nbytes),
                     "d2h_bytes_per_step": int(g.nbytes + 8 * ITERS + 8 * (ITERS + 1))},
