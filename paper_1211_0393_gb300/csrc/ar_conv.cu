@@ -1046,6 +1046,7 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmx, const ConvArgs a, const 
             }
             // nothing in flight when the CTA exits (bounded waits; phases that
             // already completed return at once)
+            mbar_wait(b_bar, 0);
             mbar_wait(box_full, (uint32_t)((requested - 1) & 1));
             if (issued > 0) mbar_wait(mma_done((issued - 1) & 1), (uint32_t)(((issued - 1) >> 1) & 1));
             if (issued > 1) mbar_wait(mma_done((issued - 2) & 1), (uint32_t)(((issued - 2) >> 1) & 1));
@@ -1291,6 +1292,7 @@ conv_tc_fold_kernel(const __grid_constant__ CUtensorMap tmx, const ConvArgs a, c
     }
     if (failed && tid == 0) {
         atomicExch(&g_conv_timeout, 1);
+        mbar_wait(b_bar, 0);             // the B tiles' copy, if the first wait gave up
         for (int i = consumed; i < requested; ++i) mbar_wait(box_bar, (uint32_t)(i & 1));
         for (int i = li; i < issued; ++i) mbar_wait(mma_bar, (uint32_t)(i & 1));
     }

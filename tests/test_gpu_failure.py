@@ -36,22 +36,24 @@ def _inputs(n1, n2, seed):
 
 
 @pytest.mark.parametrize("pc", [True, False])
-def test_stencil_wait_timeout_is_reported_and_recoverable(ar, pc):
+@pytest.mark.parametrize("stencil", ["fp32", "f16x2"])
+def test_stencil_wait_timeout_is_reported_and_recoverable(ar, pc, stencil):
     # n2 % 4 == 0 and 16-byte aligned rows: the TMA stencils (and, preconditioned,
-    # the folding reblur) run
+    # the folding reblur) run; f16x2: the tensor-core stencils (producer warp and
+    # compute warps, and the folding pair whose ranks exchange the give-up)
     gd, fd, h = _inputs(256, 192, 3)
-    want, tr_want, _ = ar.ar_restore(gd, h, 0.1, 1.0, 4, pc, f_true=fd)
+    want, tr_want, _ = ar.ar_restore(gd, h, 0.1, 1.0, 4, pc, f_true=fd, stencil=stencil)
     want = want.clone()
     try:
         ar.set_stencil_wait_polls(0)
         with pytest.raises(ar.ARError) as ei:
-            ar.ar_restore(gd, h, 0.1, 1.0, 4, pc, f_true=fd)
+            ar.ar_restore(gd, h, 0.1, 1.0, 4, pc, f_true=fd, stencil=stencil)
         assert ei.value.name == "AR_ERR_TIMEOUT"
         assert "stencil" in str(ei.value)
     finally:
         ar.set_stencil_wait_polls()
     torch.cuda.synchronize()                       # the context is still usable
-    got, tr, _ = ar.ar_restore(gd, h, 0.1, 1.0, 4, pc, f_true=fd)
+    got, tr, _ = ar.ar_restore(gd, h, 0.1, 1.0, 4, pc, f_true=fd, stencil=stencil)
     assert torch.equal(got, want)
     np.testing.assert_allclose(tr, tr_want, rtol=1e-12)
 
