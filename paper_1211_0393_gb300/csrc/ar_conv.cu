@@ -846,49 +846,56 @@ __device__ __forceinline__ void split3_store16(uint16_t* planes, size_t pstride,
     }
 }
 
-// Epilogue of 16 outputs y[0..15] of row `row` at columns col .. col + 15
-// (n2 % 4 == 0, col % 16 == 0); returns the squares the mode sums.
-__device__ __forceinline__ float tc_store16(const ConvArgs& a, int row, int col, const float (&y)[16],
-                                            bool vec3) {
-    const int nv = min(16, a.n2 - col);
-    if (nv <= 0) return 0.f;
+// Epilogue of 4 outputs y of row `row` at columns col .. col + 3 (n2 % 4 == 0,
+// col % 4 == 0, all four inside the image); returns the squares the mode sums.
+__device__ __forceinline__ float tc_store4(const ConvArgs& a, int row, int col, float4 yv,
+                                           bool vec3) {
     const size_t o = (size_t)row * a.n2 + col;
-    float sq = 0.f;
     if (a.mode == CONV_SPLIT3) {
+        const float y[4] = {yv.x, yv.y, yv.z, yv.w};
+        const size_t po = (size_t)row * a.ld + col;
         if (vec3) {
-            split3_store16(a.planes, a.plane_stride, (size_t)row * a.ld + col, y, nv);
+            uint32_t w[3][2];
+#pragma unroll
+            for (int j = 0; j < 4; j += 2) {
+                float v0 = y[j], v1 = y[j + 1];
+#pragma unroll
+                for (int p = 0; p < 3; ++p) {
+                    const __nv_bfloat16 b0 = __float2bfloat16_rn(v0), b1 = __float2bfloat16_rn(v1);
+                    w[p][j / 2] = (uint32_t)__bfloat16_as_ushort(b0) |
+                                  ((uint32_t)__bfloat16_as_ushort(b1) << 16);
+                    v0 -= __bfloat162float(b0);
+                    v1 -= __bfloat162float(b1);
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+                *reinterpret_cast<uint2*>(a.planes + p * a.plane_stride + po) = make_uint2(w[p][0], w[p][1]);
         } else {
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-                if (j < nv) split3_store(a.planes, a.plane_stride, (size_t)row * a.ld + col + j, y[j]);
+            for (int j = 0; j < 4; ++j) split3_store(a.planes, a.plane_stride, po + j, y[j]);
         }
         return 0.f;
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        if (4 * q >= nv) break;
-        float4* p4 = reinterpret_cast<float4*>(a.out + o) + q;
-        const float4 yv = make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
-        if (a.mode == CONV_STORE) {
-            *p4 = yv;
-        } else if (a.mode == CONV_RESIDUAL) {
-            const float4 g = __ldg(reinterpret_cast<const float4*>(a.aux + o) + q);
-            const float4 r = make_float4(g.x - yv.x, g.y - yv.y, g.z - yv.z, g.w - yv.w);
-            *p4 = r;
-            if (a.sumsq) sq += r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
-        } else {                                           // CONV_AXPY
-            const float4 xo = *p4;
-            const float4 xn = make_float4(fmaf(a.tau, yv.x, xo.x), fmaf(a.tau, yv.y, xo.y),
-                                          fmaf(a.tau, yv.z, xo.z), fmaf(a.tau, yv.w, xo.w));
-            *p4 = xn;
-            if (a.f) {
-                const float4 f = __ldg(reinterpret_cast<const float4*>(a.f + o) + q);
-                const float e0 = xn.x - f.x, e1 = xn.y - f.y, e2 = xn.z - f.z, e3 = xn.w - f.w;
-                sq += e0 * e0 + e1 * e1 + e2 * e2 + e3 * e3;
-            }
-        }
+    float4* p4 = reinterpret_cast<float4*>(a.out + o);
+    if (a.mode == CONV_STORE) {
+        *p4 = yv;
+        return 0.f;
     }
-    return sq;
+    if (a.mode == CONV_RESIDUAL) {
+        const float4 g = __ldg(reinterpret_cast<const float4*>(a.aux + o));
+        const float4 r = make_float4(g.x - yv.x, g.y - yv.y, g.z - yv.z, g.w - yv.w);
+        *p4 = r;
+        return a.sumsq ? r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w : 0.f;
+    }
+    const float4 xo = *p4;                                   // CONV_AXPY
+    const float4 xn = make_float4(fmaf(a.tau, yv.x, xo.x), fmaf(a.tau, yv.y, xo.y),
+                                  fmaf(a.tau, yv.z, xo.z), fmaf(a.tau, yv.w, xo.w));
+    *p4 = xn;
+    if (!a.f) return 0.f;
+    const float4 f = __ldg(reinterpret_cast<const float4*>(a.f + o));
+    const float e0 = xn.x - f.x, e1 = xn.y - f.y, e2 = xn.z - f.z, e3 = xn.w - f.w;
+    return e0 * e0 + e1 * e1 + e2 * e2 + e3 * e3;
 }
 
 // The results of this thread's chunk c of the tile in D (TMEM, lane base
@@ -1056,10 +1063,16 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmx, const ConvArgs a, const 
         pdl_wait();                      // before writing what the previous kernel may read
         const int quarter = warp & 3, hw = warp >> 2;
         const int m = quarter * 32 + lane;
+        // Epilogue of tile j: each thread reads its row's accumulators (TMEM lane
+        // m) and parks the results in plane set j & 1 (free: tile j's MMAs are done
+        // and tile j + 2's split comes after this), then the warps walk the tile
+        // row by row, so that the loads and stores of global memory are whole
+        // 256-byte rows rather than 16-byte pieces of 32 rows.
+        constexpr int STG = TCW + 4;                     // staging pitch (floats)
+        static_assert(TCM * STG * 4 <= 2 * TC_PLANE_BYTES, "the staging fits a plane set");
         auto epilogue = [&](int j) -> bool {
             int r0, c0;
             tile_origin(j, &r0, &c0);
-            const int row = r0 + m;
             bool ok = true;
             if (tid == 0) ok = mbar_wait(mma_done(j & 1), (uint32_t)((j >> 1) & 1), polls);
             if (tc_bar_or<1, TC_NT>(!ok)) return false;
@@ -1067,15 +1080,28 @@ conv_tc_kernel(const __grid_constant__ CUtensorMap tmx, const ConvArgs a, const 
             if (a.early_trigger && j == nmine - 1) pdl_trigger();
             const float scale = pow2f(-sex[j & 1]) * seh;
             const uint32_t d = tmem + (uint32_t)(j & 1) * 128 + ((uint32_t)(quarter * 32) << 16);
-            float sq = 0.f;
+            float* stg = reinterpret_cast<float*>(plane_set(j));
 #pragma unroll
             for (int cc = 0; cc < 2; ++cc) {
                 const int c = 2 * hw + cc;
                 float y[16];
                 tc_load_chunk(d, c, scale, y);
-                if (row < a.n1) sq += tc_store16(a, row, c0 + 16 * c, y, vec3 != 0);
+                float4* dst = reinterpret_cast<float4*>(stg + m * STG + 16 * c);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    dst[q] = make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
             }
             fence_before_sync();
+            stencil_sync<1>(TC_NT);
+            float sq = 0.f;
+#pragma unroll 4
+            for (int it = tid; it < TCM * (TCW / 4); it += TC_NT) {
+                const int rl = it / (TCW / 4), q4 = it % (TCW / 4);
+                const int row = r0 + rl, col = c0 + 4 * q4;
+                if (row < a.n1 && col < a.n2)
+                    sq += tc_store4(a, row, col,
+                                    *reinterpret_cast<const float4*>(stg + rl * STG + 4 * q4), vec3 != 0);
+            }
             if (a.sumsq) tc_add_sumsq<1, TC_NT>(a.sumsq, sq, part, tid);
             else stencil_sync<1>(TC_NT);
             if (tid == 0) mbar_arrive(d_free(j & 1));
