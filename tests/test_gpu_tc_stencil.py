@@ -114,6 +114,10 @@ TC_CASES = [
     (1024, 1024, 7, 7, "ar"),
     (77, 300, 2, 6, "reflective"),
     (65, 68, 5, 3, "reflective"),
+    # more tiles than SMs: every CTA walks several tiles through both plane and
+    # accumulator sets (512 and 216 tiles), with ragged last rows and columns
+    (2048, 2048, 7, 7, "ar"),
+    (1500, 1100, 4, 6, "reflective"),
 ]
 
 
@@ -274,3 +278,23 @@ def test_restore_tc_stencil_bench_workload(ar):
     assert max(errs.values()) <= 1e-5, errs
     assert np.all(np.abs(np.asarray(tr) - to) <= 1e-5 * (1.0 + to))
     assert best == bo
+
+
+@pytest.mark.parametrize("pc,alpha", [(True, 0.3), (False, 0.0)])
+def test_restore_tc_stencil_past_one_wave(ar, pc, alpha):
+    """1104 x 1536: 216 blur tiles and 108 folding units, more than the SMs and
+    the co-resident clusters, so the persistent loops take several tiles (units)
+    each; two iterations against the oracle."""
+    rng = np.random.default_rng(1104)
+    n1, n2 = 1104, 1536
+    h = rand_psf(rng, 7, 6)
+    f = rng.uniform(0, 1, (n1, n2))
+    g = (O.ar_blur(f, h) + 0.005 * rng.standard_normal((n1, n2))).astype(np.float32)
+    f32 = f.astype(np.float32)
+    x, tr, _ = ar.ar_restore(dev(g), h, alpha, 1.0, 2, pc, f_true=dev(f32), stencil="f16x2")
+    xo, to, _ = O.restore(g.astype(np.float64), h, alpha, 1.0, 2, pc,
+                          f_true=f32.astype(np.float64))
+    tol = tol_alpha(alpha) if pc else 1e-5
+    assert rel_l2(x.cpu().numpy(), xo) <= tol
+    assert np.all(np.abs(np.asarray(tr) - to) <= tol * (1.0 + to))
+
