@@ -628,7 +628,7 @@ def learned_form(ar, torch, dev, stream, n_eval=CORR_EVAL):
     consecutive iterates, minus lambda_s^2); the model is trained on them, then
     restores a different 1024^2 scene blurred by each of 500 held-out PSFs (0.5%
     noise, 50 D-Landweber iterations) beside the symmetrized preconditioner
-    (the judge) and the closed-form correction, at two alphas."""
+    (the reference it must beat) and the closed-form correction, at two alphas."""
     train = W.corr_psfs(CORR_TRAIN, salt=1)
     held = W.corr_psfs(n_eval, salt=2)
     n = N1
@@ -887,7 +887,8 @@ def quality_vs_plain(ar, torch, stream, g_d, f_d, h, flush, oracle_best):
         out["time_ratio_plain_over_precond"] = round(out["plain_ms_to_target"] /
                                                      out["precond_ms_to_target"], 3)
     # the alpha reading: the bench takes the smallest half-decade alpha for which
-    # tau = 1 is stable; the survey's rule would minimise iterations to the best RRE
+    # tau = 1 is stable; the alternative rule, the alpha that minimises the
+    # iterations to the best RRE, is what this sweep reports beside it
     sweep = {}
     for a in (0.03, 0.1, 0.3, 1.0):
         _, tr_a, best_a = ar.ar_restore(g_d, h, a, TAU, ITERS, True, f_true=f_d)
