@@ -335,15 +335,39 @@ __device__ __forceinline__ void compute_tile(const ConvArgs& a, const float* til
     // rows whose loads the residual / AXPY epilogue issues together
     constexpr int EB = Q >= 5 ? (RS % 8 == 0 ? 8 : 6) : (RS % 4 == 0 ? 4 : 3);
     const int tx = threadIdx.x, ty = threadIdx.y;
+    const int col = c0 + tx, row0 = r0 + ty * RS;
+    const bool live = col < a.n2 && row0 < a.n1;
+    if (RW && a.mode == CONV_RESIDUAL) {
+        // the residual's g is read before the tap loop, so that its latency
+        // hides behind the FMAs (RS more live registers)
+        const int nr = min(RS, a.n1 - row0);
+        float gv[RS];
+#pragma unroll
+        for (int r = 0; r < RS; ++r)
+            gv[r] = live && r < nr ? __ldg(a.aux + (size_t)(row0 + r) * a.n2 + col) : 0.f;
+        float acc[RS];
+        tile_acc<Q, G>(tile, WP, coef, tx, ty, acc);
+        float sq = 0.f;
+        if (live) {
+#pragma unroll
+            for (int r = 0; r < RS; ++r) {
+                if (r < nr) {
+                    const float rv = gv[r] - acc[r];
+                    a.out[(size_t)(row0 + r) * a.n2 + col] = rv;
+                    if (a.sumsq) sq += rv * rv;          // ||g - A x||^2 when requested
+                }
+            }
+        }
+        if (a.sumsq) add_sumsq(a.sumsq, sq);
+        return;
+    }
     float acc[RS];
     tile_acc<Q, G>(tile, WP, coef, tx, ty, acc);
-    const int col = c0 + tx;
     float sq = 0.f;
-    if (col < a.n2 && r0 + ty * RS < a.n1) {
+    if (live) {
         if (RW) {
             sq = strip_epilogue<EB, G>(a, r0 + ty * RS, col, acc);
         } else {
-            const int row0 = r0 + ty * RS;
 #pragma unroll
             for (int r = 0; r < RS; ++r)
                 if (row0 + r < a.n1) sq += conv_epilogue(a, row0 + r, col, acc[r]);
