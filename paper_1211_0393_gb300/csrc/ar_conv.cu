@@ -272,59 +272,6 @@ __device__ __forceinline__ void tile_acc(const float* tile, int WP, const float*
     }
 }
 
-// The epilogue of one thread's strip of RS rows at column col, from row row0
-// on, for the modes that read global memory (residual, AXPY): the arithmetic
-// of conv_epilogue, with the loads of EB rows issued before their stores, so
-// that they do not wait on one another.
-template <int EB, class G>
-__device__ __forceinline__ float strip_epilogue(const ConvArgs& a, int row0, int col,
-                                                const float (&acc)[G::RS]) {
-    constexpr int RS = G::RS;
-    static_assert(RS % EB == 0, "chunks tile the strip");
-    const int nr = min(RS, a.n1 - row0);
-    float sq = 0.f;
-#pragma unroll
-    for (int c = 0; c < RS; c += EB) {
-        // a chunk's loads stay after the previous chunk's stores (and after the
-        // tap loop): hoisted, they would hold registers through it
-        asm volatile("" ::: "memory");
-        const size_t o0 = (size_t)(row0 + c) * a.n2 + col;
-        if (a.mode == CONV_RESIDUAL) {
-            float gv[EB];
-#pragma unroll
-            for (int r = 0; r < EB; ++r)
-                gv[r] = c + r < nr ? __ldg(a.aux + o0 + (size_t)r * a.n2) : 0.f;
-#pragma unroll
-            for (int r = 0; r < EB; ++r) {
-                if (c + r < nr) {
-                    const float rv = gv[r] - acc[c + r];
-                    a.out[o0 + (size_t)r * a.n2] = rv;
-                    if (a.sumsq) sq += rv * rv;          // ||g - A x||^2 when requested
-                }
-            }
-        } else {
-            float xv[EB], fv[EB];
-#pragma unroll
-            for (int r = 0; r < EB; ++r) {
-                xv[r] = c + r < nr ? a.out[o0 + (size_t)r * a.n2] : 0.f;
-                fv[r] = c + r < nr && a.f ? __ldg(a.f + o0 + (size_t)r * a.n2) : 0.f;
-            }
-#pragma unroll
-            for (int r = 0; r < EB; ++r) {
-                if (c + r < nr) {
-                    const float xn = fmaf(a.tau, acc[c + r], xv[r]);
-                    a.out[o0 + (size_t)r * a.n2] = xn;
-                    if (a.f) {
-                        const float e = xn - fv[r];
-                        sq += e * e;
-                    }
-                }
-            }
-        }
-    }
-    return sq;
-}
-
 // RW: the mode reads global memory in its epilogue (residual, AXPY); the
 // kernels are instantiated for both kinds, so that the store modes keep their
 // own (smaller) register allocation.
@@ -332,29 +279,41 @@ template <int Q, bool RW, class G>
 __device__ __forceinline__ void compute_tile(const ConvArgs& a, const float* tile, int WP,
                                              const float* coef, int r0, int c0) {
     constexpr int RS = G::RS;
-    // rows whose loads the residual / AXPY epilogue issues together
-    constexpr int EB = Q >= 5 ? (RS % 8 == 0 ? 8 : 6) : (RS % 4 == 0 ? 4 : 3);
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int col = c0 + tx, row0 = r0 + ty * RS;
     const bool live = col < a.n2 && row0 < a.n1;
-    if (RW && a.mode == CONV_RESIDUAL) {
-        // the residual's g is read before the tap loop, so that its latency
-        // hides behind the FMAs (RS more live registers)
+    if (RW) {
+        // the epilogue's inputs (g for the residual; x and f for the update) are
+        // read before the tap loop, so that their latency hides behind the FMAs
         const int nr = min(RS, a.n1 - row0);
-        float gv[RS];
+        const bool res = a.mode == CONV_RESIDUAL;
+        float pv[RS], fv[RS];
 #pragma unroll
-        for (int r = 0; r < RS; ++r)
-            gv[r] = live && r < nr ? __ldg(a.aux + (size_t)(row0 + r) * a.n2 + col) : 0.f;
+        for (int r = 0; r < RS; ++r) {
+            const size_t o = (size_t)(row0 + r) * a.n2 + col;
+            const bool in = live && r < nr;
+            pv[r] = in ? (res ? __ldg(a.aux + o) : a.out[o]) : 0.f;
+            fv[r] = in && !res && a.f ? __ldg(a.f + o) : 0.f;
+        }
         float acc[RS];
         tile_acc<Q, G>(tile, WP, coef, tx, ty, acc);
         float sq = 0.f;
         if (live) {
 #pragma unroll
             for (int r = 0; r < RS; ++r) {
-                if (r < nr) {
-                    const float rv = gv[r] - acc[r];
-                    a.out[(size_t)(row0 + r) * a.n2 + col] = rv;
-                    if (a.sumsq) sq += rv * rv;          // ||g - A x||^2 when requested
+                if (r >= nr) continue;
+                const size_t o = (size_t)(row0 + r) * a.n2 + col;
+                if (res) {
+                    const float rv = pv[r] - acc[r];
+                    a.out[o] = rv;
+                    if (a.sumsq) sq += rv * rv;      // ||g - A x||^2 when requested
+                } else {
+                    const float xn = fmaf(a.tau, acc[r], pv[r]);
+                    a.out[o] = xn;
+                    if (a.f) {
+                        const float e = xn - fv[r];
+                        sq += e * e;
+                    }
                 }
             }
         }
@@ -365,13 +324,9 @@ __device__ __forceinline__ void compute_tile(const ConvArgs& a, const float* til
     tile_acc<Q, G>(tile, WP, coef, tx, ty, acc);
     float sq = 0.f;
     if (live) {
-        if (RW) {
-            sq = strip_epilogue<EB, G>(a, r0 + ty * RS, col, acc);
-        } else {
 #pragma unroll
-            for (int r = 0; r < RS; ++r)
-                if (row0 + r < a.n1) sq += conv_epilogue(a, row0 + r, col, acc[r]);
-        }
+        for (int r = 0; r < RS; ++r)
+            if (row0 + r < a.n1) sq += conv_epilogue(a, row0 + r, col, acc[r]);
     }
     if (a.sumsq) add_sumsq(a.sumsq, sq);
 }
