@@ -394,15 +394,18 @@ __device__ __forceinline__ void tc_contract_body(const CUtensorMap& tmA, const C
     const int nacc = ok ? (2 * nk < NACC ? 2 * nk : NACC) : 0;
     const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
 
-    // 1) the peer's columns -> the peer's receive buffer [HALF][BM]
+    // 1) the peer's columns -> the peer's receive buffer [HALF / 4][BM][4]: a
+    //    thread's four consecutive columns are one 16-byte store, a warp's 512
+    //    contiguous bytes
     const uint32_t rrecv = mapa(recv, kpeer);
 #pragma unroll
     for (int c = 0; c < WCOLS / 16; ++c) {
         float v[16];
         acc_sum16(trow, pcol0 + c * 16, nacc, v);
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-            st_cluster_f32(rrecv + 4u * ((sub * WCOLS + c * 16 + j) * BM + lrow), v[j]);
+        for (int j = 0; j < 16; j += 4)
+            st_cluster_v4(rrecv + 16u * (((sub * WCOLS + c * 16 + j) >> 2) * BM + lrow), v[j],
+                          v[j + 1], v[j + 2], v[j + 3]);
     }
     cluster_sync();
 
@@ -414,9 +417,13 @@ __device__ __forceinline__ void tc_contract_body(const CUtensorMap& tmA, const C
         float v[16];
         acc_sum16(trow, ocol0 + c * 16, nacc, v);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
+        for (int j = 0; j < 16; j += 4) {
             const int hc = sub * WCOLS + c * 16 + j;    // column within the CTA's half
-            xv[c * 16 + j] = v[j] + recv_ptr[hc * BM + lrow];
+            const float4 r = reinterpret_cast<const float4*>(recv_ptr)[(hc >> 2) * BM + lrow];
+            xv[c * 16 + j] = v[j] + r.x;
+            xv[c * 16 + j + 1] = v[j + 1] + r.y;
+            xv[c * 16 + j + 2] = v[j + 2] + r.z;
+            xv[c * 16 + j + 3] = v[j + 3] + r.w;
         }
     }
     // paired rows: exchange through shared memory ([HALF][BM] float32 in the
@@ -443,14 +450,18 @@ __device__ __forceinline__ void tc_contract_body(const CUtensorMap& tmA, const C
         const uint32_t pbuf = base + 4u * HALF * BM;
         const uint32_t prx = mapa(pbuf, crank ^ 1u);
 #pragma unroll
-        for (int jj = 0; jj < WCOLS; ++jj)
-            st_cluster_f32(prx + 4u * ((sub * WCOLS + jj) * BM + lrow), xv[jj]);
+        for (int jj = 0; jj < WCOLS; jj += 4)       // [HALF / 4][BM][4], as the split-K buffer
+            st_cluster_v4(prx + 16u * (((sub * WCOLS + jj) >> 2) * BM + lrow), xv[jj], xv[jj + 1],
+                          xv[jj + 2], xv[jj + 3]);
         cluster_sync();
-        const float* pown = reinterpret_cast<const float*>(gbase) + HALF * BM;
+        const float4* pown = reinterpret_cast<const float4*>(gbase) + HALF * BM / 4;
 #pragma unroll
-        for (int jj = 0; jj < WCOLS; ++jj) {
-            const float o = pown[(sub * WCOLS + jj) * BM + lrow];
-            xv[jj] = parity == 0 ? xv[jj] + o : o - xv[jj];
+        for (int jj = 0; jj < WCOLS; jj += 4) {
+            const float4 o4 = pown[((sub * WCOLS + jj) >> 2) * BM + lrow];
+            const float o[4] = {o4.x, o4.y, o4.z, o4.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                xv[jj + k] = parity == 0 ? xv[jj + k] + o[k] : o[k] - xv[jj + k];
         }
     }
     float sq = 0.f;                       // this thread's (x_new - f)^2, at most WCOLS terms
