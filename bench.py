@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--matvec-only", action="store_true",
+                    help="run only the AR matvec comparison (matvec_hbm) and print it")
     ap.add_argument("--stencil", default="fp32", choices=["fp32", "f16x2"],
                     help="arithmetic of the timed step's blur and reblur (f16x2: tensor cores)")
     return ap.parse_args()
@@ -177,6 +179,10 @@ def run_own(args):
         dist.init_process_group("nccl", device_id=dev)
     ar.lib()
     stream = torch.cuda.current_stream(dev)
+    if args.matvec_only:
+        if rank == 0:
+            print(json.dumps({"matvec_hbm": matvec_hbm_form(ar, torch, dev, stream)}), flush=True)
+        return
 
     h, g, f = make_host_inputs(ar, torch, dev)
     g_d = torch.from_numpy(g).to(dev)
