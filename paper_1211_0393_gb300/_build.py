@@ -37,12 +37,21 @@ def _headers() -> list[str]:
     return glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
 
 
+# Translation units whose optimiser and ptxas run on all cores (--split-compile):
+# the stencil file, with its kernels instantiated for every PSF half-width,
+# dominates the build (about 170 s on one core).  Measured on a GB300: its kernels
+# run as fast or faster split; the contraction file compiles in seconds and its
+# kernels ran slower split, so it is compiled whole.
+SPLIT = {"ar_conv.cu"}
+
+
 def _compile(src: str) -> str:
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
     newest = max([os.path.getmtime(src)] + [os.path.getmtime(h) for h in _headers()])
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest:
         return obj
-    cmd = [nvcc()] + NVCC_FLAGS + ["-c", src, "-o", obj]
+    split = ["--split-compile=0"] if os.path.basename(src) in SPLIT else []
+    cmd = [nvcc()] + NVCC_FLAGS + split + ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
