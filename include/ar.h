@@ -99,9 +99,17 @@ typedef enum ar_precision { AR_PRECISION_FP32 = 0, AR_PRECISION_BF16X2 = 1,
  *                    accumulate in float32 (about 2^-21 relative per term, the
  *                    float32 stencil's order).  Serves q1, q2 <= 8 under AR and
  *                    Reflective BCs with n2 % 4 == 0 and a 16-byte aligned
- *                    input; other arguments take AR_STENCIL_FP32. */
+ *                    input; other arguments take AR_STENCIL_FP32.
+ *  AR_STENCIL_AUTO:  whichever of the two the library measures faster for the
+ *                    shape (one timing of each, y = A x on a zero image of the
+ *                    same size and PSF support, the first time a shape and
+ *                    boundary condition are seen on a device; kept for the
+ *                    process); AR_STENCIL_FP32 where the tensor-core path does
+ *                    not apply.  The timing allocates two images and a plan
+ *                    (stream-ordered) and synchronizes the stream. */
 #define AR_STENCIL_FP32 0
 #define AR_STENCIL_F16X2 16
+#define AR_STENCIL_AUTO 32
 
 /* Opaque preconditioner: the symmetrized-PSF eigenvalues and Tikhonov filter
  * for one (PSF, n1, n2, alpha), plus the AR transform operands and scratch
@@ -145,7 +153,7 @@ AR_API ar_status ar_reblur_apply_bc(const float* x, float* y, int n1, int n2,
 
 /*
  * ar_blur_apply_bc / ar_reblur_apply_bc with the stencil arithmetic `stencil`
- * (AR_STENCIL_FP32 or AR_STENCIL_F16X2).  With AR_STENCIL_F16X2 the call
+ * (AR_STENCIL_FP32, AR_STENCIL_F16X2 or AR_STENCIL_AUTO).  With AR_STENCIL_F16X2 the call
  * allocates (stream-ordered) and frees a plan of about 70 KB for the PSF.
  * Arguments and errors as ar_blur_apply_bc, plus AR_ERR_INVALID_ARG for an
  * unknown stencil and AR_ERR_ALLOC when the plan cannot be allocated.
@@ -291,8 +299,9 @@ AR_API ar_status ar_restore_plain_static(const float* g, const double* psf_host,
 
 /* ar_restore with an explicit ar_precision for the preconditioner's
  * contractions (ignored when precondition == 0), optionally OR-ed with
- * AR_STENCIL_F16X2 for the blur and reblur stencils (honoured with and
- * without the preconditioner).  ar_restore is
+ * AR_STENCIL_F16X2 or AR_STENCIL_AUTO for the blur and reblur stencils
+ * (honoured with and without the preconditioner; both together are
+ * AR_ERR_INVALID_ARG).  ar_restore is
  * ar_restore_ex(..., AR_PRECISION_FP32, ...). */
 AR_API ar_status ar_restore_ex(const float* g, const double* psf_host,
                                int n1, int n2, int q1, int q2, double alpha, double tau,

@@ -52,8 +52,9 @@ class BatchItem(ctypes.Structure):
 PRECISION = {"fp32": 0, "bf16x2": 1, "fft": 2, "auto": 3}
 PRECISION_NAME = {v: k for k, v in PRECISION.items()}
 
-# stencil arithmetic (ar.h AR_STENCIL_*): float32 FMAs or tensor-core fp16 split
-STENCIL = {"fp32": 0, "f16x2": 16}
+# stencil arithmetic (ar.h AR_STENCIL_*): float32 FMAs, tensor-core fp16 split, or
+# the faster of the two for the shape (measured once)
+STENCIL = {"fp32": 0, "f16x2": 16, "auto": 32}
 
 # ar_bc: the method's anti-reflective BCs and the two comparison BCs
 BC = {"ar": 0, "reflective": 1, "periodic": 2}
@@ -197,7 +198,8 @@ def ar_blur_apply(x: torch.Tensor, psf: torch.Tensor, y: torch.Tensor | None = N
     """``y = A_n x`` (blur under ``bc``: "ar", "reflective" or "periodic").
 
     ``psf`` is a float32 CUDA tensor of odd sides; ``stencil`` "fp32" (CUDA-core
-    FMAs) or "f16x2" (tensor cores, two-plane fp16 split, where it applies)."""
+    FMAs), "f16x2" (tensor cores, two-plane fp16 split, where it applies) or "auto"
+    (the faster of the two for the shape, measured the first time)."""
     return _apply("ar_blur_apply", x, psf, y, stream, bc, stencil)
 
 

@@ -145,10 +145,89 @@ ar_status check_bc(int bc) {
     return AR_OK;
 }
 
+namespace {
+// AR_STENCIL_AUTO's measured choice per (device, n1, n2, q1, q2, bc).
+std::mutex g_stencil_mu;
+std::map<std::tuple<int, int, int, int, int, int>, int> g_stencil_choice;
+}  // namespace
+
+// The faster stencil arithmetic for a blur of this shape: one timing of each
+// (y = A x on a zero image, median of three launches after a warm-up, CUDA
+// events) the first time the shape is seen on a device, kept for the process;
+// AR_STENCIL_FP32 where the tensor-core path does not apply.  psf is the
+// caller's device PSF.
+ar_status resolve_stencil(const float* psf, int n1, int n2, int q1, int q2, int bc, cudaStream_t s,
+                          int* out) {
+    *out = AR_STENCIL_FP32;
+    ConvArgs a{};
+    a.n1 = n1;
+    a.n2 = n2;
+    a.q1 = q1;
+    a.q2 = q2;
+    a.psf = psf;
+    a.bc = bc;
+    a.mode = CONV_STORE;
+    if (!conv_tc_applies(a)) return AR_OK;          // aligned buffers below: q and bc decide
+    int dev = 0;
+    AR_CUDA(cudaGetDevice(&dev));
+    const auto key = std::make_tuple(dev, n1, n2, q1, q2, bc);
+    {
+        std::lock_guard<std::mutex> lock(g_stencil_mu);
+        auto it = g_stencil_choice.find(key);
+        if (it != g_stencil_choice.end()) {
+            *out = it->second;
+            return AR_OK;
+        }
+    }
+    set_pool_threshold_once();
+    float t[2] = {0.f, 0.f};
+    ar_status st = AR_OK;
+    {
+        Scratch ws(s);
+        float *x = nullptr, *y = nullptr;
+        uint8_t* plan = nullptr;
+        const size_t n = (size_t)n1 * n2;
+        st = ws.get(&x, n);
+        if (st == AR_OK) st = ws.get(&y, n);
+        if (st == AR_OK) st = ws.get(&plan, kConvTcPlanBytes);
+        if (st == AR_OK && cudaMemsetAsync(x, 0, n * sizeof(float), s) != cudaSuccess)
+            st = fail(AR_ERR_CUDA, "stencil timing input");
+        if (st == AR_OK) st = conv_tc_plan(psf, q1, q2, 0, plan, s);
+        a.x = x;
+        a.out = y;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (st == AR_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+            st = fail(AR_ERR_CUDA, "stencil timing events");
+        for (int v = 0; st == AR_OK && v < 2; ++v) {
+            a.tcplan = v ? plan : nullptr;
+            float r[3] = {0.f, 0.f, 0.f};
+            st = conv_launch(a, s);                  // warm-up
+            for (int k = 0; st == AR_OK && k < 3; ++k) {
+                cudaEventRecord(e0, s);
+                st = conv_launch(a, s);
+                cudaEventRecord(e1, s);
+                if (st == AR_OK && cudaEventSynchronize(e1) != cudaSuccess)
+                    st = fail(AR_ERR_CUDA, "stencil timing");
+                if (st == AR_OK) cudaEventElapsedTime(&r[k], e0, e1);
+            }
+            const float lo = r[0] < r[1] ? r[0] : r[1], hi = r[0] < r[1] ? r[1] : r[0];
+            t[v] = r[2] < lo ? lo : (r[2] > hi ? hi : r[2]);
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+    if (st != AR_OK) return st;
+    const int choice = t[1] < t[0] ? AR_STENCIL_F16X2 : AR_STENCIL_FP32;
+    std::lock_guard<std::mutex> lock(g_stencil_mu);
+    g_stencil_choice[key] = choice;
+    *out = choice;
+    return AR_OK;
+}
+
 ar_status apply_common(const float* x, float* y, int n1, int n2, const float* psf, int q1, int q2,
                        int bc, void* stream, int flip, int stencil = AR_STENCIL_FP32) {
     if (!x || !y || !psf) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
-    if (stencil != AR_STENCIL_FP32 && stencil != AR_STENCIL_F16X2)
+    if (stencil != AR_STENCIL_FP32 && stencil != AR_STENCIL_F16X2 && stencil != AR_STENCIL_AUTO)
         return fail(AR_ERR_INVALID_ARG, "unknown stencil arithmetic %d", stencil);
     AR_TRY(check_bc(bc));
     AR_TRY(check_image_sizes(n1, n2, 1));
@@ -169,6 +248,7 @@ ar_status apply_common(const float* x, float* y, int n1, int n2, const float* ps
     a.mode = CONV_STORE;
     a.bc = bc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (stencil == AR_STENCIL_AUTO) AR_TRY(resolve_stencil(psf, n1, n2, q1, q2, bc, s, &stencil));
     if (stencil == AR_STENCIL_F16X2 && conv_tc_applies(a)) {
         set_pool_threshold_once();       // the plan's stream-ordered allocation stays pooled
         Scratch ws(s);
@@ -278,8 +358,9 @@ static ar_status restore_run(const float* g, const double* psf_host, int n1, int
                              double* res_trace = nullptr) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     set_pool_threshold_once();
-    const bool tc_stencil = (precision & AR_STENCIL_F16X2) != 0;
-    precision &= ~AR_STENCIL_F16X2;
+    bool tc_stencil = (precision & AR_STENCIL_F16X2) != 0;
+    const bool auto_stencil = (precision & AR_STENCIL_AUTO) != 0;
+    precision &= ~(AR_STENCIL_F16X2 | AR_STENCIL_AUTO);
     const size_t n = (size_t)n1 * n2;
     const size_t nb = n * sizeof(float);
     const size_t k = (size_t)(2 * q1 + 1) * (2 * q2 + 1);
@@ -366,6 +447,11 @@ static ar_status restore_run(const float* g, const double* psf_host, int n1, int
         reblur.early_trigger = reblur.mode == CONV_SPLIT3 || reblur.mode == CONV_STORE ? 1 : 0;
         blur.spread = reblur.spread = 1;
         reblur.f = f_true;
+        if (st == AR_OK && auto_stencil) {            // the psf upload is ordered before
+            int choice = AR_STENCIL_FP32;
+            st = resolve_stencil(psf, n1, n2, q1, q2, bc, s, &choice);
+            tc_stencil = choice == AR_STENCIL_F16X2;
+        }
         if (st == AR_OK && tc_stencil && conv_tc_applies(blur)) {
             // the PSF's tensor-core plans for A and A' (the reblur's input r is
             // aligned like x_out when x_out is; conv_launch checks each call)
@@ -540,7 +626,10 @@ static ar_status validate_restore_args(const float* g, const double* psf_host, i
     if (!g || !psf_host || !x_out) return fail(AR_ERR_INVALID_ARG, "null pointer argument");
     AR_TRY(check_bc(bc));
     const bool pc = precondition != 0;
-    precision &= ~AR_STENCIL_F16X2;       // the stencil flag combines with every precision
+    if ((precision & AR_STENCIL_F16X2) && (precision & AR_STENCIL_AUTO))
+        return fail(AR_ERR_INVALID_ARG, "AR_STENCIL_F16X2 and AR_STENCIL_AUTO together");
+    precision &= ~(AR_STENCIL_F16X2 | AR_STENCIL_AUTO);   // the stencil flags combine with
+                                                          // every precision
     if (pc) AR_TRY(check_precision(precision, bc, n1, n2));
     else if (precision < AR_PRECISION_FP32 || precision > AR_PRECISION_AUTO)
         return fail(AR_ERR_INVALID_ARG, "unknown precision %d", precision);

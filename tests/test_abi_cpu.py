@@ -214,16 +214,17 @@ def test_injected_allocation_failure_is_reported(L):
 
 
 def test_stencil_arithmetic_validation(L):
-    """AR_STENCIL_F16X2 (16) is accepted by the apply calls and OR-ed into the
-    restoration's precision; anything else is rejected before any GPU work."""
+    """AR_STENCIL_F16X2 (16) and AR_STENCIL_AUTO (32) are accepted by the apply calls
+    and OR-ed into the restoration's precision (not both); anything else is
+    rejected before any GPU work."""
     args = (FAKE, FAKE * 4, 8, 8, FAKE * 16, 1, 1, 0)
     for stencil in (3, 17, -1):
         assert L.ar_blur_apply_ex(*args, stencil, None) == 1
         assert L.ar_reblur_apply_ex(*args, stencil, None) == 1
-    for stencil in (0, 16):                    # accepted: the alias check runs next
+    for stencil in (0, 16, 32):                # accepted: the alias check runs next
         assert L.ar_blur_apply_ex(FAKE, FAKE + 4, 8, 8, FAKE * 16, 1, 1, 0, stencil, None) == 2
     hp = _psf(2, 2).ctypes.data
-    for precision in (16 | 7, 32):
+    for precision in (16 | 7, 64, 16 | 32):     # unknown, or both stencil flags
         assert L.ar_restore_bc(FAKE, hp, 16, 16, 2, 2, 0.1, 1.0, 3, 0, 1, precision, None,
                                None, FAKE * 64, None, None, None) == 1
     assert L.ar_restore_bc(FAKE, hp, 16, 16, 2, 2, 0.1, 1.0, 3, 0, 1, 16 | 1, None, None,

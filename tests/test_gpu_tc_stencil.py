@@ -298,3 +298,28 @@ def test_restore_tc_stencil_past_one_wave(ar, pc, alpha):
     assert rel_l2(x.cpu().numpy(), xo) <= tol
     assert np.all(np.abs(np.asarray(tr) - to) <= tol * (1.0 + to))
 
+
+
+@pytest.mark.parametrize("n,q", [(1024, 7), (4096, 7), (512, 1)])
+def test_auto_stencil_is_one_of_the_two(ar, n, q):
+    """AR_STENCIL_AUTO runs one of the two arithmetics, chosen by a timing the
+    first time the shape is seen: its result equals one of theirs bit for bit,
+    and a second call makes the same choice."""
+    rng = np.random.default_rng(n + q)
+    x = dev(rng.uniform(0, 1, (n, n)))
+    h = dev(rand_psf(rng, q, q))
+    a32 = ar.ar_blur_apply(x, h)
+    atc = ar.ar_blur_apply(x, h, stencil="f16x2")
+    got1 = ar.ar_blur_apply(x, h, stencil="auto")
+    got2 = ar.ar_blur_apply(x, h, stencil="auto")
+    assert torch.equal(got1, a32) or torch.equal(got1, atc)
+    assert torch.equal(got1, got2)
+
+
+def test_restore_auto_stencil_is_one_of_the_two(ar):
+    h = W.psf_config1()
+    g, f = _workload(64, h, "blocks", 0, 0.01)
+    gd, fd = dev(g), dev(f)
+    outs = [ar.ar_restore(gd, h, 0.03, 1.0, 5, True, f_true=fd, stencil=st)[0].clone()
+            for st in ("fp32", "f16x2", "auto")]
+    assert torch.equal(outs[2], outs[0]) or torch.equal(outs[2], outs[1])
